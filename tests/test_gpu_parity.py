@@ -1,0 +1,238 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Permanents, coefficients and job lists must agree bit for bit; the KKLLL
+estimate within 1e-5 relative (FP32 against fp64); the cost-network
+gradient within FP32 rounding of the fp64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+pk = pytest.importorskip("paper_1112_6072_gb300")
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+M256 = (1 << 256) - 1
+
+
+def signed_low(v, bits):
+    v &= (1 << bits) - 1
+    return v - (1 << bits) if v >> (bits - 1) else v
+
+
+# ---------------------------------------------------------------- leaf Ryser (K2)
+def test_leaf_batch_small_sizes_all_paths():
+    """n = 1..20 dense small-integer leaves, every register width, a ragged
+    tail of tiny jobs, and the 128-bit ring."""
+    mats = []
+    rng = np.random.default_rng(11)
+    for n in list(range(1, 21)) + [3, 7, 12, 17, 19]:
+        mats.append(W.leaf_batch(1, int(rng.integers(1 << 30)), nmin=n, nmax=n)[0])
+    with pk.Plan(mats) as plan:
+        plan.expand()
+        plan.evaluate(order=np.arange(plan.njobs, dtype=np.uint32))
+        got = plan.results()
+    want = [oracle.permanent(m) for m in mats]
+    assert got == want
+
+
+def test_leaf_batch_signed_and_wide():
+    """Signed entries (cancellation), the 256-bit ring and bit classes 15 and
+    31 of the row-product tree."""
+    mats = [W.random_small(n, 50 + n, lo=-3, hi=3) for n in range(2, 17)]
+    mats += [W.random_small(12, 7, lo=-900, hi=1000)]           # bit class 15, 256-bit ring
+    mats += [W.random_small(6, 8, lo=-(1 << 20), hi=1 << 20)]   # bit class 31
+    mats += [np.ones((n, n), np.int64) for n in (20, 22, 24)]    # n! beyond 64 bits
+    with pk.Plan(mats) as plan:
+        plan.expand()
+        plan.evaluate(order=np.arange(plan.njobs, dtype=np.uint32))
+        got = plan.results()
+    want = [oracle.ryser(m) if m.shape[0] <= 16 else oracle.permanent(m) for m in mats]
+    assert got[-3:] == [math.factorial(20), math.factorial(22), math.factorial(24)]
+    assert got == want
+
+
+def test_leaf_chunk_sizes_agree():
+    mats = W.leaf_batch(24, seed=5, nmin=14, nmax=20)
+    res = []
+    for c in (1, 3, 6, 10):
+        with pk.Plan(mats, chunk_log2=c) as plan:
+            plan.expand()
+            plan.evaluate(order=np.arange(plan.njobs, dtype=np.uint32))
+            res.append(plan.results())
+    assert all(r == res[0] for r in res)
+    assert res[0] == [oracle.permanent(m) for m in mats]
+
+
+def test_leaf_batch_full_size_sample():
+    """Config-2 shape (n in [12, 24], P(nonzero) = 0.35, values 1..3): a
+    seeded sample at full size, including the largest order."""
+    mats = W.leaf_batch(10, seed=2024)
+    mats += W.leaf_batch(1, seed=99, nmin=24, nmax=24)
+    with pk.Plan(mats) as plan:
+        plan.expand()
+        plan.evaluate()
+        got = plan.results()
+    want = oracle.job_permanents(mats)
+    assert got == want
+
+
+def test_zero_and_empty_inputs():
+    z = W.random_small(5, 1)
+    z[:, 2] = 0
+    with pk.Plan([z, np.zeros((0, 0), np.int64), np.eye(3, dtype=np.int64)]) as plan:
+        plan.expand()
+        plan.evaluate()
+        assert plan.results() == [0, 1, 1]
+
+
+def test_invalid_arguments_rejected():
+    with pytest.raises(pk.PermError):
+        pk.Plan([np.full((3, 3), 1 << 40, dtype=np.int64)])
+    with pytest.raises(pk.PermError):
+        pk.Plan([np.ones((130, 130), np.int64)])
+    a = W.regular3(12, 1)
+    with pk.Plan([a], split_depth=2, leaf_size=4) as plan:
+        plan.expand()
+        with pytest.raises(pk.PermError):
+            plan.evaluate(order=np.zeros(plan.njobs, dtype=np.uint32) if plan.njobs > 1 else [5])
+
+
+# ---------------------------------------------------------------- expansion (K1)
+@pytest.mark.parametrize("n,seed,d,L", [(10, 1, 3, 0), (16, 2, 6, 4), (24, 3, 10, 8), (36, 1, 20, 16)])
+def test_job_list_matches_oracle(n, seed, d, L):
+    a = W.regular3(n, seed)
+    with pk.Plan([a], split_depth=d, leaf_size=L) as plan:
+        plan.expand()
+        got = plan.jobs_export()
+    want = oracle.jobs(a, d, L)
+    assert len(got) == len(want)
+    for (mi, gm, gc), (wm, wc) in zip(got, want):
+        assert mi == 0
+        assert gm.shape == wm.shape and (gm == wm).all()
+        assert gc == wc % (1 << 256)
+
+
+def test_job_list_signed_sparse():
+    a = W.random_small(14, 77, lo=-2, hi=2, density=0.25)
+    a[np.arange(14), np.arange(14)] = 1  # no zero line
+    with pk.Plan([a], split_depth=5, leaf_size=3) as plan:
+        plan.expand()
+        got = plan.jobs_export()
+    want = oracle.jobs(a, 5, 3)
+    assert len(got) == len(want)
+    for (_, gm, gc), (wm, wc) in zip(got, want):
+        assert (gm == wm).all() and gc == wc % (1 << 256)
+
+
+# ---------------------------------------------------------------- hybrid end to end (K1+K3+K2+K6)
+def test_config1_regular36_d20_L16():
+    a = W.regular3(36, 1)
+    with pk.Plan([a], split_depth=20, leaf_size=16) as plan:
+        plan.expand()
+        rec = plan.evaluate(records=True)
+        got = plan.result(0)
+        bits = plan.result_bits(0)
+    assert got == oracle.permanent(a)
+    # every job's coef * per(job) against the oracle's job values
+    jobs = oracle.jobs(a, 20, 16)
+    pj = oracle.job_permanents([m for m, _ in jobs])
+    for r, (m, c), p in zip(rec, jobs, pj):
+        assert signed_low(r.value_mod, bits) == c * p
+
+
+@pytest.mark.parametrize("d,L", [(0, 8), (6, 8), (10, 12), (14, 6), (4, 2)])
+def test_depth_first_evaluator(d, L):
+    """Jobs above the leaf order go through the depth-first evaluator."""
+    a = W.regular3(36, 2)
+    with pk.Plan([a], split_depth=d, leaf_size=L) as plan:
+        plan.expand()
+        rec = plan.evaluate(records=True)
+        got = plan.result(0)
+    assert got == oracle.permanent(a)
+    assert sum(r.nodes for r in rec) >= len(rec)
+
+
+def test_depth_first_signed_and_column_pivots():
+    for seed in range(4):
+        a = W.random_small(18, 300 + seed, lo=-2, hi=3, density=0.3)
+        a[np.arange(18), (np.arange(18) + seed) % 18] = 1
+        with pk.Plan([a], split_depth=3, leaf_size=6) as plan:
+            plan.expand()
+            plan.evaluate()
+            assert plan.result(0) == oracle.permanent(a)
+
+
+def test_c60_both_constructions():
+    from conftest import read_adjacency
+    mats = [W.c60(seed=3), read_adjacency("c60_adjacency.txt")]
+    want = oracle.permanent(mats[0], d=12)
+    for order in ("natural", "lpt"):
+        with pk.Plan(mats, leaf_size=12, order=order) as plan:
+            plan.expand()
+            plan.evaluate()
+            assert plan.results() == [want, want]
+
+
+def test_batch_of_matrices_one_launch():
+    mats = [W.regular3(n, n) for n in (20, 24, 28, 30)] + [W.sparse_rows(22, 5)]
+    with pk.Plan(mats, leaf_size=10) as plan:
+        plan.expand()
+        plan.order("lpt")
+        plan.evaluate()
+        got = plan.results()
+    assert got == [oracle.permanent(m) for m in mats]
+
+
+# ---------------------------------------------------------------- estimator (K4) and order
+def test_kklll_matches_oracle():
+    a = W.regular3(30, 4)
+    with pk.Plan([a], split_depth=14, leaf_size=8, kklll_trials=0, seed=1234) as plan:
+        plan.expand()
+        la = plan.estimate()
+        jobs = plan.jobs_export()
+    rng = np.random.default_rng(0)
+    for j in rng.choice(len(jobs), size=min(12, len(jobs)), replace=False):
+        want = oracle.kklll_log_ap(jobs[j][1], seed=1234, job=int(j))
+        assert abs(float(la[j]) - want) < 1e-5, (j, la[j], want)
+
+
+def test_lpt_order_is_stable_sort_of_estimate():
+    a = W.regular3(32, 9)
+    with pk.Plan([a], split_depth=12, leaf_size=8) as plan:
+        plan.expand()
+        la = plan.estimate()
+        q = plan.order("lpt")
+    want = sorted(range(len(la)), key=lambda i: (-float(la[i]), i))
+    assert list(q) == want
+
+
+# ---------------------------------------------------------------- cost network (K5)
+def test_mlp_gradient_matches_oracle():
+    rng = np.random.default_rng(3)
+    p = pk.mlp_init(3)
+    x = rng.normal(size=(300, pk.MLP_FEATURES)).astype(np.float32)
+    y = rng.normal(size=300).astype(np.float32)
+    loss, g = pk.mlp_grad(p, x, y)
+    wl, wg = omlp.loss_and_grad(p.astype(np.float64), x.astype(np.float64), y.astype(np.float64))
+    assert abs(loss - wl) <= 1e-5 * max(1.0, abs(wl))
+    assert np.allclose(g, wg, rtol=1e-3, atol=1e-5 * np.abs(wg).max())
+    pred = pk.mlp_predict(p, x)
+    assert np.allclose(pred, omlp.forward(p, x)[0], rtol=1e-4, atol=1e-5)
+
+
+def test_mlp_training_reduces_loss():
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=(2000, pk.MLP_FEATURES)).astype(np.float32)
+    y = (x[:, 0] * 2 - x[:, 3] + 0.5 * x[:, 10]).astype(np.float32)
+    p0 = pk.mlp_init(0)
+    l0, _ = pk.mlp_grad(p0, x, y)
+    p1, l1 = pk.mlp_train(p0, x, y, steps=300, lr=3e-3)
+    assert l1 < 0.1 * l0
