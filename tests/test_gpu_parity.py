@@ -106,7 +106,7 @@ def test_invalid_arguments_rejected():
 
 
 # ---------------------------------------------------------------- expansion (K1)
-@pytest.mark.parametrize("n,seed,d,L", [(10, 1, 3, 0), (16, 2, 6, 4), (24, 3, 10, 8), (36, 1, 20, 16)])
+@pytest.mark.parametrize("n,seed,d,L", [(10, 1, 3, 2), (16, 2, 6, 4), (24, 3, 10, 8), (36, 1, 20, 16)])
 def test_job_list_matches_oracle(n, seed, d, L):
     a = W.regular3(n, seed)
     with pk.Plan([a], split_depth=d, leaf_size=L) as plan:
