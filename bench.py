@@ -152,6 +152,10 @@ def run_ours(args, rank, world, torch):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         step_ms = float(t.item())
     value = LEAF_COUNT * world / (step_ms * 1e-3)
+    launches = plan.last_launches if hasattr(plan, "last_launches") else None
+    if args.kernels_only:
+        return {"metric": METRIC, "value": value, "unit": "leaf permanents/s", "ms_per_step": step_ms,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "kernels_only": True}
 
     # end to end through the public API from host buffers
     e2e_ms = []
@@ -202,7 +206,7 @@ def run_ours(args, rank, world, torch):
                    "parallelism": f"jobs sharded per rank (x{world})"},
         "e2e": {"value": LEAF_COUNT * world / (min(e2e_ms) * 1e-3), "unit": "leaf permanents/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms": min(e2e_ms)},
-        "gpu_launches": None,
+        "gpu_launches": launches * args.steps if launches is not None else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_basis": f"{sms} SMs x {imad_per_clk_sm} IMAD/clk x {sm_mhz:.0f} MHz (median under load)",
@@ -291,7 +295,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chunk-log2", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--leaf-count", type=int, default=LEAF_COUNT,
+                    help="matrices in the leaf batch (smaller for profiler captures)")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="skip the e2e, C60 and probe legs (profiler captures)")
     args = ap.parse_args()
+    globals()["LEAF_COUNT"] = args.leaf_count
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":

@@ -161,6 +161,10 @@ perm_status perm_eval_batch(perm_jobs_t* jobs, const uint32_t* order, perm_job_r
  * the plan's stream. */
 perm_status perm_last_eval_ms(perm_plan_t* plan, float* ms);
 
+/* Number of kernel launches the last perm_eval_batch issued between its two
+ * timing events (scans included). */
+perm_status perm_last_eval_launches(perm_plan_t* plan, int32_t* launches);
+
 /* a8 -- per(A) of matrix `index` after perm_eval_batch, as a magnitude in
  * little-endian uint32 limbs and a sign (-1, 0, +1).  cap too small ->
  * PERM_ESHORTBUF with *nlimbs set to the required length. */

@@ -32,7 +32,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "overflow", 3: "timeout", 4: "cuda 
 
 EXPORTED = [
     "perm_opts_default", "perm_plan_create", "perm_plan_destroy", "perm_expand", "perm_estimate",
-    "perm_order", "perm_eval_batch", "perm_last_eval_ms", "perm_result", "perm_result_bits",
+    "perm_order", "perm_eval_batch", "perm_last_eval_ms", "perm_last_eval_launches", "perm_result", "perm_result_bits",
     "perm_result_words", "perm_jobs_export", "perm_exact", "perm_job_features", "perm_mlp_grad",
     "perm_mlp_train", "perm_mlp_predict", "perm_mlp_attach", "perm_ubench_imad",
     "perm_status_string", "perm_last_error",
@@ -96,6 +96,7 @@ def _lib():
         lib.perm_order.argtypes = [vp, ctypes.c_int32, P(ctypes.c_uint32)]
         lib.perm_eval_batch.argtypes = [vp, P(ctypes.c_uint32), P(perm_job_result)]
         lib.perm_last_eval_ms.argtypes = [vp, P(ctypes.c_float)]
+        lib.perm_last_eval_launches.argtypes = [vp, P(ctypes.c_int32)]
         lib.perm_result.argtypes = [vp, ctypes.c_int32, P(ctypes.c_uint32), ctypes.c_int32,
                                     P(ctypes.c_int32), P(ctypes.c_int32)]
         lib.perm_result_bits.argtypes = [vp, ctypes.c_int32, P(ctypes.c_int32)]
@@ -298,6 +299,12 @@ class Plan:
     def last_eval_ms(self) -> float:
         v = ctypes.c_float()
         _ck(_lib().perm_last_eval_ms(self._h, ctypes.byref(v)), "perm_last_eval_ms")
+        return v.value
+
+    @property
+    def last_launches(self) -> int:
+        v = ctypes.c_int32()
+        _ck(_lib().perm_last_eval_launches(self._h, ctypes.byref(v)), "perm_last_eval_launches")
         return v.value
 
     def result_bits(self, i) -> int:

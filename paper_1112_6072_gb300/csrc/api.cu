@@ -159,6 +159,7 @@ struct perm_plan {
   perm_jobs* jobs = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   float last_ms = 0.f;
+  int32_t last_launches = 0;
   bool evaluated = false;
   std::vector<float> mlp;
 };
@@ -650,24 +651,6 @@ extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, pe
     }
   }
   if (dfs_max > PERM_MAX_JOB_N) return PERM_EINVAL;
-  // stable partition of the leaf queue into (NMAX, W) groups
-  static const int kGroupNmax[4] = {8, 16, 24, 32};
-  int64_t group_count[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  {
-    std::vector<uint32_t> grouped;
-    grouped.reserve(leafq.size());
-    std::vector<int> gid(leafq.size());
-    for (size_t k = 0; k < leafq.size(); ++k) {
-      const int m = J->h_m[leafq[k]];
-      const int nm = m <= 8 ? 0 : (m <= 16 ? 1 : (m <= 24 ? 2 : 3));
-      gid[k] = nm + (P->w[J->h_mat[leafq[k]]] == 4 ? 4 : 0);
-      group_count[gid[k]]++;
-    }
-    for (int g = 0; g < 8; ++g)
-      for (size_t k = 0; k < leafq.size(); ++k)
-        if (gid[k] == g) grouped.push_back(leafq[k]);
-    leafq.swap(grouped);
-  }
   const int64_t nl = (int64_t)leafq.size(), nd = (int64_t)dfsq.size();
   uint32_t* d_lq = dget<uint32_t>(M, nl);
   uint32_t* d_dq = dget<uint32_t>(M, nd);
@@ -683,8 +666,34 @@ extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, pe
   const int64_t undo_w = dfs_undo_words(tile);
   int64_t* undo = nd > 0 ? dget<int64_t>(M, undo_w * dfs_warps) : nullptr;
   if (!d_lq || !d_dq || !counts || !prefix || !stmp || !ctr || (nd > 0 && !undo)) return PERM_ENOMEM;
-  if (nl) CK(cudaMemcpyAsync(d_lq, leafq.data(), 4 * nl, cudaMemcpyHostToDevice, s));
   if (nd) CK(cudaMemcpyAsync(d_dq, dfsq.data(), 4 * nd, cudaMemcpyHostToDevice, s));
+  // leaf variants: classify on the device, then group stably by variant
+  std::vector<std::pair<int64_t, int64_t>> groups;  // (offset, count) in the grouped leaf queue
+  std::vector<int32_t> group_cls;
+  if (nl) {
+    int32_t* d_cls = dget<int32_t>(M, nl);
+    if (!d_cls) return PERM_ENOMEM;
+    std::vector<int32_t> cls(nl);
+    CK(cudaMemcpyAsync(d_lq, leafq.data(), 4 * nl, cudaMemcpyHostToDevice, s));
+    CK(launch_leaf_classify(d_lq, nl, J->a, J->arena, P->d_mat_w, d_cls, s));
+    CK(cudaMemcpyAsync(cls.data(), d_cls, 4 * nl, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    M.put(d_cls);
+    std::vector<int32_t> distinct(cls.begin(), cls.end());
+    std::sort(distinct.begin(), distinct.end());
+    distinct.erase(std::unique(distinct.begin(), distinct.end()), distinct.end());
+    std::vector<uint32_t> grouped;
+    grouped.reserve(nl);
+    for (int32_t c : distinct) {
+      const int64_t start = (int64_t)grouped.size();
+      for (int64_t k = 0; k < nl; ++k)
+        if (cls[k] == c) grouped.push_back(leafq[k]);
+      groups.push_back({start, (int64_t)grouped.size() - start});
+      group_cls.push_back(c);
+    }
+    leafq.swap(grouped);
+    CK(cudaMemcpyAsync(d_lq, leafq.data(), 4 * nl, cudaMemcpyHostToDevice, s));
+  }
   const int64_t nj = std::max<int64_t>(n, 1);
   CK(cudaMemsetAsync(J->out.acc, 0, 32 * nj, s));
   CK(cudaMemsetAsync(J->out.t_start, 0xff, 8 * nj, s));
@@ -714,18 +723,16 @@ extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, pe
     CK(launch_dfs(D, tile, P->sms, wps, s));
   }
   if (nl > 0) {
-    // one persistent grid per (register width, ring width) group, queue order kept inside each group
-    int64_t off = 0;
-    for (int gi = 0; gi < 8; ++gi) {
-      const int64_t cnt = group_count[gi];
-      if (cnt == 0) continue;
-      CK(launch_leaf_batch(d_lq + off, cnt, kGroupNmax[gi % 4], gi < 4 ? 2 : 4, J->a, J->arena, chunk, counts,
+    // one persistent grid per kernel variant, queue order kept inside each variant
+    for (size_t g = 0; g < groups.size(); ++g) {
+      CK(launch_leaf_batch(d_lq + groups[g].first, groups[g].second, group_cls[g], J->a, J->arena, chunk, counts,
                            prefix, stmp, stb, ctr, J->out, P->sms, s));
-      off += cnt;
     }
     CK(launch_leaf_finalize(d_lq, nl, J->a, J->out, P->d_mat_acc, s));
   }
   CK(cudaEventRecord(P->ev1, s));
+  // per leaf group: task counts, two scan kernels, the batch; plus finalize and the depth-first grid
+  P->last_launches = (int32_t)(4 * groups.size() + (nl > 0 ? 1 : 0) + (nd > 0 ? 1 : 0));
   CK(cudaEventSynchronize(P->ev1));
   CK(cudaEventElapsedTime(&P->last_ms, P->ev0, P->ev1));
   std::vector<int32_t> st(n);
@@ -770,6 +777,12 @@ extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, pe
   for (int64_t j = 0; j < n; ++j)
     if (st[j] != 0) return (perm_status)st[j];
   P->evaluated = true;
+  return PERM_OK;
+}
+
+extern "C" perm_status perm_last_eval_launches(perm_plan_t* P, int32_t* launches) {
+  if (!P || !launches) return PERM_EINVAL;
+  *launches = P->last_launches;
   return PERM_OK;
 }
 

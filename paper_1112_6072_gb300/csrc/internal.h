@@ -24,8 +24,11 @@ cudaError_t sort_desc_f32(const float* keys_in, float* keys_out, const uint32_t*
 size_t sort_tmp_bytes_f32(int64_t n);
 
 // ---- K2 leaf batch -----------------------------------------------------------
-// One (NMAX, W) group of leaf jobs in queue order.
-cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int nmax, int W, const JobArrays& jobs,
+// Kernel variant of every queued leaf job (register width, ring width, path).
+cudaError_t launch_leaf_classify(const uint32_t* queue, int64_t nq, const JobArrays& jobs, const uint64_t* arena,
+                                 const int32_t* mat_w, int32_t* cls, cudaStream_t stream);
+// One variant group of leaf jobs in queue order.
+cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int cls, const JobArrays& jobs,
                               const uint64_t* arena, int chunk_log2, uint64_t* counts_scratch, uint64_t* prefix,
                               void* scan_tmp, size_t scan_tmp_bytes, unsigned long long* task_counter,
                               const JobOut& out, int num_sms, cudaStream_t stream);

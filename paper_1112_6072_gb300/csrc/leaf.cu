@@ -4,6 +4,13 @@
 // pulls tasks through one atomic counter in queue order (the job order set
 // by the LPT / learned ordering), so big jobs queued first are spread over
 // many warps and small jobs fill the tail.
+//
+// A classification pass gives every job its variant: register width NMAX
+// (8/16/24/32 rows), ring width W (2 or 4 words) and path -- the blocked
+// walk of ryser4.cuh with 8 or 16 "N" slots when the row sums fit 7 bits
+// and the two sparsest columns touch at most 16 rows, else the plain walk
+// of ryser.cuh with the 7-, 15- or 31-bit product tree.  Each variant is its
+// own kernel, so each gets the registers it needs and no more.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -11,28 +18,41 @@
 #include "internal.h"
 #include "jobs.cuh"
 #include "ryser.cuh"
+#include "ryser4.cuh"
 
 namespace {
 
 constexpr int LEAF_WARPS = 8;  // warps per block
 
+// path codes
+constexpr int P_G7 = 0, P_G15 = 1, P_G31 = 2, P_F8 = 3, P_F16 = 4, P_BAD = 7;
+
 struct LeafSmem {
   int32_t delta[LEAF_WARPS][(PERM_MAX_LEAF - 1) * 32];
   int32_t rho0[LEAF_WARPS][32];
+  int32_t colcnt[LEAF_WARPS][32];
 };
 
 __host__ __device__ __forceinline__ void leaf_split(int m, int chunk_log2, int& lanes, int& clog,
                                                     uint64_t& tasks) {
-  // m >= 2: 2^(m-1) codes.  Lanes walk aligned blocks of 2^clog >= 2 codes.
+  // m >= 2: 2^(m-1) codes, lanes walk aligned blocks of 2^clog codes
+  // (clog >= 2 once m >= 3, as the blocked walk needs).
   const int e = m - 1;
-  if (e <= 5) {
+  if (e == 1) {
     clog = 1;
-    lanes = 1 << (e - 1);
+    lanes = 1;
     tasks = 1;
     return;
   }
+  if (e <= 6) {
+    clog = 2;
+    lanes = 1 << (e - 2);
+    tasks = 1;
+    return;
+  }
+  const int cl = chunk_log2 < 2 ? 2 : chunk_log2;
   lanes = 32;
-  clog = e - 5 < chunk_log2 ? e - 5 : chunk_log2;
+  clog = e - 5 < cl ? e - 5 : cl;
   tasks = 1ull << (e - 5 - clog);
 }
 
@@ -54,52 +74,132 @@ __global__ void k_leaf_task_counts(const uint32_t* __restrict__ queue, int64_t n
   counts[q] = tasks;
 }
 
-// Load job `job` into the warp's leaf buffers.  Returns false (and sets the
-// job status) when an entry or a row sum leaves the int32 range.
-__device__ bool load_leaf(const uint64_t* __restrict__ arena, int64_t off, int m, int nnz, int nmax,
-                          int32_t* delta, int32_t* rho0, int lane, int& bc) {
+// One thread per queued leaf job: variant code (nmax index) | W | path << 8.
+__global__ void k_leaf_classify(const uint32_t* __restrict__ queue, int64_t nq, JobArrays jobs,
+                                const uint64_t* __restrict__ arena, const int32_t* __restrict__ mat_w,
+                                int32_t* __restrict__ cls) {
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const uint32_t job = queue[q];
+  const int m = jobs.m[job];
+  const int nnz = jobs.nnz[job];
+  CsrView v = csr_view(arena, jobs.off[job], m, nnz);
+  int cc[PERM_MAX_LEAF];
+  for (int j = 0; j < PERM_MAX_LEAF; ++j) cc[j] = 0;
+  int64_t rmax = 0;
+  bool ok = m <= PERM_MAX_LEAF;
+  for (int r = 0; r < m && ok; ++r) {
+    int64_t ra = 0;
+    for (int p = v.rowptr[r]; p < v.rowptr[r + 1]; ++p) {
+      const int64_t a = v.val[p];
+      if (a >= (1ll << 30) || a <= -(1ll << 30)) ok = false;
+      ra += a < 0 ? -a : a;
+      cc[v.col[p]]++;
+    }
+    if (ra >= (1ll << 31)) ok = false;
+    rmax = ra > rmax ? ra : rmax;
+  }
+  const int nmi = m <= 8 ? 0 : (m <= 16 ? 1 : (m <= 24 ? 2 : 3));
+  const int W = mat_w[jobs.mat[job]];
+  int path = P_BAD;
+  if (ok) {
+    const int bc = bit_class(rmax);
+    path = bc == 7 ? P_G7 : (bc == 15 ? P_G15 : P_G31);
+    if (bc == 7 && m >= 3) {
+      int ca = 0, cb = -1;
+      for (int j = 1; j < m; ++j)
+        if (cc[j] < cc[ca]) ca = j;
+      for (int j = 0; j < m; ++j)
+        if (j != ca && (cb < 0 || cc[j] < cc[cb])) cb = j;
+      int k = 0;
+      for (int r = 0; r < m; ++r) {
+        bool t = false;
+        for (int p = v.rowptr[r]; p < v.rowptr[r + 1]; ++p) t = t || v.col[p] == ca || v.col[p] == cb;
+        k += t;
+      }
+      if (k <= 8) path = P_F8;
+      else if (k <= 16 && m > 8) path = P_F16;
+    }
+  }
+  cls[q] = nmi | ((W == 4) ? 4 : 0) | (path << 8);
+}
+
+// Load a leaf for the plain walk: rows in order, Gray column j = column j,
+// the last column carries the Nijenhuis-Wilf offset.
+__device__ void load_plain(const uint64_t* __restrict__ arena, int64_t off, int m, int nnz, int nmax,
+                           int32_t* delta, int32_t* rho0, int lane) {
   CsrView v = csr_view(arena, off, m, nnz);
   const int cols = m - 1;
   for (int k = lane; k < cols * nmax; k += 32) delta[k] = 0;
   __syncwarp();
-  int64_t rmax = 0;
-  bool ok = true;
   for (int i = lane; i < nmax; i += 32) {
     if (i >= m) {
       rho0[i] = 1;
       continue;
     }
-    int64_t rs = 0, ra = 0, last = 0;
+    int64_t rs = 0, last = 0;
     for (int p = v.rowptr[i]; p < v.rowptr[i + 1]; ++p) {
-      int c = v.col[p];
-      int64_t a = v.val[p];
-      if (a >= (1ll << 30) || a <= -(1ll << 30)) ok = false;
+      const int c = v.col[p];
+      const int64_t a = v.val[p];
       rs += a;
-      ra += a < 0 ? -a : a;
-      if (c < cols)
-        delta[c * nmax + i] = (int32_t)(2 * a);
-      else
-        last = a;
+      if (c < cols) delta[c * nmax + i] = (int32_t)(2 * a); else last = a;
     }
-    if (ra >= (1ll << 31)) ok = false;
-    rmax = ra > rmax ? ra : rmax;
     rho0[i] = (int32_t)(2 * last - rs);
   }
-  ok = __all_sync(0xffffffffu, ok);
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    int64_t o = __shfl_xor_sync(0xffffffffu, rmax, d);
-    rmax = o > rmax ? o : rmax;
-  }
-  bc = bit_class(rmax);
   __syncwarp();
-  return ok;
 }
 
-// One persistent grid per (NMAX, W) group: every job of the group is held in
-// NMAX registers per lane (rows beyond m padded with rho = 1) and summed
-// modulo 2^(64W).
-template <int NMAX, int W>
+// Load a leaf for the blocked walk: the two sparsest columns become Gray
+// columns 0 and 1, the rows they touch come first, the highest remaining
+// column carries the offset.
+__device__ void load_blocked(const uint64_t* __restrict__ arena, int64_t off, int m, int nnz, int nmax,
+                             int32_t* delta, int32_t* rho0, int32_t* colcnt, int lane) {
+  CsrView v = csr_view(arena, off, m, nnz);
+  const int cols = m - 1;
+  for (int k = lane; k < cols * nmax; k += 32) delta[k] = 0;
+  colcnt[lane] = 0;
+  __syncwarp();
+  if (lane < m)
+    for (int p = v.rowptr[lane]; p < v.rowptr[lane + 1]; ++p) atomicAdd(&colcnt[v.col[p]], 1);
+  __syncwarp();
+  // two sparsest columns (lowest index on ties)
+  const unsigned key = lane < m ? ((unsigned)colcnt[lane] << 8) | (unsigned)lane : 0xffffffffu;
+  unsigned ka = key;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) ka = min(ka, __shfl_xor_sync(0xffffffffu, ka, d));
+  const int ca = (int)(ka & 0xff);
+  unsigned kb = lane == ca ? 0xffffffffu : key;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) kb = min(kb, __shfl_xor_sync(0xffffffffu, kb, d));
+  const int cb = (int)(kb & 0xff);
+  int clast = m - 1;
+  while (clast == ca || clast == cb) --clast;
+  // rows touching ca or cb first
+  bool touched = false;
+  if (lane < m)
+    for (int p = v.rowptr[lane]; p < v.rowptr[lane + 1]; ++p) touched = touched || v.col[p] == ca || v.col[p] == cb;
+  const uint32_t tm = __ballot_sync(0xffffffffu, touched);
+  const uint32_t below = (1u << lane) - 1u;
+  const int k = __popc(tm);
+  const uint32_t valid = m >= 32 ? 0xffffffffu : ((1u << m) - 1u);
+  const int slot = touched ? __popc(tm & below) : k + __popc(~tm & valid & below);
+  if (lane < m) {
+    int64_t rs = 0, last = 0;
+    for (int p = v.rowptr[lane]; p < v.rowptr[lane + 1]; ++p) {
+      const int c = v.col[p];
+      const int64_t a = v.val[p];
+      rs += a;
+      // Gray index of physical column c: ca -> 0, cb -> 1, clast -> offset, others in order from 2
+      const int gj = c == ca ? 0 : (c == cb ? 1 : (c == clast ? -1 : 2 + c - (ca < c) - (cb < c) - (clast < c)));
+      if (gj >= 0) delta[gj * nmax + slot] = (int32_t)(2 * a); else last = a;
+    }
+    rho0[slot] = (int32_t)(2 * last - rs);
+  }
+  for (int i = m + lane; i < nmax; i += 32) rho0[i] = 1;
+  __syncwarp();
+}
+
+template <int NMAX, int W, int PATH>
 __global__ void __launch_bounds__(LEAF_WARPS * 32)
     k_leaf_batch(const uint32_t* __restrict__ queue, int64_t nq, const uint64_t* __restrict__ prefix,
                  JobArrays jobs, const uint64_t* __restrict__ arena, int chunk_log2,
@@ -111,8 +211,7 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32)
   int32_t* rho0 = sm.rho0[wib];
   const uint64_t total = prefix[nq];
   int64_t cur_q = -1;
-  int m = 0, bc = 31;
-  bool ok = false;
+  int m = 0;
   for (;;) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(task_counter, 1ull);
@@ -131,33 +230,42 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32)
     if (q != cur_q) {
       cur_q = q;
       m = jobs.m[job];
-      ok = m <= NMAX;
-      if (ok && m >= 2) ok = load_leaf(arena, jobs.off[job], m, jobs.nnz[job], NMAX, delta, rho0, lane, bc);
-      if (!ok && lane == 0) out.status[job] = PERM_EOVERFLOW;
+      if (m >= 2) {
+        if (PATH == P_F8 || PATH == P_F16)
+          load_blocked(arena, jobs.off[job], m, jobs.nnz[job], NMAX, delta, rho0, sm.colcnt[wib], lane);
+        else
+          load_plain(arena, jobs.off[job], m, jobs.nnz[job], NMAX, delta, rho0, lane);
+      }
     }
     uint64_t words[4] = {0, 0, 0, 0};
-    if (ok) {
-      if (m == 1) {
-        if (lane == 0) {
-          CsrView v = csr_view(arena, jobs.off[job], 1, jobs.nnz[job]);
-          int64_t a = jobs.nnz[job] ? v.val[0] : 0;
-          uint64_t s = a < 0 ? ~0ull : 0ull;
-          words[0] = (uint64_t)a;
-          words[1] = words[2] = words[3] = s;
-        }
+    if (m == 1) {
+      if (lane == 0) {
+        CsrView v = csr_view(arena, jobs.off[job], 1, jobs.nnz[job]);
+        const int64_t a = jobs.nnz[job] ? v.val[0] : 0;
+        const uint64_t s = a < 0 ? ~0ull : 0ull;
+        words[0] = (uint64_t)a;
+        words[1] = words[2] = words[3] = s;
+      }
+    } else if (m >= 2) {
+      int lanes, clog;
+      uint64_t tasks;
+      leaf_split(m, chunk_log2, lanes, clog, tasks);
+      const uint64_t cnt = 1ull << clog;
+      const uint64_t gb = (lt * 32 + lane) * cnt;
+      const uint64_t mycnt = lane < lanes ? cnt : 0;  // idle lanes of small jobs contribute zero
+      if (PATH == P_F8 && m >= 3) {
+        run_lane4<NMAX, 8, W>(delta, rho0, m, gb, mycnt, words);
+      } else if (PATH == P_F16 && m >= 3) {
+        if constexpr (NMAX >= 16) run_lane4<NMAX, 16, W>(delta, rho0, m, gb, mycnt, words);
       } else {
-        int lanes, clog;
-        uint64_t tasks;
-        leaf_split(m, chunk_log2, lanes, clog, tasks);
-        const uint64_t cnt = 1ull << clog;
-        const uint64_t gb = (lt * 32 + lane) * cnt;
-        // idle lanes (small jobs) run an empty range and contribute zero
-        const uint64_t mycnt = lane < lanes ? cnt : 0;
-        run_lane<NMAX, W>(bc, delta, rho0, m, gb, mycnt, words);
+        constexpr int BC = PATH == P_G15 ? 15 : (PATH == P_G31 ? 31 : 7);
+        typename WideT<W>::type s = ryser_lane<NMAX, W, BC>(delta, rho0, m, gb, mycnt);
+        s = warp_sum(s);
+        to_words(s, words);
       }
     }
     if (lane == 0) {
-      if (ok) atomic_add_words(out.acc + 4ll * job, words, 4);
+      atomic_add_words(out.acc + 4ll * job, words, 4);
       const uint64_t t1 = globaltimer_ns();
       unsigned long long prev = atomicMin(out.t_start + job, (unsigned long long)t0);
       if (prev == ~0ull) out.sm[job] = (int32_t)smid();
@@ -191,27 +299,64 @@ __global__ void k_leaf_finalize(const uint32_t* __restrict__ queue, int64_t nq, 
   atomic_add_words(mat_acc + 4ll * jobs.mat[job], v.w, 4);
 }
 
+__global__ void k_leaf_reject(const uint32_t* __restrict__ queue, int64_t nq, JobOut out) {
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q < nq) out.status[queue[q]] = PERM_EOVERFLOW;
+}
+
+template <int NMAX, int W, int PATH>
+cudaError_t launch_variant(const uint32_t* queue, int64_t nq, const uint64_t* prefix, const JobArrays& jobs,
+                           const uint64_t* arena, int chunk_log2, unsigned long long* task_counter,
+                           const JobOut& out, int num_sms, cudaStream_t stream) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_batch<NMAX, W, PATH>, LEAF_WARPS * 32, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+  }
+  k_leaf_batch<NMAX, W, PATH><<<num_sms * per_sm, LEAF_WARPS * 32, 0, stream>>>(queue, nq, prefix, jobs, arena,
+                                                                                chunk_log2, task_counter, out);
+  return cudaGetLastError();
+}
+
+#define LEAF_ARGS queue, nq, prefix, jobs, arena, chunk_log2, task_counter, out, num_sms, stream
 
 template <int NMAX, int W>
-cudaError_t launch_group(const uint32_t* queue, int64_t nq, const uint64_t* prefix, const JobArrays& jobs,
-                         const uint64_t* arena, int chunk_log2, unsigned long long* task_counter, const JobOut& out,
-                         int num_sms, cudaStream_t stream) {
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_batch<NMAX, W>, LEAF_WARPS * 32, 0);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  k_leaf_batch<NMAX, W><<<num_sms * per_sm, LEAF_WARPS * 32, 0, stream>>>(queue, nq, prefix, jobs, arena,
-                                                                          chunk_log2, task_counter, out);
-  return cudaGetLastError();
+cudaError_t launch_path(int path, const uint32_t* queue, int64_t nq, const uint64_t* prefix, const JobArrays& jobs,
+                        const uint64_t* arena, int chunk_log2, unsigned long long* task_counter, const JobOut& out,
+                        int num_sms, cudaStream_t stream) {
+  switch (path) {
+    case P_G7: return launch_variant<NMAX, W, P_G7>(LEAF_ARGS);
+    case P_G15: return launch_variant<NMAX, W, P_G15>(LEAF_ARGS);
+    case P_G31: return launch_variant<NMAX, W, P_G31>(LEAF_ARGS);
+    case P_F8: return launch_variant<NMAX, W, P_F8>(LEAF_ARGS);
+    case P_F16:
+      if constexpr (NMAX >= 16) return launch_variant<NMAX, W, P_F16>(LEAF_ARGS);
+      return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
-cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int nmax, int W, const JobArrays& jobs,
+cudaError_t launch_leaf_classify(const uint32_t* queue, int64_t nq, const JobArrays& jobs, const uint64_t* arena,
+                                 const int32_t* mat_w, int32_t* cls, cudaStream_t stream) {
+  if (nq <= 0) return cudaSuccess;
+  k_leaf_classify<<<(unsigned)((nq + 127) / 128), 128, 0, stream>>>(queue, nq, jobs, arena, mat_w, cls);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int cls, const JobArrays& jobs,
                               const uint64_t* arena, int chunk_log2, uint64_t* counts_scratch, uint64_t* prefix,
                               void* scan_tmp, size_t scan_tmp_bytes, unsigned long long* task_counter,
                               const JobOut& out, int num_sms, cudaStream_t stream) {
   if (nq <= 0) return cudaSuccess;
+  const int path = cls >> 8;
+  if (path == P_BAD) {
+    k_leaf_reject<<<(unsigned)((nq + 255) / 256), 256, 0, stream>>>(queue, nq, out);
+    return cudaGetLastError();
+  }
   const int tb = 256;
   k_leaf_task_counts<<<(unsigned)((nq + 1 + tb - 1) / tb), tb, 0, stream>>>(queue, nq, jobs.m, chunk_log2,
                                                                               counts_scratch);
@@ -219,12 +364,21 @@ cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int nmax, int W
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(task_counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
-#define LEAF_CASE(NM, WW) \
-  if (nmax == NM && W == WW) return launch_group<NM, WW>(queue, nq, prefix, jobs, arena, chunk_log2, task_counter, out, num_sms, stream);
-  LEAF_CASE(8, 2) LEAF_CASE(16, 2) LEAF_CASE(24, 2) LEAF_CASE(32, 2)
-  LEAF_CASE(8, 4) LEAF_CASE(16, 4) LEAF_CASE(24, 4) LEAF_CASE(32, 4)
-#undef LEAF_CASE
-  return cudaErrorInvalidValue;
+  const int nmi = cls & 3;
+  if ((cls & 4) == 0) {
+    switch (nmi) {
+      case 0: return launch_path<8, 2>(path, LEAF_ARGS);
+      case 1: return launch_path<16, 2>(path, LEAF_ARGS);
+      case 2: return launch_path<24, 2>(path, LEAF_ARGS);
+      default: return launch_path<32, 2>(path, LEAF_ARGS);
+    }
+  }
+  switch (nmi) {
+    case 0: return launch_path<8, 4>(path, LEAF_ARGS);
+    case 1: return launch_path<16, 4>(path, LEAF_ARGS);
+    case 2: return launch_path<24, 4>(path, LEAF_ARGS);
+    default: return launch_path<32, 4>(path, LEAF_ARGS);
+  }
 }
 
 cudaError_t launch_leaf_finalize(const uint32_t* queue, int64_t nq, const JobArrays& jobs, const JobOut& out,
