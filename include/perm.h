@@ -225,6 +225,36 @@ perm_status perm_mlp_predict(const float* params, const float* feats, int32_t co
 /* Attach model parameters (host, copied) to a plan for PERM_ORDER_LEARNED. */
 perm_status perm_mlp_attach(perm_plan_t* plan, const float* params);
 
+/* ---- allocation-free leaf batch -------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory while they run: code that is recording
+ * a CUDA graph (where cudaMalloc is not allowed), hosts whose own allocator
+ * must own every device allocation, and real-time loops that allocate only
+ * at start-up.  It evaluates count dense matrices of one order n by the
+ * leaf Ryser / Nijenhuis-Wilf kernel without allocating anything: no
+ * cudaMalloc, no cudaFree, no allocating library call.
+ *   a      device, count matrices of order n back to back, row-major int64
+ *          (n*n entries each), |a_ij| < 2^30 and every row |sum| < 2^31
+ *   n      1 <= n <= PERM_MAX_LEAF
+ *   count  1 <= count <= PERM_NOALLOC_MAX_COUNT, else PERM_EINVAL
+ *   out    device, count*4 words: per(A_k) in 256-bit two's complement
+ *   status device, count int32: PERM_OK, or PERM_EOVERFLOW (out set to 0)
+ *          when an entry or row sum is out of range or the bound
+ *          min(prod row |sums|, prod column |sums|) reaches 2^(254-n)
+ *   stream cudaStream_t; the call only enqueues work and returns.
+ * Working memory is one file-scope device array of PERM_NOALLOC_SCRATCH_BYTES
+ * that every GPU which loads the library keeps until the process exits.
+ * Every call uses that same array and clears it first, so calls whose work
+ * overlaps on the GPU (on different streams, or from different host threads
+ * at the same time) race and give wrong results; issue them one after
+ * another on one stream.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture begins. */
+#define PERM_NOALLOC_MAX_COUNT 4096
+#define PERM_NOALLOC_SCRATCH_BYTES (256 + 32 * PERM_NOALLOC_MAX_COUNT)
+perm_status perm_leaf_batch_noalloc(const int64_t* a, int32_t n, int32_t count, uint64_t* out,
+                                    int32_t* status, void* stream);
+
 /* ---- measurement -------------------------------------------------------------- */
 
 /* Integer multiply-add throughput probe: `blocks` x 256 threads each run

@@ -35,7 +35,7 @@ EXPORTED = [
     "perm_order", "perm_eval_batch", "perm_last_eval_ms", "perm_last_eval_launches", "perm_result", "perm_result_bits",
     "perm_result_words", "perm_jobs_export", "perm_exact", "perm_job_features", "perm_mlp_grad",
     "perm_mlp_train", "perm_mlp_predict", "perm_mlp_attach", "perm_ubench_imad",
-    "perm_status_string", "perm_last_error",
+    "perm_status_string", "perm_last_error", "perm_leaf_batch_noalloc",
 ]
 
 
@@ -112,6 +112,7 @@ def _lib():
         lib.perm_mlp_predict.argtypes = [f, f, ctypes.c_int32, vp, f]
         lib.perm_mlp_attach.argtypes = [vp, f]
         lib.perm_ubench_imad.argtypes = [ctypes.c_int32, ctypes.c_int32, vp, f, P(ctypes.c_double)]
+        lib.perm_leaf_batch_noalloc.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp]
         lib.perm_status_string.argtypes = [ctypes.c_int]
         lib.perm_status_string.restype = ctypes.c_char_p
         lib.perm_last_error.argtypes = []
@@ -438,3 +439,16 @@ def ubench_imad(blocks=152 * 8, iters=4096, stream=None):
     _ck(_lib().perm_ubench_imad(int(blocks), int(iters), _stream_handle(stream), ctypes.byref(ms),
                                 ctypes.byref(rate)), "perm_ubench_imad")
     return ms.value, rate.value
+
+
+def leaf_batch_noalloc(a_ptr, n, count, out_ptr, status_ptr, stream=None):
+    """Allocation-free leaf batch (perm_leaf_batch_noalloc): for callers that
+    cannot allocate device memory while they run, e.g. while recording a CUDA
+    graph.  All pointers are device addresses the caller owns: ``count``
+    row-major int64 n x n matrices, ``count * 4`` uint64 result words (256-bit
+    two's complement) and ``count`` int32 statuses.  The work is only
+    enqueued on the stream; calls whose work overlaps on the GPU race on the
+    library's one scratch array, so issue them in order on one stream."""
+    _ck(_lib().perm_leaf_batch_noalloc(ctypes.c_void_p(int(a_ptr)), int(n), int(count),
+                                       ctypes.c_void_p(int(out_ptr)), ctypes.c_void_p(int(status_ptr)),
+                                       ctypes.c_void_p(_stream_handle(stream))), "perm_leaf_batch_noalloc")
