@@ -242,6 +242,27 @@ def run_c60(pk, torch, args):
     return out
 
 
+C100_PRINTED = 149364113290700  # Table T12 total
+
+
+def run_c100(pk, torch, args):
+    """The paper's C100 adjacency: whole path, natural order, leaf order L."""
+    a = W.paper_adjacency("c100")
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    with pk.Plan([a], leaf_size=args.leaf_size, order="natural", timeout_ns=3600 * 10**9) as p:
+        nj = p.expand()
+        p.order("natural")
+        rec = p.evaluate(records=True)
+        val = p.result(0)
+        ev = p.last_eval_ms
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t
+    return {"per": str(val), "printed": str(C100_PRINTED), "equal": val == C100_PRINTED, "wall_s": wall,
+            "eval_ms": ev, "jobs": nj, "leaf_size": args.leaf_size,
+            "nodes": int(sum(r.nodes for r in rec)), "leaves": int(sum(r.leaves for r in rec))}
+
+
 def run_reference(args):
     """The oracle (plain CPU) on a bounded sample of the same workload."""
     import oracle
@@ -299,8 +320,25 @@ def main():
                     help="matrices in the leaf batch (smaller for profiler captures)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="skip the e2e, C60 and probe legs (profiler captures)")
+    ap.add_argument("--c60-only", action="store_true",
+                    help="run only the C60 whole-path leg and print its timings")
+    ap.add_argument("--c100", action="store_true",
+                    help="per(A) of the paper's C100 adjacency (Appendix) against its printed total")
+    ap.add_argument("--leaf-size", type=int, default=12)
     args = ap.parse_args()
     globals()["LEAF_COUNT"] = args.leaf_count
+    if args.c60_only:
+        import torch
+        import paper_1112_6072_gb300 as pk
+        torch.cuda.set_device(0)
+        print(json.dumps({"c60": run_c60(pk, torch, args)}))
+        return
+    if args.c100:
+        import torch
+        import paper_1112_6072_gb300 as pk
+        torch.cuda.set_device(0)
+        print(json.dumps({"c100": run_c100(pk, torch, args)}))
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":

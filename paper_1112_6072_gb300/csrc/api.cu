@@ -125,6 +125,55 @@ static void free_jobs(Mem& M, JobArrays& a) {
   memset(&a, 0, sizeof(a));
 }
 
+// A device buffer that only grows (by at least half its size), so a level
+// loop reuses it instead of allocating per level.
+struct Grow {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+static bool grow(Mem& M, Grow& g, size_t bytes) {
+  if (bytes <= g.cap && g.p) return true;
+  M.put(g.p);
+  const size_t nb = std::max(bytes, g.cap + g.cap / 2);
+  g.p = M.get(nb);
+  g.cap = g.p ? nb : 0;
+  return g.p != nullptr;
+}
+
+// Job header arrays with a capacity.
+struct JobBuf {
+  Grow m, nnz, off, mat, dl, coef;
+  bool ensure(Mem& M, int64_t n) {
+    const size_t k = (size_t)std::max<int64_t>(n, 1);
+    return grow(M, m, 4 * k) && grow(M, nnz, 4 * k) && grow(M, off, 8 * k) && grow(M, mat, 4 * k) &&
+           grow(M, dl, 4 * k) && grow(M, coef, 32 * k);
+  }
+  JobArrays view() const {
+    JobArrays a;
+    a.m = reinterpret_cast<int32_t*>(m.p);
+    a.nnz = reinterpret_cast<int32_t*>(nnz.p);
+    a.off = reinterpret_cast<int64_t*>(off.p);
+    a.mat = reinterpret_cast<int32_t*>(mat.p);
+    a.depth_left = reinterpret_cast<int32_t*>(dl.p);
+    a.coef = reinterpret_cast<uint64_t*>(coef.p);
+    return a;
+  }
+  void free(Mem& M) {
+    for (Grow* g : {&m, &nnz, &off, &mat, &dl, &coef}) {
+      M.put(g->p);
+      g->p = nullptr;
+      g->cap = 0;
+    }
+  }
+  void release_ownership() {
+    for (Grow* g : {&m, &nnz, &off, &mat, &dl, &coef}) {
+      g->p = nullptr;
+      g->cap = 0;
+    }
+  }
+};
+
 // ---------------------------------------------------------------- handles
 struct perm_jobs {
   perm_plan* plan = nullptr;
@@ -391,12 +440,17 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
   perm_jobs* J = new perm_jobs();
   J->plan = P;
   P->jobs = J;
-  JobArrays cur{};
-  uint64_t* cur_arena = nullptr;
+  // ping-pong job arrays and arenas, grown geometrically and reused across levels
+  JobBuf jb[2];
+  Grow ar[2], g_words, g_base, g_valid, g_pos, g_tmp;
+  JobBuf slots;
+  int cb = 0;  // index of the current level's buffers
   int64_t ncur = nroots;
-  if (!alloc_jobs(M, cur, std::max<int64_t>(nroots, 1))) return PERM_ENOMEM;
-  cur_arena = dget<uint64_t>(M, std::max<int64_t>((int64_t)P->h_arena.size(), 2));
-  if (!cur_arena) return PERM_ENOMEM;
+  if (!jb[0].ensure(M, std::max<int64_t>(nroots, 1)) ||
+      !grow(M, ar[0], 8 * (size_t)std::max<int64_t>((int64_t)P->h_arena.size(), 2)))
+    return PERM_ENOMEM;
+  JobArrays cur = jb[0].view();
+  uint64_t* cur_arena = reinterpret_cast<uint64_t*>(ar[0].p);
   if (nroots > 0) {
     std::vector<uint64_t> coef(4 * nroots, 0ull);
     for (int64_t r = 0; r < nroots; ++r) coef[4 * r] = 1;
@@ -408,84 +462,80 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
     CK(cudaMemcpyAsync(cur.depth_left, rdl.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(cur.coef, coef.data(), 32 * nroots, cudaMemcpyHostToDevice, s));
   }
-  int32_t* d_err = dget<int32_t>(M, 2);  // [0] first error status, [1] largest order of a level
-  if (!d_err) return PERM_ENOMEM;
-  CK(cudaMemsetAsync(d_err, 0, 8, s));
+  // stat[0]: first error status (int32 in the low half), [1]: largest kept
+  // order, [2]: words of the kept blocks, [3]: kept jobs
+  long long* d_stat = dget<long long>(M, 4);
+  if (!d_stat) return PERM_ENOMEM;
+  CK(cudaMemsetAsync(d_stat, 0, 32, s));
   int max_order = maxn;
-  int64_t cur_arena_words = (int64_t)P->h_arena.size();
+  int64_t cur_arena_words = (int64_t)P->h_arena.size();  // roots sit back to back
+  int64_t used_words = cur_arena_words;                    // words of the current jobs' blocks
   for (int level = 0; level < maxd && ncur > 0; ++level) {
     if (adaptive) {
       const bool big = max_order > PERM_MAX_JOB_N;
       const bool want_more = ncur < kTargetJobs * std::max<int64_t>(1, nroots) && max_order > P->L;
       if (!big && !want_more) break;
     }
-    // child capacity and offsets
-    int64_t* words = dget<int64_t>(M, ncur);
-    int64_t* base = dget<int64_t>(M, ncur);
-    size_t tb = scan_tmp_bytes_i64(ncur);
-    void* tmp = M.get(tb);
-    if (!words || !base || !tmp) return PERM_ENOMEM;
+    // every parent reserves two child slots of its own block size
+    const int64_t out_words = 2 * used_words;
+    const int nb = cb ^ 1;
+    const size_t tb = std::max(scan_tmp_bytes_i64(ncur), scan_tmp_bytes_i32(2 * ncur));
+    if (!grow(M, g_words, 8 * (size_t)ncur) || !grow(M, g_base, 8 * (size_t)ncur) ||
+        !grow(M, g_valid, 8 * (size_t)ncur) || !grow(M, g_pos, 8 * (size_t)ncur) || !grow(M, g_tmp, tb) ||
+        !grow(M, ar[nb], 8 * (size_t)std::max<int64_t>(out_words, 2)) || !slots.ensure(M, 2 * ncur))
+      return PERM_ENOMEM;
+    int64_t* words = reinterpret_cast<int64_t*>(g_words.p);
+    int64_t* base = reinterpret_cast<int64_t*>(g_base.p);
+    int32_t* valid = reinterpret_cast<int32_t*>(g_valid.p);
+    int32_t* pos = reinterpret_cast<int32_t*>(g_pos.p);
+    uint64_t* next_arena = reinterpret_cast<uint64_t*>(ar[nb].p);
     CK(launch_child_capacity(cur, ncur, words, s));
-    CK(scan_exclusive_i64(words, base, ncur, tmp, tb, s));
-    int64_t last_w = 0, last_b = 0;
-    CK(cudaMemcpyAsync(&last_w, words + ncur - 1, 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&last_b, base + ncur - 1, 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    const int64_t out_words = last_w + last_b;
-    uint64_t* next_arena = dget<uint64_t>(M, std::max<int64_t>(out_words, 2));
-    JobArrays slots{};
-    int32_t* valid = dget<int32_t>(M, 2 * ncur);
-    int32_t* pos = dget<int32_t>(M, 2 * ncur);
-    if (!next_arena || !valid || !pos || !alloc_jobs(M, slots, 2 * ncur)) return PERM_ENOMEM;
+    CK(scan_exclusive_i64(words, base, ncur, g_tmp.p, g_tmp.cap, s));
     ExpandLevelArgs A;
     A.parent = cur;
     A.arena_in = cur_arena;
     A.np = ncur;
-    A.child = slots;
+    A.child = slots.view();
     A.arena_out = next_arena;
     A.child_off_base = base;
     A.valid = valid;
     A.leaf_size = P->L;
-    A.err = d_err;
+    A.err = reinterpret_cast<int32_t*>(d_stat);
     CK(launch_expand_level(A, max_order, s));
-    size_t tb2 = scan_tmp_bytes_i32(2 * ncur);
-    void* tmp2 = M.get(tb2);
-    if (!tmp2) return PERM_ENOMEM;
-    CK(scan_exclusive_i32(valid, pos, 2 * ncur, tmp2, tb2, s));
-    int32_t lv = 0, lp = 0, herr = 0;
-    CK(cudaMemcpyAsync(&lv, valid + 2 * ncur - 1, 4, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&lp, pos + 2 * ncur - 1, 4, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&herr, d_err, 4, cudaMemcpyDeviceToHost, s));
+    CK(scan_exclusive_i32(valid, pos, 2 * ncur, g_tmp.p, g_tmp.cap, s));
+    // the kept children: at most 2 * ncur; size the next arrays for that bound
+    if (!jb[nb].ensure(M, 2 * ncur)) return PERM_ENOMEM;
+    CK(cudaMemsetAsync(d_stat + 1, 0, 24, s));
+    CK(launch_compact_jobs(slots.view(), valid, pos, 2 * ncur, jb[nb].view(), d_stat + 1, s));
+    long long st[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(st, d_stat, 32, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    const int32_t herr = (int32_t)(st[0] & 0xffffffff);
     if (herr != 0) return (perm_status)herr;
-    const int64_t nnext = (int64_t)lv + lp;
-    JobArrays next{};
-    if (!alloc_jobs(M, next, std::max<int64_t>(nnext, 1))) return PERM_ENOMEM;
-    CK(cudaMemsetAsync(d_err + 1, 0, 4, s));
-    CK(launch_compact_jobs(slots, valid, pos, 2 * ncur, next, d_err + 1, s));
-    int32_t new_max = 0;
-    CK(cudaMemcpyAsync(&new_max, d_err + 1, 4, cudaMemcpyDeviceToHost, s));
-    free_jobs(M, slots);
-    free_jobs(M, cur);
-    M.put(cur_arena);
-    M.put(words);
-    M.put(base);
-    M.put(tmp);
-    M.put(tmp2);
-    M.put(valid);
-    M.put(pos);
-    cur = next;
+    cb = nb;
+    cur = jb[cb].view();
     cur_arena = next_arena;
     cur_arena_words = out_words;
-    CK(cudaStreamSynchronize(s));
-    ncur = nnext;
-    max_order = new_max;  // carried jobs keep their order
+    ncur = st[3];
+    max_order = (int)st[1];  // carried jobs keep their order
+    used_words = st[2];
   }
-  M.put(d_err);
+  M.put(d_stat);
+  // the current buffers become the job set; the rest is released
   J->n = ncur;
-  J->a = cur;
+  J->a = jb[cb].view();
   J->arena = cur_arena;
   J->arena_words = cur_arena_words;
+  jb[cb].release_ownership();
+  ar[cb].p = nullptr;
+  jb[cb ^ 1].free(M);
+  M.put(ar[cb ^ 1].p);
+  slots.free(M);
+  M.put(g_words.p);
+  M.put(g_base.p);
+  M.put(g_valid.p);
+  M.put(g_pos.p);
+  M.put(g_tmp.p);
   J->h_m.resize(ncur);
   J->h_mat.resize(ncur);
   if (ncur > 0) {
@@ -519,7 +569,11 @@ extern "C" perm_status perm_estimate(perm_jobs_t* J, float* log_ap) {
   if (!J) return PERM_EINVAL;
   perm_plan* P = J->plan;
   if (J->max_order > PERM_MAX_JOB_N) return PERM_EINVAL;
-  CK(launch_kklll(J->a, J->n, J->arena, P->opts.kklll_trials, P->opts.seed, J->d_logap, J->max_order, P->s));
+  void* scratch = P->M.get(kklll_scratch_bytes(J->n, J->max_order, P->opts.kklll_trials));
+  if (!scratch) return PERM_ENOMEM;
+  CK(launch_kklll(J->a, J->n, J->arena, P->opts.kklll_trials, P->opts.seed, J->d_logap, J->max_order, scratch,
+                  P->s));
+  P->M.put(scratch);
   J->has_logap = true;
   if (log_ap && J->n > 0) {
     CK(cudaMemcpyAsync(log_ap, J->d_logap, 4 * J->n, cudaMemcpyDeviceToHost, P->s));
@@ -651,6 +705,15 @@ extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, pe
     }
   }
   if (dfs_max > PERM_MAX_JOB_N) return PERM_EINVAL;
+  // depth-first queue grouped by ring width, queue order kept inside each group
+  int64_t nd_w2 = 0;
+  {
+    std::vector<uint32_t> g2, g4;
+    for (uint32_t j : dfsq) (P->w[J->h_mat[j]] == 4 ? g4 : g2).push_back(j);
+    nd_w2 = (int64_t)g2.size();
+    g2.insert(g2.end(), g4.begin(), g4.end());
+    dfsq.swap(g2);
+  }
   const int64_t nl = (int64_t)leafq.size(), nd = (int64_t)dfsq.size();
   uint32_t* d_lq = dget<uint32_t>(M, nl);
   uint32_t* d_dq = dget<uint32_t>(M, nd);
@@ -660,9 +723,14 @@ extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, pe
   void* stmp = M.get(stb);
   unsigned long long* ctr = dget<unsigned long long>(M, 2);
   const int tile = dfs_max <= 32 ? 32 : 64;
-  const int wps = P->opts.workers_per_sm > 0 ? P->opts.workers_per_sm : (tile <= 32 ? 16 : 4);
-  const int dfs_warps = P->sms * ((wps + dfs_warps_per_block(tile) - 1) / dfs_warps_per_block(tile)) *
-                        dfs_warps_per_block(tile);
+  // the narrow variant (int32 tile, leaves <= 16 rows) unless the leaf order needs the wide one
+  const bool wide_first = P->L > 16;
+  const int wps = P->opts.workers_per_sm > 0 ? P->opts.workers_per_sm : (tile <= 32 ? 24 : 10);
+  int dfs_warps = 0;
+  for (bool w : {false, true}) {
+    const int wpb = dfs_warps_per_block(tile, w);
+    dfs_warps = std::max(dfs_warps, P->sms * ((wps + wpb - 1) / wpb) * wpb);
+  }
   const int64_t undo_w = dfs_undo_words(tile);
   int64_t* undo = nd > 0 ? dget<int64_t>(M, undo_w * dfs_warps) : nullptr;
   if (!d_lq || !d_dq || !counts || !prefix || !stmp || !ctr || (nd > 0 && !undo)) return PERM_ENOMEM;
@@ -706,8 +774,8 @@ extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, pe
   CK(cudaMemsetAsync(ctr, 0, 16, s));
   const int chunk = P->opts.chunk_log2 > 0 ? P->opts.chunk_log2 : 10;
   CK(cudaEventRecord(P->ev0, s));
+  DfsArgs D{};
   if (nd > 0) {
-    DfsArgs D;
     D.queue = d_dq;
     D.nq = nd;
     D.jobs = J->a;
@@ -720,7 +788,13 @@ extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, pe
     D.undo = undo;
     D.undo_words_per_warp = undo_w;
     D.timeout_ns = P->opts.timeout_ns > 0 ? P->opts.timeout_ns : 10000000000ll;
-    CK(launch_dfs(D, tile, P->sms, wps, s));
+    // ring width 2 then 4; each launch has its own job counter
+    D.nq = nd_w2;
+    CK(launch_dfs(D, tile, wide_first, 2, P->sms, wps, s));
+    D.queue = d_dq + nd_w2;
+    D.nq = nd - nd_w2;
+    D.job_counter = ctr;
+    CK(launch_dfs(D, tile, wide_first, 4, P->sms, wps, s));
   }
   if (nl > 0) {
     // one persistent grid per kernel variant, queue order kept inside each variant
@@ -737,6 +811,38 @@ extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, pe
   CK(cudaEventElapsedTime(&P->last_ms, P->ev0, P->ev1));
   std::vector<int32_t> st(n);
   if (n) CK(cudaMemcpyAsync(st.data(), J->out.status, 4 * n, cudaMemcpyDeviceToHost, s));
+  if (nd > 0 && !wide_first) {
+    // jobs the narrow depth-first variant could not hold run again on the wide one
+    CK(cudaStreamSynchronize(s));
+    std::vector<uint32_t> retry;
+    int64_t nr2 = 0;
+    for (int64_t k = 0; k < nd; ++k)
+      if (st[dfsq[k]] == DFS_RETRY) {
+        retry.push_back(dfsq[k]);
+        if (k < nd_w2) ++nr2;
+      }
+    if (!retry.empty()) {
+      const int64_t nr = (int64_t)retry.size();
+      CK(cudaMemcpyAsync(d_dq, retry.data(), 4 * nr, cudaMemcpyHostToDevice, s));
+      CK(cudaMemsetAsync(ctr, 0, 16, s));
+      float ms2 = 0.f;
+      CK(cudaEventRecord(P->ev0, s));
+      D.queue = d_dq;
+      D.nq = nr2;
+      D.job_counter = ctr + 1;
+      CK(launch_dfs(D, tile, true, 2, P->sms, wps, s));
+      D.queue = d_dq + nr2;
+      D.nq = nr - nr2;
+      D.job_counter = ctr;
+      CK(launch_dfs(D, tile, true, 4, P->sms, wps, s));
+      CK(cudaEventRecord(P->ev1, s));
+      CK(cudaEventSynchronize(P->ev1));
+      CK(cudaEventElapsedTime(&ms2, P->ev0, P->ev1));
+      P->last_ms += ms2;
+      P->last_launches += 1;
+      CK(cudaMemcpyAsync(st.data(), J->out.status, 4 * n, cudaMemcpyDeviceToHost, s));
+    }
+  }
   if (results && n) {
     std::vector<unsigned long long> acc(4 * n), t0(n), t1(n), lv(n), nd_(n);
     std::vector<int32_t> sm(n), mat(n), nnz(n);

@@ -2,32 +2,41 @@
 // one atomic counter (Algorithm PH, Step 3: the next job goes to the next
 // free worker) and evaluate each by Algorithm H_per (Section 2.1): Eq. 2
 // depth first while the order exceeds max(L, 2) and s < 5, Ryser /
-// Nijenhuis-Wilf (ryser.cuh) at the leaves.
+// Nijenhuis-Wilf (ryser.cuh, ryser4.cuh) at the leaves.
 //
-// The job lives in a dense int64 tile in shared memory.  Lines are never
-// moved: deleting a row or column clears a bit of the active masks R and C,
-// so "lowest index" keeps the meaning it has in the compacted matrices of
-// the oracle.  A merge overwrites one line in place after saving it to the
+// The job lives in a dense tile in shared memory.  Lines are never moved:
+// deleting a row or column clears a bit of the active masks R and C, so
+// "lowest index" keeps the meaning it has in the compacted matrices of the
+// oracle.  A merge overwrites one line in place after saving it to the
 // warp's undo stack in global memory; backtracking restores it.  Nonzero
-// patterns are kept as bit masks per row (rowbits) and per column (colbits),
-// so a line count is one popcount against the active masks.
+// patterns are kept as bit masks per row (rowbits) and per column
+// (colbits), so a line count is one popcount against the active masks.
+//
+// Variants: tile entries int32 (more warps per SM) or int64, and leaves of
+// up to 16 or up to 32 rows.  A job that the narrow variant cannot hold (an
+// entry leaving int32, a leaf above 16 rows) reports DFS_RETRY and the host
+// runs it again on the int64 / 32-row variant.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "internal.h"
 #include "ryser.cuh"
+#include "ryser4.cuh"
 #include "wide.cuh"
 
 namespace {
 
-template <int TILE>
+template <int TILE, typename E>
 struct DfsCfg {
   static constexpr int STRIDE = TILE + 1;
-  static constexpr int WARPS = TILE <= 32 ? 8 : 4;
-  static constexpr size_t TILE_BYTES = sizeof(int64_t) * TILE * STRIDE;
+  static constexpr int WARPS = sizeof(E) == 4 ? (TILE <= 32 ? 8 : 5) : (TILE <= 32 ? 8 : 4);
+  // blocks per SM the register budget is sized for (shared memory allows this many)
+  static constexpr int MINB = (sizeof(E) == 4 && TILE <= 32) ? 2 : 1;
+  static constexpr size_t TILE_BYTES = (sizeof(E) * TILE * STRIDE + 15) / 16 * 16;
   static constexpr size_t MASK_BYTES = 2 * sizeof(uint64_t) * TILE;
-  static constexpr size_t LEAF_BYTES = sizeof(int32_t) * ((PERM_MAX_LEAF - 1) * 32 + 32);
+  // delta, rho0, column masks of the leaf
+  static constexpr size_t LEAF_BYTES = sizeof(int32_t) * ((PERM_MAX_LEAF - 1) * 32 + 32 + 32);
   static constexpr size_t WARP_BYTES = TILE_BYTES + MASK_BYTES + LEAF_BYTES;
   static constexpr size_t SMEM = WARPS * WARP_BYTES;
   // undo stack words per level: meta (8 x int32 = 4 words), pv[4], coef[4], saved mask, line[TILE]
@@ -49,9 +58,11 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
   return v;
 }
 
-__device__ __forceinline__ bool mad2_checked(int64_t a, int64_t x, int64_t b, int64_t y, int64_t& out) {
-  __int128 r = (__int128)a * x + (__int128)b * y;
-  out = (int64_t)r;
+// a*x + b*y, false when the result leaves E
+template <typename E>
+__device__ __forceinline__ bool mad2_checked(int64_t a, int64_t x, int64_t b, int64_t y, E& out) {
+  const __int128 r = (__int128)a * x + (__int128)b * y;
+  out = (E)r;
   return r == (__int128)out;
 }
 
@@ -65,21 +76,49 @@ __device__ __forceinline__ int nth_bit(uint64_t mask, int n) {
 
 __device__ __forceinline__ uint64_t bit64(int i) { return 1ull << i; }
 
-template <int TILE>
+// Lane shares of one leaf, summed over the warp into lane 0's words.
+template <int LN, int W>
+__device__ __forceinline__ void leaf_dispatch(int nmax, int path, const int32_t* delta, const int32_t* rho0,
+                                              int m, uint64_t gb, uint64_t cnt, uint64_t* words) {
+  // path: 0/1/2 plain walk with bit class 7/15/31, 3 blocked NN=8, 4 blocked NN=16
+#define DFS_PLAIN(NM, WW)                                                                  \
+  do {                                                                                     \
+    typename WideT<WW>::type s_;                                                           \
+    if (path == 0) s_ = ryser_lane<NM, WW, 7>(delta, rho0, m, gb, cnt);                    \
+    else if (path == 1) s_ = ryser_lane<NM, WW, 15>(delta, rho0, m, gb, cnt);              \
+    else s_ = ryser_lane<NM, WW, 31>(delta, rho0, m, gb, cnt);                             \
+    s_ = warp_sum(s_);                                                                     \
+    to_words(s_, words);                                                                   \
+  } while (0)
+#define DFS_CASE(NM, WW)                                                                   \
+  if (path == 3) run_lane4<NM, 8, WW>(delta, rho0, m, gb, cnt, words);                      \
+  else if (path == 4) { if constexpr (NM >= 16) run_lane4<NM, 16, WW>(delta, rho0, m, gb, cnt, words); } \
+  else DFS_PLAIN(NM, WW);
+  if (nmax == 8) { DFS_CASE(8, W) }
+  else if (nmax == 16) { DFS_CASE(16, W) }
+  else if constexpr (LN >= 32) {
+    if (nmax == 24) { DFS_CASE(24, W) } else { DFS_CASE(32, W) }
+  }
+#undef DFS_CASE
+#undef DFS_PLAIN
+}
+
+template <int TILE, typename E, int LN, int W>
 struct Dfs {
-  static constexpr int S = DfsCfg<TILE>::STRIDE;
+  static constexpr int S = DfsCfg<TILE, E>::STRIDE;
   static constexpr int RPL = TILE / 32;  // lines per lane
-  int64_t* T;
+  E* T;
   uint64_t* rowbits;
   uint64_t* colbits;
   int32_t* delta;
   int32_t* rho0;
+  uint32_t* cmask;
   int64_t* undo;
   int lane;
   uint64_t R, C;
   u256 coef;
 
-  __device__ int64_t* frame_words(int lv) { return undo + (int64_t)lv * DfsCfg<TILE>::FRAME_WORDS; }
+  __device__ int64_t* frame_words(int lv) { return undo + (int64_t)lv * DfsCfg<TILE, E>::FRAME_WORDS; }
 
   __device__ void store_frame(int lv, const Frame& f, const int64_t* pv, const u256& c) {
     int64_t* w = frame_words(lv);
@@ -121,7 +160,7 @@ struct Dfs {
   }
   __device__ static int nchildren(int k) { return (k == 3 || k == 4) ? 2 : 1; }
 
-  // Apply child c; returns false on int64 overflow of a merged entry.
+  // Apply child c; returns false when a merged entry leaves E.
   __device__ bool apply(int lv, const Frame& f, const int64_t* pv, int c) {
     int kind, x;
     child_kind(f.k, c, kind, x);
@@ -145,9 +184,9 @@ struct Dfs {
         const int r = lane + 32 * t;
         bool nz = false;
         if ((R >> r) & 1) {
-          const int64_t old = T[r * S + p];
-          int64_t nv;
-          if (!mad2_checked(a, T[r * S + q], b, old, nv)) ok = false;
+          const E old = T[r * S + p];
+          E nv;
+          if (!mad2_checked<E>(a, T[r * S + q], b, old, nv)) ok = false;
           saved[r] = old;
           T[r * S + p] = nv;
           nz = nv != 0;
@@ -178,9 +217,9 @@ struct Dfs {
         const int cc = lane + 32 * t;
         bool nz = false;
         if ((C >> cc) & 1) {
-          const int64_t old = T[p * S + cc];
-          int64_t nv;
-          if (!mad2_checked(a, T[q * S + cc], b, old, nv)) ok = false;
+          const E old = T[p * S + cc];
+          E nv;
+          if (!mad2_checked<E>(a, T[q * S + cc], b, old, nv)) ok = false;
           saved[cc] = old;
           T[p * S + cc] = nv;
           nz = nv != 0;
@@ -198,7 +237,7 @@ struct Dfs {
     return __all_sync(0xffffffffu, ok);
   }
 
-  __device__ void undo_child(int lv, const Frame& f, const int64_t* pv, const u256& pcoef, int c) {
+  __device__ void undo_child(int lv, const Frame& f, const u256& pcoef, int c) {
     int kind, x;
     child_kind(f.k, c, kind, x);
     const int64_t* saved = frame_words(lv) + 13;
@@ -216,7 +255,7 @@ struct Dfs {
       for (int t = 0; t < RPL; ++t) {
         const int r = lane + 32 * t;
         if (r != i && ((R >> r) & 1)) {
-          const int64_t old = saved[r];
+          const E old = (E)saved[r];
           T[r * S + p] = old;
           if (old != 0) rowbits[r] |= bit64(p); else rowbits[r] &= ~bit64(p);
         }
@@ -235,7 +274,7 @@ struct Dfs {
       for (int t = 0; t < RPL; ++t) {
         const int cc = lane + 32 * t;
         if (cc != j && ((C >> cc) & 1)) {
-          const int64_t old = saved[cc];
+          const E old = (E)saved[cc];
           T[p * S + cc] = old;
           if (old != 0) colbits[cc] |= bit64(p); else colbits[cc] &= ~bit64(p);
         }
@@ -259,56 +298,122 @@ struct Dfs {
   }
 
   // Ryser on the active sub-matrix; adds coef * per into acc (lane 0).
-  __device__ bool leaf(int W, u256& acc) {
+  // Returns a status: 0, PERM_EOVERFLOW, PERM_EINVAL, or DFS_RETRY.
+  __device__ int leaf(u256& acc) {
     const int m = __popcll(R);
-    const int nmax = nmax_for(m);
-    bool ok = true;
     if (m == 1) {
       const int r = __ffsll((long long)R) - 1, c = __ffsll((long long)C) - 1;
-      if (lane == 0) acc = u256_add(acc, u256_mul_s64(coef, T[r * S + c]));
-      return true;
+      if (lane == 0) acc = u256_add(acc, u256_mul_s64(coef, (int64_t)T[r * S + c]));
+      return 0;
     }
-    if (m > PERM_MAX_LEAF) return false;
+    if (m > PERM_MAX_LEAF) return PERM_EINVAL;
+    if (m > LN) return DFS_RETRY;
+    const int nmax = nmax_for(m);
+    // row ranges, and per leaf column the leaf rows holding a nonzero
+    int64_t rmax = 0;
+    bool ok = true;
+    int myrow = lane < m ? nth_bit(R, lane) : 0;
+    int mycol = lane < m ? nth_bit(C, lane) : 0;
+    if (lane < m) {
+      int64_t ra = 0;
+      uint64_t cm = C;
+      while (cm) {
+        const int c = __ffsll((long long)cm) - 1;
+        cm &= cm - 1;
+        const int64_t a = (int64_t)T[myrow * S + c];
+        if (a >= (1ll << 30) || a <= -(1ll << 30)) ok = false;
+        ra += a < 0 ? -a : a;
+      }
+      if (ra >= (1ll << 31)) ok = false;
+      rmax = ra;
+      uint32_t msk = 0;
+      uint64_t rm = R;
+      int ii = 0;
+      while (rm) {
+        const int r = __ffsll((long long)rm) - 1;
+        rm &= rm - 1;
+        if (T[r * S + mycol] != 0) msk |= 1u << ii;
+        ++ii;
+      }
+      cmask[lane] = msk;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      const int64_t o = __shfl_xor_sync(0xffffffffu, rmax, d);
+      rmax = o > rmax ? o : rmax;
+    }
+    __syncwarp();
+    if (!ok) return PERM_EOVERFLOW;
+    const int bc = bit_class(rmax);
+    int path = bc == 7 ? 0 : (bc == 15 ? 1 : 2);
+    int ca = 0, cb = 1, clast = m - 1;
+    if (bc == 7 && m >= 3) {
+      // the leaf-column pair touching the fewest leaf rows, lowest pair on ties
+      unsigned key = 0xffffffffu;
+      if (lane < m) {
+        const uint32_t ma = cmask[lane];
+        for (int b = lane + 1; b < m; ++b) {
+          const unsigned kk = ((unsigned)__popc(ma | cmask[b]) << 16) | ((unsigned)lane << 8) | (unsigned)b;
+          key = kk < key ? kk : key;
+        }
+      }
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) key = min(key, __shfl_xor_sync(0xffffffffu, key, d));
+      const int k = (int)(key >> 16);
+      if (k <= 8 || (k <= 16 && nmax >= 16)) {
+        path = k <= 8 ? 3 : 4;
+        ca = (int)((key >> 8) & 0xff);
+        cb = (int)(key & 0xff);
+        while (clast == ca || clast == cb) --clast;
+      }
+    }
+    // fill delta / rho0 (leaf columns jj, leaf rows ii)
     const int cols = m - 1;
     for (int k = lane; k < cols * nmax; k += 32) delta[k] = 0;
     __syncwarp();
-    int64_t rmax = 0;
-    for (int ii = lane; ii < nmax; ii += 32) {
-      if (ii >= m) {
-        rho0[ii] = 1;
-        continue;
-      }
-      const int r = nth_bit(R, ii);
-      int64_t rs = 0, ra = 0, last = 0;
+    int slot = lane;
+    if (path >= 3) {
+      const uint32_t touched_mask = cmask[ca] | cmask[cb];
+      const bool touched = lane < m && ((touched_mask >> lane) & 1);
+      const uint32_t below = (1u << lane) - 1u;
+      const int kk = __popc(touched_mask);
+      const uint32_t valid = m >= 32 ? 0xffffffffu : ((1u << m) - 1u);
+      slot = touched ? __popc(touched_mask & below) : kk + __popc(~touched_mask & valid & below);
+    }
+    if (lane < m) {
+      int64_t rs = 0, last = 0;
       uint64_t cm = C;
       int jj = 0;
       while (cm) {
         const int c = __ffsll((long long)cm) - 1;
         cm &= cm - 1;
-        const int64_t a = T[r * S + c];
-        if (a >= (1ll << 30) || a <= -(1ll << 30)) ok = false;
+        const int64_t a = (int64_t)T[myrow * S + c];
         rs += a;
-        ra += a < 0 ? -a : a;
-        if (jj < cols) delta[jj * nmax + ii] = (int32_t)(2 * a); else last = a;
+        int gj;
+        if (path >= 3)
+          gj = jj == ca ? 0 : (jj == cb ? 1 : (jj == clast ? -1 : 2 + jj - (ca < jj) - (cb < jj) - (clast < jj)));
+        else
+          gj = jj < cols ? jj : -1;
+        if (gj >= 0) delta[gj * nmax + slot] = (int32_t)(2 * a); else last = a;
         ++jj;
       }
-      if (ra >= (1ll << 31)) ok = false;
-      rmax = ra > rmax ? ra : rmax;
-      rho0[ii] = (int32_t)(2 * last - rs);
+      rho0[slot] = (int32_t)(2 * last - rs);
     }
-    ok = __all_sync(0xffffffffu, ok);
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      int64_t o = __shfl_xor_sync(0xffffffffu, rmax, d);
-      rmax = o > rmax ? o : rmax;
-    }
+    for (int i = m + lane; i < nmax; i += 32) rho0[i] = 1;
     __syncwarp();
-    if (!ok) return false;
-    const int bc = bit_class(rmax);
     const int e = m - 1;
     int lanes;
     uint64_t cnt;
-    if (e <= 5) {
+    if (path >= 3) {
+      if (e <= 6) {
+        lanes = 1 << (e - 2);
+        cnt = 4;
+      } else {
+        lanes = 32;
+        cnt = 1ull << (e - 5);
+      }
+    } else if (e <= 5) {
       lanes = 1 << (e - 1);
       cnt = 2;
     } else {
@@ -317,7 +422,7 @@ struct Dfs {
     }
     uint64_t words[4] = {0, 0, 0, 0};
     const uint64_t gb = (uint64_t)lane * cnt;
-    dispatch_lane(nmax, W, bc, delta, rho0, m, gb, lane < lanes ? cnt : 0, words);
+    leaf_dispatch<LN, W>(nmax, path, delta, rho0, m, gb, lane < lanes ? cnt : 0, words);
     if (lane == 0) {
       u256 s;
       for (int k = 0; k < 4; ++k) s.w[k] = words[k];
@@ -326,24 +431,25 @@ struct Dfs {
       acc = u256_add(acc, u256_mul(s, coef));
     }
     __syncwarp();
-    return true;
+    return 0;
   }
 };
 
-template <int TILE>
-__global__ void __launch_bounds__(DfsCfg<TILE>::WARPS * 32) k_dfs(DfsArgs A) {
+template <int TILE, typename E, int LN, int W>
+__global__ void __launch_bounds__(DfsCfg<TILE, E>::WARPS * 32, DfsCfg<TILE, E>::MINB) k_dfs(DfsArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  typedef DfsCfg<TILE> Cfg;
+  typedef DfsCfg<TILE, E> Cfg;
   constexpr int S = Cfg::STRIDE;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   unsigned char* base = smem_raw + (size_t)wib * Cfg::WARP_BYTES;
-  Dfs<TILE> D;
-  D.T = reinterpret_cast<int64_t*>(base);
+  Dfs<TILE, E, LN, W> D;
+  D.T = reinterpret_cast<E*>(base);
   D.rowbits = reinterpret_cast<uint64_t*>(base + Cfg::TILE_BYTES);
   D.colbits = D.rowbits + TILE;
   D.delta = reinterpret_cast<int32_t*>(base + Cfg::TILE_BYTES + Cfg::MASK_BYTES);
   D.rho0 = D.delta + (PERM_MAX_LEAF - 1) * 32;
+  D.cmask = reinterpret_cast<uint32_t*>(D.rho0 + 32);
   const int64_t gwarp = (int64_t)blockIdx.x * Cfg::WARPS + wib;
   D.undo = A.undo + gwarp * A.undo_words_per_warp;
   D.lane = lane;
@@ -358,7 +464,6 @@ __global__ void __launch_bounds__(DfsCfg<TILE>::WARPS * 32) k_dfs(DfsArgs A) {
     const uint64_t t0 = globaltimer_ns();
     const int m = A.jobs.m[job];
     const int nnz = A.jobs.nnz[job];
-    const int W = A.mat_w[A.jobs.mat[job]];
     int status = 0;
     u256 acc = u256_zero();
     unsigned long long nodes = 0, leaves = 0;
@@ -370,21 +475,26 @@ __global__ void __launch_bounds__(DfsCfg<TILE>::WARPS * 32) k_dfs(DfsArgs A) {
       for (int k = lane; k < TILE * S; k += 32) D.T[k] = 0;
       for (int k = lane; k < TILE; k += 32) D.rowbits[k] = D.colbits[k] = 0;
       __syncwarp();
+      bool fits = true;
       for (int r = lane; r < m; r += 32) {
         uint64_t rb = 0;
         for (int q = v.rowptr[r]; q < v.rowptr[r + 1]; ++q) {
           const int c = v.col[q];
-          D.T[r * S + c] = v.val[q];
+          const int64_t x = v.val[q];
+          if ((int64_t)(E)x != x) fits = false;
+          D.T[r * S + c] = (E)x;
           rb |= bit64(c);
           atomicOr((unsigned long long*)&D.colbits[c], (unsigned long long)bit64(r));
         }
         D.rowbits[r] = rb;
       }
+      fits = __all_sync(0xffffffffu, fits);
       __syncwarp();
+      if (!fits) status = DFS_RETRY;
       D.R = D.C = (m == 64) ? ~0ull : (bit64(m) - 1);
       for (int t = 0; t < 4; ++t) D.coef.w[t] = A.jobs.coef[4ll * job + t];
       int depth = 0;
-      bool done = false;
+      bool done = status != 0;
       while (!done) {
         // ---- visit the current node
         ++nodes;
@@ -399,10 +509,8 @@ __global__ void __launch_bounds__(DfsCfg<TILE>::WARPS * 32) k_dfs(DfsArgs A) {
         if (s > 0) {
           if (mact <= cut || s >= 5) {
             ++leaves;
-            if (!D.leaf(W, acc)) {
-              status = mact > PERM_MAX_LEAF ? PERM_EINVAL : PERM_EOVERFLOW;
-              break;
-            }
+            status = D.leaf(acc);
+            if (status != 0) break;
           } else if (depth >= TILE - 1) {
             status = PERM_EINVAL;
             break;
@@ -419,7 +527,7 @@ __global__ void __launch_bounds__(DfsCfg<TILE>::WARPS * 32) k_dfs(DfsArgs A) {
                 const int c = __ffsll((long long)line) - 1;
                 line &= line - 1;
                 f.pos[t] = c;
-                pv[t] = f.is_col ? D.T[c * S + f.idx] : D.T[f.idx * S + c];
+                pv[t] = (int64_t)(f.is_col ? D.T[c * S + f.idx] : D.T[f.idx * S + c]);
               } else {
                 f.pos[t] = 0;
               }
@@ -427,7 +535,7 @@ __global__ void __launch_bounds__(DfsCfg<TILE>::WARPS * 32) k_dfs(DfsArgs A) {
             D.store_frame(depth, f, pv, D.coef);
             __syncwarp();
             if (!D.apply(depth, f, pv, 0)) {
-              status = PERM_EOVERFLOW;
+              status = sizeof(E) == 4 ? DFS_RETRY : PERM_EOVERFLOW;
               break;
             }
             ++depth;
@@ -445,13 +553,13 @@ __global__ void __launch_bounds__(DfsCfg<TILE>::WARPS * 32) k_dfs(DfsArgs A) {
           int64_t pv[4];
           u256 pc;
           D.load_frame(depth - 1, f, pv, pc);
-          D.undo_child(depth - 1, f, pv, pc, f.child);
-          if (f.child + 1 < Dfs<TILE>::nchildren(f.k)) {
+          D.undo_child(depth - 1, f, pc, f.child);
+          if (f.child + 1 < Dfs<TILE, E, LN, W>::nchildren(f.k)) {
             f.child += 1;
             D.set_child(depth - 1, f.child);
             __syncwarp();
             if (!D.apply(depth - 1, f, pv, f.child)) {
-              status = PERM_EOVERFLOW;
+              status = sizeof(E) == 4 ? DFS_RETRY : PERM_EOVERFLOW;
               done = true;
             }
             break;
@@ -475,29 +583,46 @@ __global__ void __launch_bounds__(DfsCfg<TILE>::WARPS * 32) k_dfs(DfsArgs A) {
   }
 }
 
-template <int TILE>
-cudaError_t launch_dfs_tile(const DfsArgs& a, int num_sms, int warps_per_sm, cudaStream_t s) {
-  typedef DfsCfg<TILE> C;
+template <int TILE, typename E, int LN, int W>
+cudaError_t launch_dfs_variant(const DfsArgs& a, int num_sms, int warps_per_sm, cudaStream_t s) {
+  typedef DfsCfg<TILE, E> C;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_dfs<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_dfs<TILE, E, LN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfs<TILE, E, LN, W>, C::WARPS * 32, C::SMEM);
+  if (e != cudaSuccess) return e;
   int blocks_per_sm = (warps_per_sm + C::WARPS - 1) / C::WARPS;
+  if (blocks_per_sm > per_sm) blocks_per_sm = per_sm;
   if (blocks_per_sm < 1) blocks_per_sm = 1;
-  k_dfs<TILE><<<num_sms * blocks_per_sm, C::WARPS * 32, C::SMEM, s>>>(a);
+  k_dfs<TILE, E, LN, W><<<num_sms * blocks_per_sm, C::WARPS * 32, C::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t dfs_smem_bytes(int tile) { return tile <= 32 ? DfsCfg<32>::SMEM : DfsCfg<64>::SMEM; }
-int dfs_warps_per_block(int tile) { return tile <= 32 ? DfsCfg<32>::WARPS : DfsCfg<64>::WARPS; }
-int64_t dfs_undo_words(int tile) { return tile <= 32 ? DfsCfg<32>::UNDO_WORDS : DfsCfg<64>::UNDO_WORDS; }
+int dfs_warps_per_block(int tile, bool wide) {
+  if (wide) return tile <= 32 ? DfsCfg<32, int64_t>::WARPS : DfsCfg<64, int64_t>::WARPS;
+  return tile <= 32 ? DfsCfg<32, int32_t>::WARPS : DfsCfg<64, int32_t>::WARPS;
+}
+int64_t dfs_undo_words(int tile) { return tile <= 32 ? DfsCfg<32, int32_t>::UNDO_WORDS : DfsCfg<64, int32_t>::UNDO_WORDS; }
 
-cudaError_t launch_dfs(const DfsArgs& a, int tile, int num_sms, int warps_per_sm, cudaStream_t s) {
+template <int W>
+cudaError_t launch_dfs_w(const DfsArgs& a, int tile, bool wide, int num_sms, int warps_per_sm, cudaStream_t s) {
+  if (wide) {
+    if (tile <= 32) return launch_dfs_variant<32, int64_t, 32, W>(a, num_sms, warps_per_sm, s);
+    return launch_dfs_variant<64, int64_t, 32, W>(a, num_sms, warps_per_sm, s);
+  }
+  if (tile <= 32) return launch_dfs_variant<32, int32_t, 16, W>(a, num_sms, warps_per_sm, s);
+  return launch_dfs_variant<64, int32_t, 16, W>(a, num_sms, warps_per_sm, s);
+}
+
+cudaError_t launch_dfs(const DfsArgs& a, int tile, bool wide, int W, int num_sms, int warps_per_sm, cudaStream_t s) {
   if (a.nq <= 0) return cudaSuccess;
-  if (tile <= 32) return launch_dfs_tile<32>(a, num_sms, warps_per_sm, s);
-  return launch_dfs_tile<64>(a, num_sms, warps_per_sm, s);
+  if (W == 2) return launch_dfs_w<2>(a, tile, wide, num_sms, warps_per_sm, s);
+  return launch_dfs_w<4>(a, tile, wide, num_sms, warps_per_sm, s);
 }

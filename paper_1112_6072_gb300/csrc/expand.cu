@@ -339,18 +339,32 @@ __global__ void k_child_capacity(JobArrays parent, int64_t np, int64_t* words) {
   if (p < np) words[p] = 2 * blk_words(parent.m[p], parent.nnz[p]);
 }
 
+// stat[0]: largest kept order, stat[1]: words of the kept blocks, stat[2]:
+// kept jobs -- reduced per warp, one atomic per warp.
 __global__ void k_compact(JobArrays src, const int32_t* valid, const int32_t* pos, int64_t nslots, JobArrays dst,
-                          int32_t* max_order) {
-  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= nslots || !valid[s]) return;
-  atomicMax(max_order, src.m[s]);
-  const int64_t d = pos[s];
-  dst.m[d] = src.m[s];
-  dst.nnz[d] = src.nnz[s];
-  dst.off[d] = src.off[s];
-  dst.mat[d] = src.mat[s];
-  dst.depth_left[d] = src.depth_left[s];
-  for (int w = 0; w < 4; ++w) dst.coef[4 * d + w] = src.coef[4 * s + w];
+                          long long* stat) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool keep = s < nslots && valid[s];
+  unsigned m = 0, words = 0;
+  if (keep) {
+    const int64_t d = pos[s];
+    m = (unsigned)src.m[s];
+    words = (unsigned)blk_words(src.m[s], src.nnz[s]);
+    dst.m[d] = src.m[s];
+    dst.nnz[d] = src.nnz[s];
+    dst.off[d] = src.off[s];
+    dst.mat[d] = src.mat[s];
+    dst.depth_left[d] = src.depth_left[s];
+    for (int w = 0; w < 4; ++w) dst.coef[4 * d + w] = src.coef[4 * s + w];
+  }
+  const unsigned mx = __reduce_max_sync(0xffffffffu, m);
+  const unsigned sw = __reduce_add_sync(0xffffffffu, words);
+  const unsigned nk = __reduce_add_sync(0xffffffffu, keep ? 1u : 0u);
+  if ((threadIdx.x & 31) == 0 && nk) {
+    atomicMax(stat, (long long)mx);
+    atomicAdd(reinterpret_cast<unsigned long long*>(stat + 1), (unsigned long long)sw);
+    atomicAdd(reinterpret_cast<unsigned long long*>(stat + 2), (unsigned long long)nk);
+  }
 }
 
 template <int TILE>
@@ -386,8 +400,8 @@ cudaError_t launch_child_capacity(const JobArrays& parent, int64_t np, int64_t* 
 }
 
 cudaError_t launch_compact_jobs(const JobArrays& src, const int32_t* valid, const int32_t* pos, int64_t nslots,
-                                JobArrays dst, int32_t* max_order, cudaStream_t s) {
+                                JobArrays dst, long long* stat, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
-  k_compact<<<(unsigned)((nslots + 255) / 256), 256, 0, s>>>(src, valid, pos, nslots, dst, max_order);
+  k_compact<<<(unsigned)((nslots + 255) / 256), 256, 0, s>>>(src, valid, pos, nslots, dst, stat);
   return cudaGetLastError();
 }

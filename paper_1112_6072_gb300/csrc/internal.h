@@ -54,10 +54,11 @@ struct ExpandLevelArgs {
 cudaError_t launch_expand_level(const ExpandLevelArgs& a, int max_order, cudaStream_t s);
 // words[p] = 2 * blk_words(parent p) (capacity for its two children)
 cudaError_t launch_child_capacity(const JobArrays& parent, int64_t np, int64_t* words, cudaStream_t s);
-// Compact valid slots into dst (natural order kept); atomically raises
-// *max_order to the largest order kept.
+// Compact valid slots into dst (natural order kept).  Accumulates into
+// stat[0] the largest kept order, stat[1] the kept blocks' words and
+// stat[2] the kept job count (zero them first).
 cudaError_t launch_compact_jobs(const JobArrays& src, const int32_t* valid, const int32_t* pos, int64_t nslots,
-                                JobArrays dst, int32_t* max_order, cudaStream_t s);
+                                JobArrays dst, long long* stat, cudaStream_t s);
 
 // ---- K3 depth-first evaluator --------------------------------------------------
 struct DfsArgs {
@@ -74,13 +75,19 @@ struct DfsArgs {
   int64_t undo_words_per_warp;
   int64_t timeout_ns;
 };
-cudaError_t launch_dfs(const DfsArgs& a, int tile, int num_sms, int warps_per_sm, cudaStream_t s);
-size_t dfs_smem_bytes(int tile);
-int dfs_warps_per_block(int tile);
+// Internal job status of the narrow depth-first variant (int32 tile, leaves
+// up to 16 rows): the job needs the wide variant (int64 tile, leaves up to 32).
+#define DFS_RETRY 100
+// All queued jobs must belong to matrices of ring width W (2 or 4 words).
+cudaError_t launch_dfs(const DfsArgs& a, int tile, bool wide, int W, int num_sms, int warps_per_sm, cudaStream_t s);
+int dfs_warps_per_block(int tile, bool wide);
+int64_t dfs_undo_words(int tile);
 
 // ---- K4 KKLLL estimator -------------------------------------------------------
+// scratch: kklll_scratch_bytes(njobs, max_order, trials) bytes of device memory
 cudaError_t launch_kklll(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, int trials, uint64_t seed,
-                         float* log_ap, int max_order, cudaStream_t s);
+                         float* log_ap, int max_order, void* scratch, cudaStream_t s);
+size_t kklll_scratch_bytes(int64_t njobs, int max_order, int trials);
 
 // ---- K5 features and MLP -------------------------------------------------------
 cudaError_t launch_features(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, const float* log_ap,

@@ -187,11 +187,338 @@ cudaError_t launch_k(const JobArrays& jobs, int64_t njobs, const uint64_t* arena
   return cudaGetLastError();
 }
 
+// Register form for jobs of order m <= RL: a group of RL lanes runs one
+// trial at a time, lane r holding row r of the trial matrix in registers;
+// a warp runs 32 / RL trials side by side.  Rows never move: the pivot of
+// step k is chosen among the lanes not yet pivoted by largest |z|^2, ties to
+// the row currently at the lowest position (positions follow the row swaps
+// of partial pivoting), and its row is broadcast through shared memory.  The
+// step loop is unrolled to RL so every register index is a constant.
+template <int RL>
+__global__ void __launch_bounds__(128)
+    k_kklll_rows(JobArrays jobs, int64_t njobs, const uint64_t* __restrict__ arena, int trials, uint64_t seed,
+                 float* __restrict__ log_ap) {
+  constexpr int TPW = 32 / RL;  // trials per warp
+  __shared__ float2 prow_s[4][TPW][RL];
+  __shared__ uint32_t pat_s[4][32];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int grp = lane / RL;
+  const int r = lane % RL;
+  const unsigned gmask = (RL == 32) ? 0xffffffffu : (((1u << RL) - 1u) << (grp * RL));
+  float2* prow = prow_s[wib][grp];
+  uint32_t* pat = pat_s[wib];
+  const float RE[3] = {1.0f, -0.5f, -0.5f};
+  const float IM[3] = {0.0f, 0.86602540378443864676f, -0.86602540378443864676f};
+  const int64_t nwarps = (int64_t)gridDim.x * 4;
+  for (int64_t job = (int64_t)blockIdx.x * 4 + wib; job < njobs; job += nwarps) {
+    __syncwarp();
+    const int m = jobs.m[job];
+    if (m <= 0) {
+      if (lane == 0) log_ap[job] = 0.0f;
+      continue;
+    }
+    CsrView v = csr_view(arena, jobs.off[job], m, jobs.nnz[job]);
+    if (lane < m) {
+      uint32_t b = 0;
+      for (int q = v.rowptr[lane]; q < v.rowptr[lane + 1]; ++q) b |= 1u << v.col[q];
+      pat[lane] = b;
+    }
+    __syncwarp();
+    const int T = trials > 0 ? trials : m * m;
+    const uint64_t jkey = seed ^ ((uint64_t)job * K_JOB);
+    const uint32_t myrow = r < m ? pat[r] : 0u;
+    double lmax = -INFINITY, lsum = 0.0;  // running log-sum-exp of this group's trials
+    const int rounds = (T + TPW - 1) / TPW;
+    for (int it = 0; it < rounds; ++it) {
+      const int t = it * TPW + grp;
+      const bool live = t < T;
+      const uint64_t tkey = jkey ^ ((uint64_t)t * K_TRIAL);
+      float2 row[RL];
+#pragma unroll
+      for (int c = 0; c < RL; ++c) {
+        float2 z = make_float2(0.f, 0.f);
+        if (live && c < m && ((myrow >> c) & 1)) {
+          const uint64_t h = splitmix64_mix(tkey ^ ((uint64_t)(r * m + c) * K_ENTRY));
+          const int w = (int)(((h >> 32) * 3ull) >> 32);
+          z = make_float2(RE[w], IM[w]);
+        }
+        row[c] = z;
+      }
+      bool done = r >= m;
+      int pos = r;
+      float pm = 1.0f;
+      int pe = 0;
+      bool singular = !live;
+#pragma unroll
+      for (int k = 0; k < RL; ++k) {
+        if (k < m && !singular) {
+          const float mag = done ? -1.0f : row[k].x * row[k].x + row[k].y * row[k].y;
+          unsigned long long key = done ? 0ull
+                                        : ((unsigned long long)__float_as_uint(mag) << 32) |
+                                              (unsigned long long)(0xffffu - (unsigned)pos) << 8 | (unsigned)r;
+#pragma unroll
+          for (int d = RL / 2; d > 0; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(gmask, key, d, RL);
+            key = o > key ? o : key;
+          }
+          const float pmag = __uint_as_float((uint32_t)(key >> 32));
+          const int plane = (int)(key & 0xff);
+          if (!(pmag > 0.0f)) {
+            singular = true;
+          } else {
+            const int ppos = __shfl_sync(gmask, pos, plane, RL);
+            if (r == plane) {
+#pragma unroll
+              for (int c = k; c < RL; ++c) prow[c] = row[c];
+            }
+            // the row now at position k moves to the pivot's old position
+            if (pos == k) pos = ppos;
+            if (r == plane) {
+              pos = k;
+              done = true;
+            }
+            __syncwarp(gmask);
+            int ex;
+            pm = frexpf(pm * pmag, &ex);
+            pe += ex;
+            if (!done) {
+              const float2 piv = prow[k];
+              const float inv = 1.0f / pmag;
+              const float2 a = row[k];
+              const float2 f = make_float2((a.x * piv.x + a.y * piv.y) * inv, (a.y * piv.x - a.x * piv.y) * inv);
+#pragma unroll
+              for (int c = k + 1; c < RL; ++c) {
+                const float2 pc = prow[c];
+                row[c].x -= f.x * pc.x - f.y * pc.y;
+                row[c].y -= f.x * pc.y + f.y * pc.x;
+              }
+            }
+            __syncwarp(gmask);
+          }
+        }
+      }
+      if (r == 0 && !singular) {
+        const double l = log((double)pm) + (double)pe * 0.69314718055994530942;
+        if (l > lmax) {
+          lsum = lsum * exp(lmax - l) + 1.0;
+          lmax = l;
+        } else {
+          lsum += exp(l - lmax);
+        }
+      }
+    }
+    // merge the groups' log-sum-exp accumulators into lane 0
+#pragma unroll
+    for (int d = RL; d < 32; d <<= 1) {
+      const double om = __shfl_down_sync(0xffffffffu, lmax, d);
+      const double os = __shfl_down_sync(0xffffffffu, lsum, d);
+      if (om > lmax) {
+        lsum = lsum * exp(lmax - om) + os;
+        lmax = om;
+      } else if (om > -INFINITY) {
+        lsum += os * exp(om - lmax);
+      }
+    }
+    if (lane == 0) log_ap[job] = lmax == -INFINITY ? -INFINITY : (float)(lmax + log(lsum / (double)T));
+  }
+}
+
+// Thread form for jobs of order m <= MT: every thread runs one whole trial,
+// its m x m complex matrix in shared memory laid out [element][lane] so the
+// 32 lanes of a warp never conflict.  A warp takes 32 trials of one job;
+// the (max, sum) log-sum-exp of each warp's trials goes to part[] and a
+// second kernel combines a job's parts.
+template <int MT>
+struct TCfg {
+  static constexpr int WARPS = MT <= 8 ? 12 : (MT <= 12 ? 5 : 3);
+  static constexpr size_t WARP_BYTES = sizeof(float2) * MT * MT * 32;
+  static constexpr size_t SMEM = WARPS * WARP_BYTES;
+};
+
+template <int MT>
+__global__ void __launch_bounds__(TCfg<MT>::WARPS * 32)
+    k_kklll_thread(JobArrays jobs, int64_t njobs, const uint64_t* __restrict__ arena, int trials, uint64_t seed,
+                   int chunks_per_job, double2* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float2* Wt = reinterpret_cast<float2*>(smem_raw + (size_t)wib * TCfg<MT>::WARP_BYTES);
+#define WT(i, j) Wt[((i) * MT + (j)) * 32 + lane]
+  const float RE[3] = {1.0f, -0.5f, -0.5f};
+  const float IM[3] = {0.0f, 0.86602540378443864676f, -0.86602540378443864676f};
+  const int64_t items = njobs * (int64_t)chunks_per_job;
+  const int64_t nwarps = (int64_t)gridDim.x * TCfg<MT>::WARPS;
+  for (int64_t item = (int64_t)blockIdx.x * TCfg<MT>::WARPS + wib; item < items; item += nwarps) {
+    const int64_t job = item / chunks_per_job;
+    const int chunk = (int)(item % chunks_per_job);
+    const int m = jobs.m[job];
+    const int T = trials > 0 ? trials : m * m;
+    const int t = chunk * 32 + lane;
+    double lmax = -INFINITY, lsum = 0.0;
+    if (m >= 1 && m <= MT && t < T) {
+      CsrView v = csr_view(arena, jobs.off[job], m, jobs.nnz[job]);
+      const uint64_t tkey = seed ^ ((uint64_t)job * K_JOB) ^ ((uint64_t)t * K_TRIAL);
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) WT(i, j) = make_float2(0.f, 0.f);
+      for (int i = 0; i < m; ++i)
+        for (int q = v.rowptr[i]; q < v.rowptr[i + 1]; ++q) {
+          const int j = v.col[q];
+          const uint64_t h = splitmix64_mix(tkey ^ ((uint64_t)(i * m + j) * K_ENTRY));
+          const int w = (int)(((h >> 32) * 3ull) >> 32);
+          WT(i, j) = make_float2(RE[w], IM[w]);
+        }
+      float pm = 1.0f;
+      int pe = 0;
+      bool singular = false;
+      for (int k = 0; k < m && !singular; ++k) {
+        int p = k;
+        float best = -1.0f;
+        for (int r = k; r < m; ++r) {
+          const float2 z = WT(r, k);
+          const float mg = z.x * z.x + z.y * z.y;
+          if (mg > best) {
+            best = mg;
+            p = r;
+          }
+        }
+        if (!(best > 0.0f)) {
+          singular = true;
+          break;
+        }
+        if (p != k)
+          for (int c = k; c < m; ++c) {
+            const float2 a = WT(k, c);
+            WT(k, c) = WT(p, c);
+            WT(p, c) = a;
+          }
+        int ex;
+        pm = frexpf(pm * best, &ex);
+        pe += ex;
+        const float2 piv = WT(k, k);
+        const float inv = 1.0f / best;
+        const float2 ip = make_float2(piv.x * inv, -piv.y * inv);
+        // two rows per pass: independent load / update / store chains
+        int r = k + 1;
+        for (; r + 1 < m; r += 2) {
+          const float2 a0 = WT(r, k), a1 = WT(r + 1, k);
+          const float2 f0 = make_float2(a0.x * ip.x - a0.y * ip.y, a0.x * ip.y + a0.y * ip.x);
+          const float2 f1 = make_float2(a1.x * ip.x - a1.y * ip.y, a1.x * ip.y + a1.y * ip.x);
+#pragma unroll 4
+          for (int c = k + 1; c < m; ++c) {
+            const float2 pc = WT(k, c);
+            float2 z0 = WT(r, c), z1 = WT(r + 1, c);
+            z0.x -= f0.x * pc.x - f0.y * pc.y;
+            z0.y -= f0.x * pc.y + f0.y * pc.x;
+            z1.x -= f1.x * pc.x - f1.y * pc.y;
+            z1.y -= f1.x * pc.y + f1.y * pc.x;
+            WT(r, c) = z0;
+            WT(r + 1, c) = z1;
+          }
+        }
+        if (r < m) {
+          const float2 a = WT(r, k);
+          const float2 f = make_float2(a.x * ip.x - a.y * ip.y, a.x * ip.y + a.y * ip.x);
+#pragma unroll 4
+          for (int c = k + 1; c < m; ++c) {
+            const float2 pc = WT(k, c);
+            float2 z = WT(r, c);
+            z.x -= f.x * pc.x - f.y * pc.y;
+            z.y -= f.x * pc.y + f.y * pc.x;
+            WT(r, c) = z;
+          }
+        }
+      }
+      if (!singular) {
+        lmax = log((double)pm) + (double)pe * 0.69314718055994530942;
+        lsum = 1.0;
+      }
+    }
+#undef WT
+    // warp log-sum-exp of the 32 trials
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      const double om = __shfl_xor_sync(0xffffffffu, lmax, d);
+      const double os = __shfl_xor_sync(0xffffffffu, lsum, d);
+      const double mx = om > lmax ? om : lmax;
+      if (mx > -INFINITY) {
+        lsum = (lmax > -INFINITY ? lsum * exp(lmax - mx) : 0.0) + (om > -INFINITY ? os * exp(om - mx) : 0.0);
+        lmax = mx;
+      }
+    }
+    if (lane == 0) part[item] = make_double2(lmax, lsum);
+  }
+}
+
+__global__ void k_kklll_combine(JobArrays jobs, int64_t njobs, int trials, int chunks_per_job,
+                                const double2* __restrict__ part, float* __restrict__ log_ap) {
+  const int64_t job = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (job >= njobs) return;
+  const int m = jobs.m[job];
+  const int T = trials > 0 ? trials : m * m;
+  double lmax = -INFINITY, lsum = 0.0;
+  for (int c = 0; c < chunks_per_job; ++c) {
+    const double2 p = part[job * chunks_per_job + c];
+    if (p.x == -INFINITY) continue;
+    if (p.x > lmax) {
+      lsum = (lmax > -INFINITY ? lsum * exp(lmax - p.x) : 0.0) + p.y;
+      lmax = p.x;
+    } else {
+      lsum += p.y * exp(p.x - lmax);
+    }
+  }
+  log_ap[job] = m == 0 ? 0.0f : (lmax == -INFINITY ? -INFINITY : (float)(lmax + log(lsum / (double)T)));
+}
+
+template <int MT>
+cudaError_t launch_thread(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, int trials, uint64_t seed,
+                          float* log_ap, double2* part, int chunks, cudaStream_t s) {
+  typedef TCfg<MT> C;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_kklll_thread<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int64_t items = njobs * chunks;
+  int64_t blocks = (items + C::WARPS - 1) / C::WARPS;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_kklll_thread<MT><<<(unsigned)blocks, C::WARPS * 32, C::SMEM, s>>>(jobs, njobs, arena, trials, seed, chunks,
+                                                                     part);
+  k_kklll_combine<<<(unsigned)((njobs + 255) / 256), 256, 0, s>>>(jobs, njobs, trials, chunks, part, log_ap);
+  return cudaGetLastError();
+}
+
+template <int RL>
+cudaError_t launch_rows(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, int trials, uint64_t seed,
+                        float* log_ap, cudaStream_t s) {
+  int64_t blocks = (njobs + 3) / 4;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_kklll_rows<RL><<<(unsigned)blocks, 128, 0, s>>>(jobs, njobs, arena, trials, seed, log_ap);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
+static int kklll_chunks(int max_order, int trials) {
+  const int T = trials > 0 ? trials : max_order * max_order;
+  return (T + 31) / 32;
+}
+
+size_t kklll_scratch_bytes(int64_t njobs, int max_order, int trials) {
+  if (max_order > 16) return 16;
+  return sizeof(double2) * (size_t)(njobs > 0 ? njobs : 1) * (size_t)kklll_chunks(max_order, trials);
+}
+
 cudaError_t launch_kklll(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, int trials, uint64_t seed,
-                         float* log_ap, int max_order, cudaStream_t s) {
+                         float* log_ap, int max_order, void* scratch, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
-  if (max_order <= 32) return launch_k<32>(jobs, njobs, arena, trials, seed, log_ap, s);
+  double2* part = reinterpret_cast<double2*>(scratch);
+  const int chunks = kklll_chunks(max_order, trials);
+  if (max_order <= 8) return launch_thread<8>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
+  if (max_order <= 12) return launch_thread<12>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
+  if (max_order <= 16) return launch_thread<16>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
+  if (max_order <= 32) return launch_rows<32>(jobs, njobs, arena, trials, seed, log_ap, s);
   return launch_k<64>(jobs, njobs, arena, trials, seed, log_ap, s);
 }

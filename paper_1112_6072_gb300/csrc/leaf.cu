@@ -84,8 +84,8 @@ __global__ void k_leaf_classify(const uint32_t* __restrict__ queue, int64_t nq, 
   const int m = jobs.m[job];
   const int nnz = jobs.nnz[job];
   CsrView v = csr_view(arena, jobs.off[job], m, nnz);
-  int cc[PERM_MAX_LEAF];
-  for (int j = 0; j < PERM_MAX_LEAF; ++j) cc[j] = 0;
+  uint32_t cm[PERM_MAX_LEAF];  // rows holding a nonzero, per column
+  for (int j = 0; j < PERM_MAX_LEAF; ++j) cm[j] = 0;
   int64_t rmax = 0;
   bool ok = m <= PERM_MAX_LEAF;
   for (int r = 0; r < m && ok; ++r) {
@@ -94,7 +94,7 @@ __global__ void k_leaf_classify(const uint32_t* __restrict__ queue, int64_t nq, 
       const int64_t a = v.val[p];
       if (a >= (1ll << 30) || a <= -(1ll << 30)) ok = false;
       ra += a < 0 ? -a : a;
-      cc[v.col[p]]++;
+      cm[v.col[p]] |= 1u << r;
     }
     if (ra >= (1ll << 31)) ok = false;
     rmax = ra > rmax ? ra : rmax;
@@ -106,17 +106,13 @@ __global__ void k_leaf_classify(const uint32_t* __restrict__ queue, int64_t nq, 
     const int bc = bit_class(rmax);
     path = bc == 7 ? P_G7 : (bc == 15 ? P_G15 : P_G31);
     if (bc == 7 && m >= 3) {
-      int ca = 0, cb = -1;
-      for (int j = 1; j < m; ++j)
-        if (cc[j] < cc[ca]) ca = j;
-      for (int j = 0; j < m; ++j)
-        if (j != ca && (cb < 0 || cc[j] < cc[cb])) cb = j;
-      int k = 0;
-      for (int r = 0; r < m; ++r) {
-        bool t = false;
-        for (int p = v.rowptr[r]; p < v.rowptr[r + 1]; ++p) t = t || v.col[p] == ca || v.col[p] == cb;
-        k += t;
-      }
+      // the column pair touching the fewest rows (lowest pair on ties)
+      int k = 64;
+      for (int a = 0; a < m; ++a)
+        for (int b = a + 1; b < m; ++b) {
+          const int u = __popc(cm[a] | cm[b]);
+          k = u < k ? u : k;
+        }
       if (k <= 8) path = P_F8;
       else if (k <= 16 && m > 8) path = P_F16;
     }
@@ -160,18 +156,22 @@ __device__ void load_blocked(const uint64_t* __restrict__ arena, int64_t off, in
   colcnt[lane] = 0;
   __syncwarp();
   if (lane < m)
-    for (int p = v.rowptr[lane]; p < v.rowptr[lane + 1]; ++p) atomicAdd(&colcnt[v.col[p]], 1);
+    for (int p = v.rowptr[lane]; p < v.rowptr[lane + 1]; ++p)
+      atomicOr(reinterpret_cast<unsigned*>(&colcnt[v.col[p]]), 1u << lane);
   __syncwarp();
-  // two sparsest columns (lowest index on ties)
-  const unsigned key = lane < m ? ((unsigned)colcnt[lane] << 8) | (unsigned)lane : 0xffffffffu;
-  unsigned ka = key;
+  // the column pair touching the fewest rows, lowest (a, b) on ties
+  unsigned key = 0xffffffffu;
+  if (lane < m) {
+    const unsigned ma = (unsigned)colcnt[lane];
+    for (int b = lane + 1; b < m; ++b) {
+      const unsigned kk = ((unsigned)__popc(ma | (unsigned)colcnt[b]) << 16) | ((unsigned)lane << 8) | (unsigned)b;
+      key = kk < key ? kk : key;
+    }
+  }
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) ka = min(ka, __shfl_xor_sync(0xffffffffu, ka, d));
-  const int ca = (int)(ka & 0xff);
-  unsigned kb = lane == ca ? 0xffffffffu : key;
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) kb = min(kb, __shfl_xor_sync(0xffffffffu, kb, d));
-  const int cb = (int)(kb & 0xff);
+  for (int d = 16; d > 0; d >>= 1) key = min(key, __shfl_xor_sync(0xffffffffu, key, d));
+  const int ca = (int)((key >> 8) & 0xff);
+  const int cb = (int)(key & 0xff);
   int clast = m - 1;
   while (clast == ca || clast == cb) --clast;
   // rows touching ca or cb first

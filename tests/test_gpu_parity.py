@@ -170,6 +170,46 @@ def test_depth_first_signed_and_column_pivots():
             assert plan.result(0) == oracle.permanent(a)
 
 
+def test_depth_first_wide_retry_dense_block():
+    """A dense 17 x 17 block reached inside a depth-first job is a leaf of
+    17 rows (s >= 5): the narrow kernel hands the job to the wide one."""
+    sp = W.regular3(20, 3)
+    n = 37
+    a = np.zeros((n, n), np.int64)
+    a[:20, :20] = sp
+    a[20:, 20:] = 1
+    with pk.Plan([a], split_depth=2, leaf_size=12) as plan:
+        plan.expand()
+        rec = plan.evaluate(records=True)
+        got = plan.result(0)
+    assert got == oracle.permanent(sp) * math.factorial(17)
+    assert all(r.status == 0 for r in rec)
+
+
+@pytest.mark.parametrize("rows,cols", [([0], []), ([7], [3]), ([2, 9], [5])])
+def test_depth_first_big_entries_exact_or_overflow(rows, cols):
+    """Rows and columns scaled by s = 2^29 + 7 scale the permanent by s per
+    line (multilinearity).  Merged entries outgrow int32 (the narrow kernel
+    hands the job on) and may outgrow the leaf's range: the result is then
+    PERM_EOVERFLOW -- never a wrong value."""
+    base = W.regular3(30, 5)
+    s = (1 << 29) + 7
+    a = base.copy()
+    for r in rows:
+        a[r] *= s
+    for c in cols:
+        a[:, c] *= s
+    want = oracle.permanent(base) * s ** (len(rows) + len(cols))
+    try:
+        with pk.Plan([a], split_depth=4, leaf_size=10) as plan:
+            plan.expand()
+            plan.evaluate()
+            got = plan.result(0)
+        assert got == want
+    except pk.PermError as e:
+        assert e.status == 2
+
+
 def test_c60_both_constructions():
     from conftest import read_adjacency
     mats = [W.c60(seed=3), read_adjacency("c60_adjacency.txt")]
@@ -192,15 +232,18 @@ def test_batch_of_matrices_one_launch():
 
 
 # ---------------------------------------------------------------- estimator (K4) and order
-def test_kklll_matches_oracle():
-    a = W.regular3(30, 4)
-    with pk.Plan([a], split_depth=14, leaf_size=8, kklll_trials=0, seed=1234) as plan:
+@pytest.mark.parametrize("n,d,trials", [(30, 14, 0), (20, 12, 0), (40, 16, 0), (50, 8, 300)])
+def test_kklll_matches_oracle(n, d, trials):
+    """Register kernels for job orders <= 8, 16, 32 and the shared-memory
+    kernel above 32; relative 1e-5 on the mean (FP32 against fp64)."""
+    a = W.regular3(n, 4)
+    with pk.Plan([a], split_depth=d, leaf_size=4, kklll_trials=trials, seed=1234) as plan:
         plan.expand()
         la = plan.estimate()
         jobs = plan.jobs_export()
     rng = np.random.default_rng(0)
-    for j in rng.choice(len(jobs), size=min(12, len(jobs)), replace=False):
-        want = oracle.kklll_log_ap(jobs[j][1], seed=1234, job=int(j))
+    for j in rng.choice(len(jobs), size=min(8, len(jobs)), replace=False):
+        want = oracle.kklll_log_ap(jobs[j][1], seed=1234, job=int(j), trials=trials or None)
         assert abs(float(la[j]) - want) < 1e-5, (j, la[j], want)
 
 

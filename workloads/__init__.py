@@ -22,6 +22,7 @@ __all__ = [
     "regular3",
     "c60_coordinates",
     "c60",
+    "paper_adjacency",
     "shuffle_vertices",
     "leaf_batch",
     "sparse_rows",
@@ -89,6 +90,27 @@ def c60(seed: int | None = None) -> np.ndarray:
     a = (np.abs(d - dmin) < 1e-6).astype(np.int64)
     if seed is not None:
         a = shuffle_vertices(a, seed)
+    return a
+
+
+def paper_adjacency(name: str) -> np.ndarray:
+    """The C100 or C60 adjacency matrix printed in the paper's Appendix
+    (``name`` = "c100" or "c60"), read from the fixture under tests/golden."""
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden",
+                        f"{name}_adjacency.txt")
+    rows = []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            rows.append([int(x) for x in line.split()])
+    n = len(rows)
+    a = np.zeros((n, n), dtype=np.int64)
+    for r in rows:
+        for u in r[1:]:
+            a[r[0] - 1, u - 1] = 1
     return a
 
 
