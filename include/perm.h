@@ -88,6 +88,9 @@ typedef struct {
   perm_free_fn free;
   void* alloc_ctx;
   int64_t timeout_ns;      /* device watchdog for bounded waits; 0 = 10 s */
+  int32_t model_uses_estimate; /* 1: job features include the KKLLL estimate (runs the
+                                  estimator); 0: that feature is 0 and the learned order
+                                  needs no estimate */
 } perm_opts;
 
 /* Fill opts with the defaults above. */
@@ -157,6 +160,14 @@ perm_status perm_order(perm_jobs_t* jobs, int32_t kind, uint32_t* order_out);
  * row sum left int32), PERM_ETIMEOUT, PERM_ECUDA. */
 perm_status perm_eval_batch(perm_jobs_t* jobs, const uint32_t* order, perm_job_result* results);
 
+/* a7, a8 again, as a CUDA graph: repeat the last perm_eval_batch of this job
+ * set (same queue, same buffers).  The first call captures that
+ * evaluation's memsets and launches into a graph (on a stream the library
+ * creates), later calls launch the instantiated graph on the plan's stream.
+ * results as for perm_eval_batch.  PERM_ESTATE if the job set has not been
+ * evaluated yet. */
+perm_status perm_eval_replay(perm_jobs_t* jobs, perm_job_result* results);
+
 /* Wall time of the last perm_eval_batch on the device (ms), from events on
  * the plan's stream. */
 perm_status perm_last_eval_ms(perm_plan_t* plan, float* ms);
@@ -202,8 +213,9 @@ perm_status perm_exact(const perm_matrix* a, const perm_opts* opts, uint32_t* li
 #define PERM_MLP_PARAMS (64 * 12 + 64 + 64 * 64 + 64 + 64 + 1)
 
 /* Features of every job of the set, computed on the device (a5).  feats
- * (host) receives njobs * PERM_MLP_FEATURES floats.  Runs perm_estimate if
- * the set has no estimate yet. */
+ * (host) receives njobs * PERM_MLP_FEATURES floats.  With
+ * opts.model_uses_estimate set, runs perm_estimate if the set has no
+ * estimate yet; otherwise the estimate feature is 0. */
 perm_status perm_job_features(perm_jobs_t* jobs, float* feats);
 
 /* One forward and backward pass on a batch (device kernels): feats (host,

@@ -35,7 +35,7 @@ EXPORTED = [
     "perm_order", "perm_eval_batch", "perm_last_eval_ms", "perm_last_eval_launches", "perm_result", "perm_result_bits",
     "perm_result_words", "perm_jobs_export", "perm_exact", "perm_job_features", "perm_mlp_grad",
     "perm_mlp_train", "perm_mlp_predict", "perm_mlp_attach", "perm_ubench_imad",
-    "perm_status_string", "perm_last_error", "perm_leaf_batch_noalloc",
+    "perm_status_string", "perm_last_error", "perm_leaf_batch_noalloc", "perm_eval_replay",
 ]
 
 
@@ -65,7 +65,8 @@ class perm_opts(ctypes.Structure):
                 ("kklll_trials", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("workers_per_sm", ctypes.c_int32), ("chunk_log2", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("alloc", alloc_fn_t), ("free", free_fn_t),
-                ("alloc_ctx", ctypes.c_void_p), ("timeout_ns", ctypes.c_int64)]
+                ("alloc_ctx", ctypes.c_void_p), ("timeout_ns", ctypes.c_int64),
+                ("model_uses_estimate", ctypes.c_int32)]
 
 
 class perm_job_result(ctypes.Structure):
@@ -95,6 +96,7 @@ def _lib():
         lib.perm_estimate.argtypes = [vp, P(ctypes.c_float)]
         lib.perm_order.argtypes = [vp, ctypes.c_int32, P(ctypes.c_uint32)]
         lib.perm_eval_batch.argtypes = [vp, P(ctypes.c_uint32), P(perm_job_result)]
+        lib.perm_eval_replay.argtypes = [vp, P(perm_job_result)]
         lib.perm_last_eval_ms.argtypes = [vp, P(ctypes.c_float)]
         lib.perm_last_eval_launches.argtypes = [vp, P(ctypes.c_int32)]
         lib.perm_result.argtypes = [vp, ctypes.c_int32, P(ctypes.c_uint32), ctypes.c_int32,
@@ -203,7 +205,8 @@ class Plan:
     """
 
     def __init__(self, mats, split_depth=-1, leaf_size=0, order="lpt", kklll_trials=0, seed=0x5EED,
-                 workers_per_sm=0, chunk_log2=0, stream=None, torch_allocator=False, timeout_ns=0):
+                 workers_per_sm=0, chunk_log2=0, stream=None, torch_allocator=False, timeout_ns=0,
+                 model_uses_estimate=True):
         lib = _lib()
         self._mats = [np.ascontiguousarray(np.asarray(m, dtype=np.int64)) for m in mats]
         for m in self._mats:
@@ -225,6 +228,7 @@ class Plan:
         o.chunk_log2 = int(chunk_log2)
         o.stream = _stream_handle(stream)
         o.timeout_ns = int(timeout_ns)
+        o.model_uses_estimate = 1 if model_uses_estimate else 0
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator()
@@ -291,6 +295,15 @@ class Plan:
             optr = oa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
         res = (perm_job_result * max(self.njobs, 1))() if records else None
         _ck(lib.perm_eval_batch(self._jobs, optr, res), "perm_eval_batch")
+        if not records:
+            return None
+        return [JobRecord(r.matrix, r.order, r.nnz, r.status, _words_to_int(r.value), r.t_start_ns,
+                          r.t_end_ns, r.sm, r.queue_pos, r.leaves, r.nodes) for r in res[:self.njobs]]
+
+    def replay(self, records=False):
+        """Repeat the last evaluation as a captured CUDA graph."""
+        res = (perm_job_result * max(self.njobs, 1))() if records else None
+        _ck(_lib().perm_eval_replay(self._jobs, res), "perm_eval_replay")
         if not records:
             return None
         return [JobRecord(r.matrix, r.order, r.nnz, r.status, _words_to_int(r.value), r.t_start_ns,

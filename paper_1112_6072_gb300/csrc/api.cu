@@ -62,6 +62,7 @@ extern "C" void perm_opts_default(perm_opts* o) {
   o->chunk_log2 = 0;
   o->stream = nullptr;
   o->timeout_ns = 0;
+  o->model_uses_estimate = 1;
 }
 
 // ---------------------------------------------------------------- memory
@@ -174,6 +175,32 @@ struct JobBuf {
   }
 };
 
+// Prepared evaluation of one queue: host-side split into leaf and
+// depth-first queues, leaf kernel variants, and the device buffers the
+// launches use.  Kept with the job set so the launch sequence can be
+// captured once into a CUDA graph and replayed.
+struct EvalState {
+  std::vector<uint32_t> q, leafq, dfsq;
+  int64_t nl = 0, nd = 0, nd_w2 = 0;
+  std::vector<std::pair<int64_t, int64_t>> groups;  // (offset, count) in the grouped leaf queue
+  std::vector<int32_t> group_cls;
+  uint32_t* d_lq = nullptr;
+  uint32_t* d_dq = nullptr;
+  uint32_t* d_rq = nullptr;  // retry queue
+  uint64_t* counts = nullptr;
+  uint64_t* prefix = nullptr;
+  void* stmp = nullptr;
+  size_t stb = 0;
+  unsigned long long* ctr = nullptr;
+  int64_t* undo = nullptr;
+  int64_t undo_w = 0;
+  int tile = 32, wps = 0, chunk = 10;
+  bool wide_first = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+};
+
 // ---------------------------------------------------------------- handles
 struct perm_jobs {
   perm_plan* plan = nullptr;
@@ -188,7 +215,21 @@ struct perm_jobs {
   float* d_logap = nullptr;
   bool has_logap = false;
   JobOut out{};
+  EvalState* ev = nullptr;
 };
+
+static void free_eval(Mem& M, perm_jobs* J) {
+  EvalState* E = J->ev;
+  if (!E) return;
+  if (E->exec) cudaGraphExecDestroy(E->exec);
+  if (E->graph) cudaGraphDestroy(E->graph);
+  if (E->cap) cudaStreamDestroy(E->cap);
+  for (void* p : {(void*)E->d_lq, (void*)E->d_dq, (void*)E->d_rq, (void*)E->counts, (void*)E->prefix, E->stmp,
+                  (void*)E->ctr, (void*)E->undo})
+    M.put(p);
+  delete E;
+  J->ev = nullptr;
+}
 
 struct perm_plan {
   perm_opts opts{};
@@ -381,6 +422,7 @@ extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, 
 static void free_jobset(perm_plan* P) {
   perm_jobs* J = P->jobs;
   if (!J) return;
+  free_eval(P->M, J);
   free_jobs(P->M, J->a);
   P->M.put(J->arena);
   P->M.put(J->d_queue);
@@ -585,13 +627,14 @@ extern "C" perm_status perm_estimate(perm_jobs_t* J, float* log_ap) {
 extern "C" perm_status perm_job_features(perm_jobs_t* J, float* feats) {
   if (!J || !feats) return PERM_EINVAL;
   perm_plan* P = J->plan;
-  if (!J->has_logap) {
+  const bool use_ap = P->opts.model_uses_estimate != 0;
+  if (use_ap && !J->has_logap) {
     perm_status st = perm_estimate(J, nullptr);
     if (st != PERM_OK) return st;
   }
   float* d = dget<float>(P->M, J->n * PERM_MLP_FEATURES);
   if (!d) return PERM_ENOMEM;
-  CK(launch_features(J->a, J->n, J->arena, J->d_logap, d, P->s));
+  CK(launch_features(J->a, J->n, J->arena, use_ap ? J->d_logap : nullptr, d, P->s));
   CK(cudaMemcpyAsync(feats, d, sizeof(float) * J->n * PERM_MLP_FEATURES, cudaMemcpyDeviceToHost, P->s));
   CK(cudaStreamSynchronize(P->s));
   P->M.put(d);
@@ -639,7 +682,8 @@ extern "C" perm_status perm_order(perm_jobs_t* J, int32_t kind, uint32_t* order_
     perm_status st = sort_queue_by(P, J, J->d_logap);
     if (st != PERM_OK) return st;
   } else if (kind == PERM_ORDER_LEARNED) {
-    if (!J->has_logap) {
+    const bool use_ap = P->opts.model_uses_estimate != 0;
+    if (use_ap && !J->has_logap) {
       perm_status st = perm_estimate(J, nullptr);
       if (st != PERM_OK) return st;
     }
@@ -648,7 +692,7 @@ extern "C" perm_status perm_order(perm_jobs_t* J, int32_t kind, uint32_t* order_
     float* pred = dget<float>(P->M, n);
     if (!feats || !params || !pred) return PERM_ENOMEM;
     CK(cudaMemcpyAsync(params, P->mlp.data(), 4 * PERM_MLP_PARAMS, cudaMemcpyHostToDevice, P->s));
-    CK(launch_features(J->a, n, J->arena, J->d_logap, feats, P->s));
+    CK(launch_features(J->a, n, J->arena, use_ap ? J->d_logap : nullptr, feats, P->s));
     CK(mlp_predict(params, feats, (int32_t)n, pred, P->s));
     perm_status st = sort_queue_by(P, J, pred);
     P->M.put(feats);
@@ -667,13 +711,17 @@ extern "C" perm_status perm_order(perm_jobs_t* J, int32_t kind, uint32_t* order_
 }
 
 // ---------------------------------------------------------------- a7, a8: evaluate
-extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, perm_job_result* results) {
-  if (!J) return PERM_EINVAL;
+// prepare: split the queue, classify leaf variants, upload, size buffers.
+static perm_status eval_prepare(perm_jobs* J, const uint32_t* order) {
   perm_plan* P = J->plan;
   cudaStream_t s = P->s;
   Mem& M = P->M;
   const int64_t n = J->n;
-  std::vector<uint32_t> q(n);
+  free_eval(M, J);
+  J->ev = new EvalState();
+  EvalState& E = *J->ev;
+  std::vector<uint32_t>& q = E.q;
+  q.resize(n);
   if (order) {
     std::vector<uint8_t> seen(n, 0);
     for (int64_t k = 0; k < n; ++k) {
@@ -692,7 +740,8 @@ extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, pe
     }
   }
   // leaf-order jobs go to the batched leaf kernel, the rest to the depth-first one
-  std::vector<uint32_t> leafq, dfsq;
+  std::vector<uint32_t>& leafq = E.leafq;
+  std::vector<uint32_t>& dfsq = E.dfsq;
   leafq.reserve(n);
   int dfs_max = 0;
   for (int64_t k = 0; k < n; ++k) {
@@ -715,29 +764,35 @@ extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, pe
     dfsq.swap(g2);
   }
   const int64_t nl = (int64_t)leafq.size(), nd = (int64_t)dfsq.size();
-  uint32_t* d_lq = dget<uint32_t>(M, nl);
-  uint32_t* d_dq = dget<uint32_t>(M, nd);
-  uint64_t* counts = dget<uint64_t>(M, nl + 1);
-  uint64_t* prefix = dget<uint64_t>(M, nl + 1);
-  size_t stb = scan_tmp_bytes_u64(nl + 1);
-  void* stmp = M.get(stb);
-  unsigned long long* ctr = dget<unsigned long long>(M, 2);
-  const int tile = dfs_max <= 32 ? 32 : 64;
+  E.nl = nl;
+  E.nd = nd;
+  E.nd_w2 = nd_w2;
+  uint32_t* d_lq = E.d_lq = dget<uint32_t>(M, nl);
+  uint32_t* d_dq = E.d_dq = dget<uint32_t>(M, nd);
+  E.d_rq = dget<uint32_t>(M, nd);
+  E.counts = dget<uint64_t>(M, nl + 1);
+  E.prefix = dget<uint64_t>(M, nl + 1);
+  E.stb = scan_tmp_bytes_u64(nl + 1);
+  E.stmp = M.get(E.stb);
+  E.ctr = dget<unsigned long long>(M, 2);
+  E.tile = dfs_max <= 32 ? 32 : 64;
   // the narrow variant (int32 tile, leaves <= 16 rows) unless the leaf order needs the wide one
-  const bool wide_first = P->L > 16;
-  const int wps = P->opts.workers_per_sm > 0 ? P->opts.workers_per_sm : (tile <= 32 ? 24 : 10);
+  E.wide_first = P->L > 16;
+  E.wps = P->opts.workers_per_sm > 0 ? P->opts.workers_per_sm : (E.tile <= 32 ? 24 : 10);
+  E.chunk = P->opts.chunk_log2 > 0 ? P->opts.chunk_log2 : 10;
   int dfs_warps = 0;
   for (bool w : {false, true}) {
-    const int wpb = dfs_warps_per_block(tile, w);
-    dfs_warps = std::max(dfs_warps, P->sms * ((wps + wpb - 1) / wpb) * wpb);
+    const int wpb = dfs_warps_per_block(E.tile, w);
+    dfs_warps = std::max(dfs_warps, P->sms * ((E.wps + wpb - 1) / wpb) * wpb);
   }
-  const int64_t undo_w = dfs_undo_words(tile);
-  int64_t* undo = nd > 0 ? dget<int64_t>(M, undo_w * dfs_warps) : nullptr;
-  if (!d_lq || !d_dq || !counts || !prefix || !stmp || !ctr || (nd > 0 && !undo)) return PERM_ENOMEM;
+  E.undo_w = dfs_undo_words(E.tile);
+  E.undo = nd > 0 ? dget<int64_t>(M, E.undo_w * dfs_warps) : nullptr;
+  if (!d_lq || !d_dq || !E.d_rq || !E.counts || !E.prefix || !E.stmp || !E.ctr || (nd > 0 && !E.undo))
+    return PERM_ENOMEM;
   if (nd) CK(cudaMemcpyAsync(d_dq, dfsq.data(), 4 * nd, cudaMemcpyHostToDevice, s));
   // leaf variants: classify on the device, then group stably by variant
-  std::vector<std::pair<int64_t, int64_t>> groups;  // (offset, count) in the grouped leaf queue
-  std::vector<int32_t> group_cls;
+  std::vector<std::pair<int64_t, int64_t>>& groups = E.groups;
+  std::vector<int32_t>& group_cls = E.group_cls;
   if (nl) {
     int32_t* d_cls = dget<int32_t>(M, nl);
     if (!d_cls) return PERM_ENOMEM;
@@ -762,87 +817,114 @@ extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, pe
     leafq.swap(grouped);
     CK(cudaMemcpyAsync(d_lq, leafq.data(), 4 * nl, cudaMemcpyHostToDevice, s));
   }
-  const int64_t nj = std::max<int64_t>(n, 1);
-  CK(cudaMemsetAsync(J->out.acc, 0, 32 * nj, s));
-  CK(cudaMemsetAsync(J->out.t_start, 0xff, 8 * nj, s));
-  CK(cudaMemsetAsync(J->out.t_end, 0, 8 * nj, s));
-  CK(cudaMemsetAsync(J->out.status, 0, 4 * nj, s));
-  CK(cudaMemsetAsync(J->out.sm, 0xff, 4 * nj, s));
-  CK(cudaMemsetAsync(J->out.leaves, 0, 8 * nj, s));
-  CK(cudaMemsetAsync(J->out.nodes, 0, 8 * nj, s));
-  CK(cudaMemsetAsync(P->d_mat_acc, 0, 32ull * P->count, s));
-  CK(cudaMemsetAsync(ctr, 0, 16, s));
-  const int chunk = P->opts.chunk_log2 > 0 ? P->opts.chunk_log2 : 10;
-  CK(cudaEventRecord(P->ev0, s));
+  CK(cudaStreamSynchronize(s));
+  return PERM_OK;
+}
+
+static DfsArgs dfs_args(perm_jobs* J) {
+  perm_plan* P = J->plan;
+  EvalState& E = *J->ev;
   DfsArgs D{};
-  if (nd > 0) {
-    D.queue = d_dq;
-    D.nq = nd;
-    D.jobs = J->a;
-    D.arena = J->arena;
-    D.mat_w = P->d_mat_w;
-    D.leaf_size = P->L;
-    D.job_counter = ctr + 1;
-    D.out = J->out;
-    D.mat_acc = P->d_mat_acc;
-    D.undo = undo;
-    D.undo_words_per_warp = undo_w;
-    D.timeout_ns = P->opts.timeout_ns > 0 ? P->opts.timeout_ns : 10000000000ll;
+  D.queue = E.d_dq;
+  D.nq = E.nd_w2;
+  D.jobs = J->a;
+  D.arena = J->arena;
+  D.mat_w = P->d_mat_w;
+  D.leaf_size = P->L;
+  D.job_counter = E.ctr + 1;
+  D.out = J->out;
+  D.mat_acc = P->d_mat_acc;
+  D.undo = E.undo;
+  D.undo_words_per_warp = E.undo_w;
+  D.timeout_ns = P->opts.timeout_ns > 0 ? P->opts.timeout_ns : 10000000000ll;
+  return D;
+}
+
+// enqueue: memsets and launches only (no host synchronisation), on stream s.
+static cudaError_t eval_enqueue(perm_jobs* J, cudaStream_t s) {
+  perm_plan* P = J->plan;
+  EvalState& E = *J->ev;
+  const int64_t nj = std::max<int64_t>(J->n, 1);
+  cudaError_t e;
+#define EQ(call)                          \
+  do {                                    \
+    if ((e = (call)) != cudaSuccess) return e; \
+  } while (0)
+  EQ(cudaMemsetAsync(J->out.acc, 0, 32 * nj, s));
+  EQ(cudaMemsetAsync(J->out.t_start, 0xff, 8 * nj, s));
+  EQ(cudaMemsetAsync(J->out.t_end, 0, 8 * nj, s));
+  EQ(cudaMemsetAsync(J->out.status, 0, 4 * nj, s));
+  EQ(cudaMemsetAsync(J->out.sm, 0xff, 4 * nj, s));
+  EQ(cudaMemsetAsync(J->out.leaves, 0, 8 * nj, s));
+  EQ(cudaMemsetAsync(J->out.nodes, 0, 8 * nj, s));
+  EQ(cudaMemsetAsync(P->d_mat_acc, 0, 32ull * P->count, s));
+  EQ(cudaMemsetAsync(E.ctr, 0, 16, s));
+  if (E.nd > 0) {
     // ring width 2 then 4; each launch has its own job counter
-    D.nq = nd_w2;
-    CK(launch_dfs(D, tile, wide_first, 2, P->sms, wps, s));
-    D.queue = d_dq + nd_w2;
-    D.nq = nd - nd_w2;
-    D.job_counter = ctr;
-    CK(launch_dfs(D, tile, wide_first, 4, P->sms, wps, s));
+    DfsArgs D = dfs_args(J);
+    EQ(launch_dfs(D, E.tile, E.wide_first, 2, P->sms, E.wps, s));
+    D.queue = E.d_dq + E.nd_w2;
+    D.nq = E.nd - E.nd_w2;
+    D.job_counter = E.ctr;
+    EQ(launch_dfs(D, E.tile, E.wide_first, 4, P->sms, E.wps, s));
   }
-  if (nl > 0) {
+  if (E.nl > 0) {
     // one persistent grid per kernel variant, queue order kept inside each variant
-    for (size_t g = 0; g < groups.size(); ++g) {
-      CK(launch_leaf_batch(d_lq + groups[g].first, groups[g].second, group_cls[g], J->a, J->arena, chunk, counts,
-                           prefix, stmp, stb, ctr, J->out, P->sms, s));
-    }
-    CK(launch_leaf_finalize(d_lq, nl, J->a, J->out, P->d_mat_acc, s));
+    for (size_t g = 0; g < E.groups.size(); ++g)
+      EQ(launch_leaf_batch(E.d_lq + E.groups[g].first, E.groups[g].second, E.group_cls[g], J->a, J->arena, E.chunk,
+                           E.counts, E.prefix, E.stmp, E.stb, E.ctr, J->out, P->sms, s));
+    EQ(launch_leaf_finalize(E.d_lq, E.nl, J->a, J->out, P->d_mat_acc, s));
   }
-  CK(cudaEventRecord(P->ev1, s));
-  // per leaf group: task counts, two scan kernels, the batch; plus finalize and the depth-first grid
-  P->last_launches = (int32_t)(4 * groups.size() + (nl > 0 ? 1 : 0) + (nd > 0 ? 1 : 0));
+#undef EQ
+  // per leaf group: task counts, two scan kernels, the batch; plus finalize and the depth-first grids
+  P->last_launches = (int32_t)(4 * E.groups.size() + (E.nl > 0 ? 1 : 0) + (E.nd > 0 ? 2 : 0));
+  return cudaSuccess;
+}
+
+// finish: wait, re-run jobs the narrow depth-first variant handed on, read
+// statuses and (optionally) the per-job records.
+static perm_status eval_finish(perm_jobs* J, perm_job_result* results) {
+  perm_plan* P = J->plan;
+  EvalState& E = *J->ev;
+  cudaStream_t s = P->s;
+  const int64_t n = J->n;
   CK(cudaEventSynchronize(P->ev1));
   CK(cudaEventElapsedTime(&P->last_ms, P->ev0, P->ev1));
   std::vector<int32_t> st(n);
   if (n) CK(cudaMemcpyAsync(st.data(), J->out.status, 4 * n, cudaMemcpyDeviceToHost, s));
-  if (nd > 0 && !wide_first) {
+  CK(cudaStreamSynchronize(s));
+  if (E.nd > 0 && !E.wide_first) {
     // jobs the narrow depth-first variant could not hold run again on the wide one
-    CK(cudaStreamSynchronize(s));
     std::vector<uint32_t> retry;
     int64_t nr2 = 0;
-    for (int64_t k = 0; k < nd; ++k)
-      if (st[dfsq[k]] == DFS_RETRY) {
-        retry.push_back(dfsq[k]);
-        if (k < nd_w2) ++nr2;
+    for (int64_t k = 0; k < E.nd; ++k)
+      if (st[E.dfsq[k]] == DFS_RETRY) {
+        retry.push_back(E.dfsq[k]);
+        if (k < E.nd_w2) ++nr2;
       }
     if (!retry.empty()) {
       const int64_t nr = (int64_t)retry.size();
-      CK(cudaMemcpyAsync(d_dq, retry.data(), 4 * nr, cudaMemcpyHostToDevice, s));
-      CK(cudaMemsetAsync(ctr, 0, 16, s));
+      CK(cudaMemcpyAsync(E.d_rq, retry.data(), 4 * nr, cudaMemcpyHostToDevice, s));
+      CK(cudaMemsetAsync(E.ctr, 0, 16, s));
       float ms2 = 0.f;
+      DfsArgs D = dfs_args(J);
       CK(cudaEventRecord(P->ev0, s));
-      D.queue = d_dq;
+      D.queue = E.d_rq;
       D.nq = nr2;
-      D.job_counter = ctr + 1;
-      CK(launch_dfs(D, tile, true, 2, P->sms, wps, s));
-      D.queue = d_dq + nr2;
+      CK(launch_dfs(D, E.tile, true, 2, P->sms, E.wps, s));
+      D.queue = E.d_rq + nr2;
       D.nq = nr - nr2;
-      D.job_counter = ctr;
-      CK(launch_dfs(D, tile, true, 4, P->sms, wps, s));
+      D.job_counter = E.ctr;
+      CK(launch_dfs(D, E.tile, true, 4, P->sms, E.wps, s));
       CK(cudaEventRecord(P->ev1, s));
       CK(cudaEventSynchronize(P->ev1));
       CK(cudaEventElapsedTime(&ms2, P->ev0, P->ev1));
       P->last_ms += ms2;
-      P->last_launches += 1;
+      P->last_launches += 2;
       CK(cudaMemcpyAsync(st.data(), J->out.status, 4 * n, cudaMemcpyDeviceToHost, s));
     }
   }
+  const std::vector<uint32_t>& q = E.q;
   if (results && n) {
     std::vector<unsigned long long> acc(4 * n), t0(n), t1(n), lv(n), nd_(n);
     std::vector<int32_t> sm(n), mat(n), nnz(n);
@@ -873,17 +955,46 @@ extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, pe
     }
   }
   CK(cudaStreamSynchronize(s));
-  M.put(d_lq);
-  M.put(d_dq);
-  M.put(counts);
-  M.put(prefix);
-  M.put(stmp);
-  M.put(ctr);
-  M.put(undo);
   for (int64_t j = 0; j < n; ++j)
     if (st[j] != 0) return (perm_status)st[j];
   P->evaluated = true;
   return PERM_OK;
+}
+
+extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, perm_job_result* results) {
+  if (!J) return PERM_EINVAL;
+  perm_plan* P = J->plan;
+  perm_status st = eval_prepare(J, order);
+  if (st != PERM_OK) return st;
+  CK(cudaEventRecord(P->ev0, P->s));
+  CK(eval_enqueue(J, P->s));
+  CK(cudaEventRecord(P->ev1, P->s));
+  return eval_finish(J, results);
+}
+
+extern "C" perm_status perm_eval_replay(perm_jobs_t* J, perm_job_result* results) {
+  if (!J) return PERM_EINVAL;
+  perm_plan* P = J->plan;
+  EvalState* E = J->ev;
+  if (!E) return PERM_ESTATE;
+  if (!E->exec) {
+    // capture the launch sequence once, on a stream of the library's own
+    // (the caller's stream may be the legacy default stream, which cannot capture)
+    CK(cudaStreamSynchronize(P->s));
+    if (!E->cap) CK(cudaStreamCreateWithFlags(&E->cap, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(E->cap, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t ce = eval_enqueue(J, E->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(E->cap, &g);
+    CK(ce);
+    CK(ee);
+    E->graph = g;
+    CK(cudaGraphInstantiate(&E->exec, E->graph, 0));
+  }
+  CK(cudaEventRecord(P->ev0, P->s));
+  CK(cudaGraphLaunch(E->exec, P->s));
+  CK(cudaEventRecord(P->ev1, P->s));
+  return eval_finish(J, results);
 }
 
 extern "C" perm_status perm_last_eval_launches(perm_plan_t* P, int32_t* launches) {

@@ -76,31 +76,50 @@ __device__ __forceinline__ int nth_bit(uint64_t mask, int n) {
 
 __device__ __forceinline__ uint64_t bit64(int i) { return 1ull << i; }
 
-// Lane shares of one leaf, summed over the warp into lane 0's words.
+// One leaf walk per (NMAX, W, path), kept out of line: the node loop of the
+// evaluator stays small in the instruction cache, and each walk exists once.
+// path: 0/1/2 plain walk with bit class 7/15/31, 3 blocked NN=8, 4 blocked NN=16
+template <int NM, int W, int PATH>
+__device__ __noinline__ void leaf_walk(const int32_t* delta, const int32_t* rho0, int m, uint64_t gb, uint64_t cnt,
+                                       uint64_t* words) {
+  if constexpr (PATH == 3) {
+    run_lane4<NM, 8, W>(delta, rho0, m, gb, cnt, words);
+  } else if constexpr (PATH == 4) {
+    run_lane4<NM, 16, W>(delta, rho0, m, gb, cnt, words);
+  } else {
+    typename WideT<W>::type s = ryser_lane<NM, W, PATH == 0 ? 7 : (PATH == 1 ? 15 : 31)>(delta, rho0, m, gb, cnt);
+    s = warp_sum(s);
+    to_words(s, words);
+  }
+}
+
+template <int NM, int W>
+__device__ __forceinline__ void leaf_paths(int path, const int32_t* delta, const int32_t* rho0, int m, uint64_t gb,
+                                           uint64_t cnt, uint64_t* words) {
+  switch (path) {
+    case 0: leaf_walk<NM, W, 0>(delta, rho0, m, gb, cnt, words); break;
+    case 1: leaf_walk<NM, W, 1>(delta, rho0, m, gb, cnt, words); break;
+    case 2: leaf_walk<NM, W, 2>(delta, rho0, m, gb, cnt, words); break;
+    case 3: leaf_walk<NM, W, 3>(delta, rho0, m, gb, cnt, words); break;
+    default:
+      if constexpr (NM >= 16) leaf_walk<NM, W, 4>(delta, rho0, m, gb, cnt, words);
+      break;
+  }
+}
+
+// Lane shares of one leaf, summed over the warp into lane 0's words.  The
+// narrow variant (LN = 16) holds every leaf in 16 register rows.
 template <int LN, int W>
 __device__ __forceinline__ void leaf_dispatch(int nmax, int path, const int32_t* delta, const int32_t* rho0,
                                               int m, uint64_t gb, uint64_t cnt, uint64_t* words) {
-  // path: 0/1/2 plain walk with bit class 7/15/31, 3 blocked NN=8, 4 blocked NN=16
-#define DFS_PLAIN(NM, WW)                                                                  \
-  do {                                                                                     \
-    typename WideT<WW>::type s_;                                                           \
-    if (path == 0) s_ = ryser_lane<NM, WW, 7>(delta, rho0, m, gb, cnt);                    \
-    else if (path == 1) s_ = ryser_lane<NM, WW, 15>(delta, rho0, m, gb, cnt);              \
-    else s_ = ryser_lane<NM, WW, 31>(delta, rho0, m, gb, cnt);                             \
-    s_ = warp_sum(s_);                                                                     \
-    to_words(s_, words);                                                                   \
-  } while (0)
-#define DFS_CASE(NM, WW)                                                                   \
-  if (path == 3) run_lane4<NM, 8, WW>(delta, rho0, m, gb, cnt, words);                      \
-  else if (path == 4) { if constexpr (NM >= 16) run_lane4<NM, 16, WW>(delta, rho0, m, gb, cnt, words); } \
-  else DFS_PLAIN(NM, WW);
-  if (nmax == 8) { DFS_CASE(8, W) }
-  else if (nmax == 16) { DFS_CASE(16, W) }
-  else if constexpr (LN >= 32) {
-    if (nmax == 24) { DFS_CASE(24, W) } else { DFS_CASE(32, W) }
+  if constexpr (LN <= 16) {
+    leaf_paths<16, W>(path, delta, rho0, m, gb, cnt, words);
+  } else {
+    if (nmax == 8) leaf_paths<8, W>(path, delta, rho0, m, gb, cnt, words);
+    else if (nmax == 16) leaf_paths<16, W>(path, delta, rho0, m, gb, cnt, words);
+    else if (nmax == 24) leaf_paths<24, W>(path, delta, rho0, m, gb, cnt, words);
+    else leaf_paths<32, W>(path, delta, rho0, m, gb, cnt, words);
   }
-#undef DFS_CASE
-#undef DFS_PLAIN
 }
 
 template <int TILE, typename E, int LN, int W>
@@ -308,7 +327,7 @@ struct Dfs {
     }
     if (m > PERM_MAX_LEAF) return PERM_EINVAL;
     if (m > LN) return DFS_RETRY;
-    const int nmax = nmax_for(m);
+    const int nmax = LN <= 16 ? 16 : nmax_for(m);
     // row ranges, and per leaf column the leaf rows holding a nonzero
     int64_t rmax = 0;
     bool ok = true;

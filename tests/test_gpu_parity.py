@@ -84,6 +84,25 @@ def test_leaf_batch_full_size_sample():
     assert got == want
 
 
+def test_graph_replay_matches_eval():
+    """The evaluation captured as a CUDA graph and replayed gives the same
+    permanents and job values, replay after replay (leaf and depth-first)."""
+    mats = W.leaf_batch(30, seed=8, nmin=10, nmax=20) + [W.regular3(30, 3)]
+    with pk.Plan(mats, leaf_size=10) as plan:
+        plan.expand()
+        rec = plan.evaluate(records=True)
+        want = plan.results()
+        for _ in range(3):
+            rec2 = plan.replay(records=True)
+            assert plan.results() == want
+            assert [r.value_mod for r in rec2] == [r.value_mod for r in rec]
+    assert want[-1] == oracle.permanent(mats[-1])
+    with pk.Plan([W.regular3(12, 1)]) as plan:
+        plan.expand()
+        with pytest.raises(pk.PermError):
+            plan.replay()
+
+
 def test_zero_and_empty_inputs():
     z = W.random_small(5, 1)
     z[:, 2] = 0
