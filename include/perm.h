@@ -69,8 +69,10 @@ typedef struct {
 } perm_matrix;
 
 /* Optional device allocator: lets a host framework (e.g. PyTorch's caching
- * allocator) own the memory.  Both NULL: cudaMallocAsync / cudaFreeAsync on
- * the plan's stream. */
+ * allocator) own the memory.  Both NULL: stream-ordered allocations on the
+ * plan's stream from a memory pool the library creates per device, which
+ * keeps up to 4 GiB of freed memory mapped for later plans (released at
+ * process exit). */
 typedef void* (*perm_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*perm_free_fn)(void* ptr, void* stream, void* ctx);
 
@@ -91,6 +93,10 @@ typedef struct {
   int32_t model_uses_estimate; /* 1: job features include the KKLLL estimate (runs the
                                   estimator); 0: that feature is 0 and the learned order
                                   needs no estimate */
+  int32_t fused_levels;    /* expansion: 1 = run consecutive levels in one cooperative launch
+                              while the frontier fits its buffers (grown to at most 2^20 jobs and
+                              2^26 arena words), then one launch per level; 0 = one launch per
+                              level throughout.  The job list is the same either way */
 } perm_opts;
 
 /* Fill opts with the defaults above. */

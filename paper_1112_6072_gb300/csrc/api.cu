@@ -8,6 +8,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -63,19 +65,48 @@ extern "C" void perm_opts_default(perm_opts* o) {
   o->stream = nullptr;
   o->timeout_ns = 0;
   o->model_uses_estimate = 1;
+  o->fused_levels = 1;
 }
 
 // ---------------------------------------------------------------- memory
+// Without a caller allocator, device memory comes from a stream-ordered pool
+// of the library's own (one per device) that keeps up to kPoolKeepBytes of
+// freed memory mapped, so repeated plans do not map and unmap it again.
+static const uint64_t kPoolKeepBytes = 4ull << 30;
+
+static cudaMemPool_t library_pool() {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+  uint64_t keep = kPoolKeepBytes;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  pools[dev] = pool;
+  return pool;
+}
+
 struct Mem {
   perm_opts opts;
   cudaStream_t s;
+  cudaMemPool_t pool = nullptr;
   std::vector<void*> live;
   void* get(size_t bytes) {
     if (bytes == 0) bytes = 16;
     void* p = nullptr;
     if (opts.alloc) {
       p = opts.alloc(bytes, (void*)s, opts.alloc_ctx);
-    } else if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    } else if ((pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s)) !=
+               cudaSuccess) {
       p = nullptr;
     }
     if (p) live.push_back(p);
@@ -180,18 +211,23 @@ struct JobBuf {
 // launches use.  Kept with the job set so the launch sequence can be
 // captured once into a CUDA graph and replayed.
 struct EvalState {
-  std::vector<uint32_t> q, leafq, dfsq;
   int64_t nl = 0, nd = 0, nd_w2 = 0;
   std::vector<std::pair<int64_t, int64_t>> groups;  // (offset, count) in the grouped leaf queue
   std::vector<int32_t> group_cls;
-  uint32_t* d_lq = nullptr;
-  uint32_t* d_dq = nullptr;
+  uint32_t* d_q = nullptr;   // the queue as evaluated
+  uint32_t* d_g = nullptr;   // grouped queue: leaf variants, then depth-first W = 2, W = 4
+  uint32_t* d_lq = nullptr;  // = d_g
+  uint32_t* d_dq = nullptr;  // = d_g + nl
   uint32_t* d_rq = nullptr;  // retry queue
+  int32_t* rflags = nullptr;
+  int32_t* rpos = nullptr;
   uint64_t* counts = nullptr;
   uint64_t* prefix = nullptr;
   void* stmp = nullptr;
   size_t stb = 0;
   unsigned long long* ctr = nullptr;
+  // [0] status summary, [1] [2] retry counts, [3 ..] evaluation key histogram
+  unsigned long long* sum = nullptr;
   int64_t* undo = nullptr;
   int64_t undo_w = 0;
   int tile = 32, wps = 0, chunk = 10;
@@ -224,8 +260,8 @@ static void free_eval(Mem& M, perm_jobs* J) {
   if (E->exec) cudaGraphExecDestroy(E->exec);
   if (E->graph) cudaGraphDestroy(E->graph);
   if (E->cap) cudaStreamDestroy(E->cap);
-  for (void* p : {(void*)E->d_lq, (void*)E->d_dq, (void*)E->d_rq, (void*)E->counts, (void*)E->prefix, E->stmp,
-                  (void*)E->ctr, (void*)E->undo})
+  for (void* p : {(void*)E->d_q, (void*)E->d_g, (void*)E->d_rq, (void*)E->rflags, (void*)E->rpos,
+                  (void*)E->counts, (void*)E->prefix, E->stmp, (void*)E->ctr, (void*)E->sum, (void*)E->undo})
     M.put(p);
   delete E;
   J->ev = nullptr;
@@ -334,6 +370,7 @@ extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, 
   P->s = (cudaStream_t)o.stream;
   P->M.opts = o;
   P->M.s = P->s;
+  if (!o.alloc) P->M.pool = library_pool();
   P->count = count;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -451,6 +488,11 @@ extern "C" void perm_plan_destroy(perm_plan_t* P) {
 
 // ---------------------------------------------------------------- a2, a3: expansion
 static const int64_t kTargetJobs = 1ll << 17;
+// fused (single-launch) expansion buffers: initial and largest capacities
+static const int64_t kFusedJobs0 = 1ll << 15;
+static const int64_t kFusedWords0 = 1ll << 21;
+static const int64_t kFusedMaxJobs = 1ll << 20;
+static const int64_t kFusedMaxWords = 1ll << 26;
 
 extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64_t* njobs) {
   if (!P) return PERM_EINVAL;
@@ -512,12 +554,106 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
   int max_order = maxn;
   int64_t cur_arena_words = (int64_t)P->h_arena.size();  // roots sit back to back
   int64_t used_words = cur_arena_words;                    // words of the current jobs' blocks
-  for (int level = 0; level < maxd && ncur > 0; ++level) {
-    if (adaptive) {
-      const bool big = max_order > PERM_MAX_JOB_N;
-      const bool want_more = ncur < kTargetJobs * std::max<int64_t>(1, nroots) && max_order > P->L;
-      if (!big && !want_more) break;
+  const int64_t target = kTargetJobs * std::max<int64_t>(1, nroots);
+  auto levels_left = [&](int level, int64_t n, int mo) {
+    if (level >= maxd || n <= 0) return false;
+    if (!adaptive) return true;
+    return mo > PERM_MAX_JOB_N || (n < target && mo > P->L);
+  };
+  int level0 = 0;
+  if (P->opts.fused_levels && levels_left(0, ncur, max_order)) {
+    // consecutive levels in one cooperative launch; buffers start small and
+    // grow by 4x (the current level copied over) when the frontier outgrows
+    // them, up to kFusedMaxJobs / kFusedMaxWords
+    int64_t cap_jobs = std::max<int64_t>(kFusedJobs0, 2 * ncur);
+    int64_t cap_words = std::max<int64_t>(kFusedWords0, 2 * used_words);
+    ExpandFrontState* d_state = dget<ExpandFrontState>(M, 1);
+    long long* d_partial = dget<long long>(M, PERM_FRONT_MAX_BLOCKS);
+    unsigned long long* d_bar = dget<unsigned long long>(M, 1);
+    unsigned long long* d_lw = dget<unsigned long long>(M, maxd);
+    int32_t* d_lm = dget<int32_t>(M, maxd);
+    if (!d_state || !d_partial || !d_bar || !d_lw || !d_lm) return PERM_ENOMEM;
+    CK(cudaMemsetAsync(d_lw, 0, 8 * (size_t)maxd, s));
+    CK(cudaMemsetAsync(d_lm, 0, 4 * (size_t)maxd, s));
+    ExpandFrontState S;
+    S.ncur = ncur;
+    S.used_words = used_words;
+    S.level = 0;
+    S.max_order = max_order;
+    S.cb = 0;
+    S.pad = 0;
+    for (;;) {
+      const int ob = S.cb ^ 1;
+      if (!jb[ob].ensure(M, cap_jobs) || !grow(M, ar[ob], 8 * (size_t)cap_words) || !slots.ensure(M, 2 * cap_jobs) ||
+          !grow(M, g_valid, 4 * (size_t)(2 * cap_jobs)))
+        return PERM_ENOMEM;
+      if (jb[S.cb].m.cap < 4 * (size_t)cap_jobs || ar[S.cb].cap < 8 * (size_t)cap_words) {
+        // move the current level into the other (large) buffers
+        const JobArrays src = jb[S.cb].view(), dst = jb[ob].view();
+        CK(cudaMemcpyAsync(dst.m, src.m, 4 * S.ncur, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(dst.nnz, src.nnz, 4 * S.ncur, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(dst.off, src.off, 8 * S.ncur, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(dst.mat, src.mat, 4 * S.ncur, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(dst.depth_left, src.depth_left, 4 * S.ncur, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(dst.coef, src.coef, 32 * S.ncur, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ar[ob].p, ar[S.cb].p, 8 * (size_t)S.used_words, cudaMemcpyDeviceToDevice, s));
+        S.cb = ob;
+        if (!jb[S.cb ^ 1].ensure(M, cap_jobs) || !grow(M, ar[S.cb ^ 1], 8 * (size_t)cap_words))
+          return PERM_ENOMEM;
+      }
+      ExpandFrontArgs F;
+      for (int k = 0; k < 2; ++k) {
+        F.buf[k] = jb[k].view();
+        F.arena[k] = reinterpret_cast<uint64_t*>(ar[k].p);
+      }
+      F.cap_jobs = cap_jobs;
+      F.cap_words = cap_words;
+      F.slots = slots.view();
+      F.valid = reinterpret_cast<int32_t*>(g_valid.p);
+      F.leaf_size = P->L;
+      F.max_levels = maxd;
+      F.adaptive = adaptive ? 1 : 0;
+      F.big_order = PERM_MAX_JOB_N;
+      F.target_jobs = target;
+      F.state = d_state;
+      F.partial = d_partial;
+      F.bar = d_bar;
+      F.lvl_words = d_lw;
+      F.lvl_maxo = d_lm;
+      F.err = reinterpret_cast<int32_t*>(d_stat);
+      CK(cudaMemcpyAsync(d_state, &S, sizeof(S), cudaMemcpyHostToDevice, s));
+      CK(cudaMemsetAsync(d_bar, 0, 8, s));
+      int grid = 0;
+      CK(launch_expand_front(F, S.max_order, &grid, s));
+      if (grid == 0) break;  // no cooperative launch on this device
+      long long st0 = 0;
+      CK(cudaMemcpyAsync(&S, d_state, sizeof(S), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(&st0, d_stat, 8, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      const int32_t herr = (int32_t)(st0 & 0xffffffff);
+      if (herr != 0) return (perm_status)herr;
+      if (!levels_left(S.level, S.ncur, S.max_order)) break;
+      // stopped for room: grow, or hand over to the per-level loop
+      if (cap_jobs >= kFusedMaxJobs || cap_words >= kFusedMaxWords) break;
+      if (2 * S.ncur > cap_jobs) cap_jobs = std::min<int64_t>(kFusedMaxJobs, 4 * cap_jobs);
+      if (2 * S.used_words > cap_words) cap_words = std::min<int64_t>(kFusedMaxWords, 4 * cap_words);
+      if (2 * S.ncur > cap_jobs || 2 * S.used_words > cap_words) break;
     }
+    M.put(d_state);
+    M.put(d_partial);
+    M.put(d_bar);
+    M.put(d_lw);
+    M.put(d_lm);
+    cb = S.cb;
+    cur = jb[cb].view();
+    cur_arena = reinterpret_cast<uint64_t*>(ar[cb].p);
+    ncur = S.ncur;
+    max_order = S.max_order;
+    used_words = S.used_words;
+    cur_arena_words = S.used_words;
+    level0 = S.level;
+  }
+  for (int level = level0; levels_left(level, ncur, max_order); ++level) {
     // every parent reserves two child slots of its own block size
     const int64_t out_words = 2 * used_words;
     const int nb = cb ^ 1;
@@ -717,65 +853,70 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order) {
   cudaStream_t s = P->s;
   Mem& M = P->M;
   const int64_t n = J->n;
+  const int leaf_max = std::max(P->L, 2);
+  if (J->max_order > leaf_max && J->max_order > PERM_MAX_JOB_N) return PERM_EINVAL;
   free_eval(M, J);
   J->ev = new EvalState();
   EvalState& E = *J->ev;
-  std::vector<uint32_t>& q = E.q;
-  q.resize(n);
+  E.d_q = dget<uint32_t>(M, n);
+  E.sum = dget<unsigned long long>(M, 3 + EVAL_KEYS);
+  E.ctr = dget<unsigned long long>(M, 2);
+  if (!E.d_q || !E.sum || !E.ctr) return PERM_ENOMEM;
   if (order) {
     std::vector<uint8_t> seen(n, 0);
     for (int64_t k = 0; k < n; ++k) {
       if (order[k] >= (uint64_t)n || seen[order[k]]) return PERM_EINVAL;
       seen[order[k]] = 1;
-      q[k] = order[k];
     }
+    if (n) CK(cudaMemcpyAsync(E.d_q, order, 4 * n, cudaMemcpyHostToDevice, s));
   } else {
     if (!J->has_order) {
       perm_status st = perm_order(J, P->opts.order, nullptr);
       if (st != PERM_OK) return st;
     }
-    if (n > 0) {
-      CK(cudaMemcpyAsync(q.data(), J->d_queue, 4 * n, cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-    }
+    if (n) CK(cudaMemcpyAsync(E.d_q, J->d_queue, 4 * n, cudaMemcpyDeviceToDevice, s));
   }
-  // leaf-order jobs go to the batched leaf kernel, the rest to the depth-first one
-  std::vector<uint32_t>& leafq = E.leafq;
-  std::vector<uint32_t>& dfsq = E.dfsq;
-  leafq.reserve(n);
-  int dfs_max = 0;
-  for (int64_t k = 0; k < n; ++k) {
-    const int m = J->h_m[q[k]];
-    if (m <= std::max(P->L, 2)) {
-      leafq.push_back(q[k]);
-    } else {
-      dfsq.push_back(q[k]);
-      dfs_max = std::max(dfs_max, m);
-    }
+  // group the queue on the device: leaf jobs by kernel variant, then the
+  // depth-first jobs by ring width, queue order kept inside every group
+  unsigned long long* hist = E.sum + 3;
+  CK(cudaMemsetAsync(hist, 0, 8 * EVAL_KEYS, s));
+  E.d_g = dget<uint32_t>(M, n);
+  uint32_t* keys = dget<uint32_t>(M, 2 * n);
+  uint32_t* vals = dget<uint32_t>(M, n);
+  const size_t sort_b = sort_tmp_bytes_u32(std::max<int64_t>(n, 1), 7);
+  void* sort_tmp = M.get(sort_b);
+  if (!E.d_g || !keys || !vals || !sort_tmp) return PERM_ENOMEM;
+  std::vector<unsigned long long> h(EVAL_KEYS, 0ull);
+  if (n) {
+    CK(launch_eval_keys(E.d_q, n, J->a, J->arena, P->d_mat_w, leaf_max, keys, vals, hist, s));
+    CK(sort_asc_u32(keys, keys + n, vals, E.d_g, n, 7, sort_tmp, sort_b, s));
+    CK(cudaMemcpyAsync(h.data(), hist, 8 * EVAL_KEYS, cudaMemcpyDeviceToHost, s));
   }
-  if (dfs_max > PERM_MAX_JOB_N) return PERM_EINVAL;
-  // depth-first queue grouped by ring width, queue order kept inside each group
-  int64_t nd_w2 = 0;
-  {
-    std::vector<uint32_t> g2, g4;
-    for (uint32_t j : dfsq) (P->w[J->h_mat[j]] == 4 ? g4 : g2).push_back(j);
-    nd_w2 = (int64_t)g2.size();
-    g2.insert(g2.end(), g4.begin(), g4.end());
-    dfsq.swap(g2);
+  M.put(keys);
+  M.put(vals);
+  M.put(sort_tmp);
+  CK(cudaStreamSynchronize(s));
+  int64_t nl = 0;
+  for (int k = 0; k < EVAL_KEY_DFS; ++k) {
+    if (h[k] == 0) continue;
+    E.groups.push_back({nl, (int64_t)h[k]});
+    E.group_cls.push_back(k);
+    nl += (int64_t)h[k];
   }
-  const int64_t nl = (int64_t)leafq.size(), nd = (int64_t)dfsq.size();
   E.nl = nl;
-  E.nd = nd;
-  E.nd_w2 = nd_w2;
-  uint32_t* d_lq = E.d_lq = dget<uint32_t>(M, nl);
-  uint32_t* d_dq = E.d_dq = dget<uint32_t>(M, nd);
-  E.d_rq = dget<uint32_t>(M, nd);
+  E.nd_w2 = (int64_t)h[EVAL_KEY_DFS];
+  E.nd = E.nd_w2 + (int64_t)h[EVAL_KEY_DFS + 1];
+  E.d_lq = E.d_g;
+  E.d_dq = E.d_g + nl;
+  const int64_t nd = E.nd;
   E.counts = dget<uint64_t>(M, nl + 1);
   E.prefix = dget<uint64_t>(M, nl + 1);
-  E.stb = scan_tmp_bytes_u64(nl + 1);
+  E.stb = std::max(scan_tmp_bytes_u64(nl + 1), scan_tmp_bytes_i32(nd + 1));
   E.stmp = M.get(E.stb);
-  E.ctr = dget<unsigned long long>(M, 2);
-  E.tile = dfs_max <= 32 ? 32 : 64;
+  E.d_rq = dget<uint32_t>(M, nd);
+  E.rflags = dget<int32_t>(M, nd + 1);
+  E.rpos = dget<int32_t>(M, nd + 1);
+  E.tile = J->max_order <= 32 ? 32 : 64;
   // the narrow variant (int32 tile, leaves <= 16 rows) unless the leaf order needs the wide one
   E.wide_first = P->L > 16;
   E.wps = P->opts.workers_per_sm > 0 ? P->opts.workers_per_sm : (E.tile <= 32 ? 24 : 10);
@@ -787,37 +928,8 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order) {
   }
   E.undo_w = dfs_undo_words(E.tile);
   E.undo = nd > 0 ? dget<int64_t>(M, E.undo_w * dfs_warps) : nullptr;
-  if (!d_lq || !d_dq || !E.d_rq || !E.counts || !E.prefix || !E.stmp || !E.ctr || (nd > 0 && !E.undo))
+  if (!E.counts || !E.prefix || !E.stmp || !E.d_rq || !E.rflags || !E.rpos || (nd > 0 && !E.undo))
     return PERM_ENOMEM;
-  if (nd) CK(cudaMemcpyAsync(d_dq, dfsq.data(), 4 * nd, cudaMemcpyHostToDevice, s));
-  // leaf variants: classify on the device, then group stably by variant
-  std::vector<std::pair<int64_t, int64_t>>& groups = E.groups;
-  std::vector<int32_t>& group_cls = E.group_cls;
-  if (nl) {
-    int32_t* d_cls = dget<int32_t>(M, nl);
-    if (!d_cls) return PERM_ENOMEM;
-    std::vector<int32_t> cls(nl);
-    CK(cudaMemcpyAsync(d_lq, leafq.data(), 4 * nl, cudaMemcpyHostToDevice, s));
-    CK(launch_leaf_classify(d_lq, nl, J->a, J->arena, P->d_mat_w, d_cls, s));
-    CK(cudaMemcpyAsync(cls.data(), d_cls, 4 * nl, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    M.put(d_cls);
-    std::vector<int32_t> distinct(cls.begin(), cls.end());
-    std::sort(distinct.begin(), distinct.end());
-    distinct.erase(std::unique(distinct.begin(), distinct.end()), distinct.end());
-    std::vector<uint32_t> grouped;
-    grouped.reserve(nl);
-    for (int32_t c : distinct) {
-      const int64_t start = (int64_t)grouped.size();
-      for (int64_t k = 0; k < nl; ++k)
-        if (cls[k] == c) grouped.push_back(leafq[k]);
-      groups.push_back({start, (int64_t)grouped.size() - start});
-      group_cls.push_back(c);
-    }
-    leafq.swap(grouped);
-    CK(cudaMemcpyAsync(d_lq, leafq.data(), 4 * nl, cudaMemcpyHostToDevice, s));
-  }
-  CK(cudaStreamSynchronize(s));
   return PERM_OK;
 }
 
@@ -846,6 +958,7 @@ static cudaError_t eval_enqueue(perm_jobs* J, cudaStream_t s) {
   EvalState& E = *J->ev;
   const int64_t nj = std::max<int64_t>(J->n, 1);
   cudaError_t e;
+  int launches = 0;
 #define EQ(call)                          \
   do {                                    \
     if ((e = (call)) != cudaSuccess) return e; \
@@ -859,6 +972,7 @@ static cudaError_t eval_enqueue(perm_jobs* J, cudaStream_t s) {
   EQ(cudaMemsetAsync(J->out.nodes, 0, 8 * nj, s));
   EQ(cudaMemsetAsync(P->d_mat_acc, 0, 32ull * P->count, s));
   EQ(cudaMemsetAsync(E.ctr, 0, 16, s));
+  EQ(cudaMemsetAsync(E.sum, 0xff, 8, s));
   if (E.nd > 0) {
     // ring width 2 then 4; each launch has its own job counter
     DfsArgs D = dfs_args(J);
@@ -867,22 +981,39 @@ static cudaError_t eval_enqueue(perm_jobs* J, cudaStream_t s) {
     D.nq = E.nd - E.nd_w2;
     D.job_counter = E.ctr;
     EQ(launch_dfs(D, E.tile, E.wide_first, 4, P->sms, E.wps, s));
+    launches += 2;
   }
   if (E.nl > 0) {
-    // one persistent grid per kernel variant, queue order kept inside each variant
-    for (size_t g = 0; g < E.groups.size(); ++g)
-      EQ(launch_leaf_batch(E.d_lq + E.groups[g].first, E.groups[g].second, E.group_cls[g], J->a, J->arena, E.chunk,
-                           E.counts, E.prefix, E.stmp, E.stb, E.ctr, J->out, P->sms, s));
+    // one task scan for the grouped leaf queue, then one persistent grid per
+    // kernel variant over its slice
+    EQ(launch_leaf_tasks(E.d_lq, E.nl, J->a, E.chunk, E.counts, E.prefix, E.stmp, E.stb, s));
+    launches += 3;
+    for (size_t g = 0; g < E.groups.size(); ++g) {
+      const int64_t o = E.groups[g].first;
+      EQ(launch_leaf_batch(E.d_lq + o, E.groups[g].second, E.group_cls[g], E.prefix + o, J->a, J->arena, E.chunk,
+                           E.ctr, J->out, P->sms, s));
+      ++launches;
+    }
     EQ(launch_leaf_finalize(E.d_lq, E.nl, J->a, J->out, P->d_mat_acc, s));
+    ++launches;
+  }
+  if (E.nd > 0 && !E.wide_first) {
+    // jobs the narrow depth-first variant handed on, for the wide one
+    EQ(launch_retry_collect(E.d_dq, E.nd, E.nd_w2, J->out.status, E.rflags, E.rpos, E.stmp, E.stb, E.d_rq,
+                            E.sum + 1, s));
+    launches += 4;
+  }
+  if (J->n > 0) {
+    EQ(launch_status_summary(J->out.status, J->n, E.sum, s));
+    ++launches;
   }
 #undef EQ
-  // per leaf group: task counts, two scan kernels, the batch; plus finalize and the depth-first grids
-  P->last_launches = (int32_t)(4 * E.groups.size() + (E.nl > 0 ? 1 : 0) + (E.nd > 0 ? 2 : 0));
+  P->last_launches = launches;
   return cudaSuccess;
 }
 
-// finish: wait, re-run jobs the narrow depth-first variant handed on, read
-// statuses and (optionally) the per-job records.
+// finish: wait, re-run jobs the narrow depth-first variant handed on, and
+// read the status summary and (optionally) the per-job records.
 static perm_status eval_finish(perm_jobs* J, perm_job_result* results) {
   perm_plan* P = J->plan;
   EvalState& E = *J->ev;
@@ -890,52 +1021,46 @@ static perm_status eval_finish(perm_jobs* J, perm_job_result* results) {
   const int64_t n = J->n;
   CK(cudaEventSynchronize(P->ev1));
   CK(cudaEventElapsedTime(&P->last_ms, P->ev0, P->ev1));
-  std::vector<int32_t> st(n);
-  if (n) CK(cudaMemcpyAsync(st.data(), J->out.status, 4 * n, cudaMemcpyDeviceToHost, s));
+  unsigned long long sum[3] = {~0ull, 0ull, 0ull};
+  if (n) CK(cudaMemcpyAsync(sum, E.sum, sizeof(sum), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (E.nd > 0 && !E.wide_first) {
-    // jobs the narrow depth-first variant could not hold run again on the wide one
-    std::vector<uint32_t> retry;
-    int64_t nr2 = 0;
-    for (int64_t k = 0; k < E.nd; ++k)
-      if (st[E.dfsq[k]] == DFS_RETRY) {
-        retry.push_back(E.dfsq[k]);
-        if (k < E.nd_w2) ++nr2;
-      }
-    if (!retry.empty()) {
-      const int64_t nr = (int64_t)retry.size();
-      CK(cudaMemcpyAsync(E.d_rq, retry.data(), 4 * nr, cudaMemcpyHostToDevice, s));
-      CK(cudaMemsetAsync(E.ctr, 0, 16, s));
-      float ms2 = 0.f;
-      DfsArgs D = dfs_args(J);
-      CK(cudaEventRecord(P->ev0, s));
-      D.queue = E.d_rq;
-      D.nq = nr2;
-      CK(launch_dfs(D, E.tile, true, 2, P->sms, E.wps, s));
-      D.queue = E.d_rq + nr2;
-      D.nq = nr - nr2;
-      D.job_counter = E.ctr;
-      CK(launch_dfs(D, E.tile, true, 4, P->sms, E.wps, s));
-      CK(cudaEventRecord(P->ev1, s));
-      CK(cudaEventSynchronize(P->ev1));
-      CK(cudaEventElapsedTime(&ms2, P->ev0, P->ev1));
-      P->last_ms += ms2;
-      P->last_launches += 2;
-      CK(cudaMemcpyAsync(st.data(), J->out.status, 4 * n, cudaMemcpyDeviceToHost, s));
-    }
+  if (n && E.nd > 0 && !E.wide_first && sum[2] > 0) {
+    const int64_t nr2 = (int64_t)sum[1], nr = (int64_t)sum[2];
+    CK(cudaMemsetAsync(E.ctr, 0, 16, s));
+    float ms2 = 0.f;
+    DfsArgs D = dfs_args(J);
+    CK(cudaEventRecord(P->ev0, s));
+    D.queue = E.d_rq;
+    D.nq = nr2;
+    CK(launch_dfs(D, E.tile, true, 2, P->sms, E.wps, s));
+    D.queue = E.d_rq + nr2;
+    D.nq = nr - nr2;
+    D.job_counter = E.ctr;
+    CK(launch_dfs(D, E.tile, true, 4, P->sms, E.wps, s));
+    CK(cudaEventRecord(P->ev1, s));
+    CK(cudaMemsetAsync(E.sum, 0xff, 8, s));
+    CK(launch_status_summary(J->out.status, n, E.sum, s));
+    CK(cudaMemcpyAsync(sum, E.sum, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventSynchronize(P->ev1));
+    CK(cudaEventElapsedTime(&ms2, P->ev0, P->ev1));
+    CK(cudaStreamSynchronize(s));
+    P->last_ms += ms2;
+    P->last_launches += 3;
   }
-  const std::vector<uint32_t>& q = E.q;
   if (results && n) {
     std::vector<unsigned long long> acc(4 * n), t0(n), t1(n), lv(n), nd_(n);
-    std::vector<int32_t> sm(n), mat(n), nnz(n);
+    std::vector<int32_t> sm(n), mat(n), nnz(n), st(n);
+    std::vector<uint32_t> q(n);
     CK(cudaMemcpyAsync(acc.data(), J->out.acc, 32 * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(t0.data(), J->out.t_start, 8 * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(t1.data(), J->out.t_end, 8 * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(lv.data(), J->out.leaves, 8 * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(nd_.data(), J->out.nodes, 8 * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(sm.data(), J->out.sm, 4 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(st.data(), J->out.status, 4 * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(mat.data(), J->a.mat, 4 * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(nnz.data(), J->a.nnz, 4 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(q.data(), E.d_q, 4 * n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     std::vector<int32_t> qpos(n);
     for (int64_t k = 0; k < n; ++k) qpos[q[k]] = (int32_t)k;
@@ -954,9 +1079,8 @@ static perm_status eval_finish(perm_jobs* J, perm_job_result* results) {
       r.nodes = (int64_t)nd_[j];
     }
   }
-  CK(cudaStreamSynchronize(s));
-  for (int64_t j = 0; j < n; ++j)
-    if (st[j] != 0) return (perm_status)st[j];
+  // the lowest job index with a failed status decides the call's status
+  if (sum[0] != ~0ull) return (perm_status)(sum[0] & 255);
   P->evaluated = true;
   return PERM_OK;
 }

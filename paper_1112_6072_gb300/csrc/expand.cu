@@ -1,11 +1,12 @@
-// K1: one level of Algorithm PH, Step 2 (Section 2.2) -- every parent job is
-// divided by Eq. 2 into at most two children, written in compact CSR.
+// K1: Algorithm PH, Step 2 (Section 2.2) -- every parent job is divided by
+// Eq. 2 into at most two children, written in compact CSR.
 //
-// One warp per parent.  The parent is scattered into a dense tile in shared
-// memory (order <= TILE); lanes own rows and columns.  The pivot is the line
-// with the fewest nonzeros (Algorithm H_per, Step 1), lowest row first, else
-// lowest column.  With the pivot line's nonzeros at positions j1 < j2 < j3 <
-// j4 and values a, b, c, d, the children are, in order:
+// One warp per parent; lane l owns the parent rows l, l+32, ... and builds
+// the child rows from the parent's sparse rows directly (work per child is
+// proportional to its nonzeros, not to m^2).  The pivot is the line with the
+// fewest nonzeros (Algorithm H_per, Step 1), lowest row first, else lowest
+// column.  With the pivot line's nonzeros at positions j1 < j2 < j3 < j4 and
+// values a, b, c, d, the children are, in order:
 //   k = 1: a * minor(j1)
 //   k = 2: merge(j1, j2)
 //   k = 3: merge(j1, j2), c * minor(j3)
@@ -16,6 +17,15 @@
 // child's coefficient.  Children holding a zero line are not emitted.  A
 // parent of order <= max(L, 2), with s >= 5, or with no levels left is
 // carried unchanged to slot 2p.
+//
+// Two drivers share the per-parent routine:
+//  - k_expand_level: one level per launch; the host reserves two blocks of
+//    the parent's size per parent (scan of capacities) and compacts after.
+//  - k_expand_front: a cooperative launch that runs consecutive levels while
+//    the frontier fits fixed buffers; blocks meet at a bounded grid barrier
+//    twice per level, children's blocks are bump-allocated in the arena, and
+//    each block compacts its own contiguous range of slots, so the natural
+//    (breadth-first) order of the jobs is the same as with k_expand_level.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -25,14 +35,15 @@
 
 namespace {
 
-template <int TILE>
-struct ExpandCfg {
-  static constexpr int STRIDE = TILE + 1;  // int64 words per tile row (odd: fewer bank conflicts)
-  static constexpr int MW = TILE > 64 ? 2 : 1;  // 64-bit mask words per line
-  static constexpr int WARPS = TILE >= 128 ? 1 : (TILE >= 64 ? 3 : 8);
-  static constexpr size_t TILE_BYTES = sizeof(int64_t) * TILE * STRIDE;
-  static constexpr size_t SMEM = WARPS * TILE_BYTES;
-};
+constexpr int kLevelWarps = 8;   // warps per block, k_expand_level
+constexpr int kFrontWarps = 16;  // warps per block, k_expand_front
+constexpr int kFrontThreads = kFrontWarps * 32;
+constexpr int64_t kBarrierTimeoutNs = 10ll * 1000 * 1000 * 1000;
+// words of a warp's shared-memory copy of its parent's CSR block (larger
+// blocks are read from global memory)
+constexpr int kStageWords = 1024;
+constexpr size_t kLevelSmem = sizeof(uint64_t) * kStageWords * kLevelWarps;
+constexpr size_t kFrontSmem = sizeof(uint64_t) * kStageWords * kFrontWarps;
 
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
 #pragma unroll
@@ -64,107 +75,77 @@ __device__ __forceinline__ bool mad2_checked(int64_t a, int64_t x, int64_t b, in
 struct ChildSpec {
   int del_row, del_col;
   int merge;      // 0 none, 1 column p merged (row pivot), 2 row p merged (column pivot)
-  int p, q;       // merged line and its partner (deleted)
+  int p, q;       // merged line and its partner (deleted), p < q
   int64_t a, b;   // merged line = a * line_q + b * line_p
   int64_t fac;    // scalar factor (minor)
 };
 
-template <int TILE>
-__device__ void write_child(const int64_t* T, int m, const ChildSpec& cs, int lane, uint64_t* blk,
-                            int& nnz_out, bool& keep, int32_t* err) {
-  constexpr int S = ExpandCfg<TILE>::STRIDE;
-  constexpr int MW = ExpandCfg<TILE>::MW;
-  constexpr int RPL = (TILE + 31) / 32;  // child rows per lane
-  const int mc = m - 1;
-  int cnt[RPL];
-  uint64_t colmask[MW];
-#pragma unroll
-  for (int w = 0; w < MW; ++w) colmask[w] = 0;
-  bool ovf = false;
-  // pass 1: row lengths and the union of nonzero columns
-#pragma unroll
-  for (int k = 0; k < RPL; ++k) {
-    const int rc = lane + 32 * k;  // child row
-    cnt[k] = 0;
-    if (rc < mc) {
-      const int r = rc + (rc >= cs.del_row);
-      int cc = 0;
-      for (int c = 0; c < m; ++c) {
-        if (c == cs.del_col) continue;
-        int64_t v = T[r * S + c];
-        if (cs.merge == 1 && c == cs.p) {
-          if (!mad2_checked(cs.a, T[r * S + cs.q], cs.b, v, v)) ovf = true;
-        } else if (cs.merge == 2 && r == cs.p) {
-          if (!mad2_checked(cs.a, T[cs.q * S + c], cs.b, v, v)) ovf = true;
-        }
-        if (v != 0) {
-          cnt[k]++;
-          colmask[cc >> 6] |= 1ull << (cc & 63);
-        }
-        ++cc;
+// The nonzeros of one child row (parent row r), in ascending child column
+// order, passed to emit(col, value).  False on int64 overflow.
+template <class F>
+__device__ __forceinline__ bool child_row(const CsrView& v, const ChildSpec& cs, int r, F&& emit) {
+  const int b = v.rowptr[r], e = v.rowptr[r + 1];
+  bool ok = true;
+  if (cs.merge == 1) {
+    int64_t xp = 0, xq = 0;
+    for (int t = b; t < e; ++t) {
+      const int c = v.col[t];
+      if (c == cs.p) xp = v.val[t];
+      if (c == cs.q) xq = v.val[t];
+    }
+    int64_t mv;
+    ok = mad2_checked(cs.a, xq, cs.b, xp, mv);
+    bool done = false;
+    for (int t = b; t < e; ++t) {
+      const int c = v.col[t];
+      if (!done && c >= cs.p) {
+        if (mv != 0) emit(cs.p, mv);
+        done = true;
+        if (c == cs.p) continue;
       }
+      if (c == cs.q) continue;
+      emit(c - (c > cs.q), v.val[t]);
+    }
+    if (!done && mv != 0) emit(cs.p, mv);
+  } else if (cs.merge == 2 && r == cs.p) {
+    const int bq = v.rowptr[cs.q], eq = v.rowptr[cs.q + 1];
+    int i = b, j = bq;
+    while (i < e || j < eq) {
+      const int ci = i < e ? v.col[i] : 0x7fffffff;
+      const int cj = j < eq ? v.col[j] : 0x7fffffff;
+      const int c = ci < cj ? ci : cj;
+      const int64_t xp = ci == c ? v.val[i++] : 0;
+      const int64_t xq = cj == c ? v.val[j++] : 0;
+      if (c == cs.del_col) continue;
+      int64_t mv;
+      if (!mad2_checked(cs.a, xq, cs.b, xp, mv)) ok = false;
+      if (mv != 0) emit(c - (c > cs.del_col), mv);
+    }
+  } else {
+    for (int t = b; t < e; ++t) {
+      const int c = v.col[t];
+      if (c == cs.del_col) continue;
+      emit(c - (c > cs.del_col), v.val[t]);
     }
   }
-#pragma unroll
-  for (int w = 0; w < MW; ++w) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) colmask[w] |= __shfl_xor_sync(0xffffffffu, colmask[w], d);
-  }
-  bool zero_row = false;
-#pragma unroll
-  for (int k = 0; k < RPL; ++k)
-    if (lane + 32 * k < mc && cnt[k] == 0) zero_row = true;
-  zero_row = __any_sync(0xffffffffu, zero_row);
-  ovf = __any_sync(0xffffffffu, ovf);
-  int ncols = 0;
-#pragma unroll
-  for (int w = 0; w < MW; ++w) ncols += __popcll(colmask[w]);
-  if (ovf && lane == 0) atomicCAS(err, 0, PERM_EOVERFLOW);
-  keep = !ovf && !zero_row && ncols == mc;
-  if (!keep) {
-    nnz_out = 0;
-    return;
-  }
-  // row offsets: lanes hold rows lane, lane+32, ...; scan in row order
-  int base = 0;
-  int offs[RPL];
-#pragma unroll
-  for (int k = 0; k < RPL; ++k) {
-    int tot;
-    offs[k] = base + warp_excl_scan(cnt[k], lane, tot);
-    base += tot;
-  }
-  nnz_out = base;
-  uint16_t* rowptr = reinterpret_cast<uint16_t*>(blk);
-  uint8_t* col = reinterpret_cast<uint8_t*>(blk + blk_rp_words(mc));
-  int64_t* val = reinterpret_cast<int64_t*>(blk + blk_rp_words(mc) + blk_col_words(base));
-  if (lane == 0) rowptr[mc] = (uint16_t)base;
-  // pass 2: write rows
-#pragma unroll
-  for (int k = 0; k < RPL; ++k) {
-    const int rc = lane + 32 * k;
-    if (rc < mc) {
-      const int r = rc + (rc >= cs.del_row);
-      rowptr[rc] = (uint16_t)offs[k];
-      int o = offs[k];
-      int cc = 0;
-      for (int c = 0; c < m; ++c) {
-        if (c == cs.del_col) continue;
-        int64_t v = T[r * S + c];
-        if (cs.merge == 1 && c == cs.p)
-          mad2_checked(cs.a, T[r * S + cs.q], cs.b, v, v);
-        else if (cs.merge == 2 && r == cs.p)
-          mad2_checked(cs.a, T[cs.q * S + c], cs.b, v, v);
-        if (v != 0) {
-          col[o] = (uint8_t)cc;
-          val[o] = v;
-          ++o;
-        }
-        ++cc;
-      }
-    }
-  }
+  return ok;
 }
+
+// Where children's blocks go: reserved (cbase + c * parent words) or
+// bump-allocated from a per-level counter.
+struct ExpandCtx {
+  JobArrays parent;
+  const uint64_t* arena_in;
+  JobArrays child;  // slots
+  uint64_t* arena_out;
+  const int64_t* child_off_base;  // reserved mode, else null
+  unsigned long long* bump;       // bump mode: words used in arena_out
+  int64_t cap_words;              // bump mode: arena_out capacity
+  int32_t* max_order;             // bump mode: largest kept order
+  int32_t* valid;
+  int32_t leaf_size;
+  int32_t* err;
+};
 
 __device__ __forceinline__ void copy_words(uint64_t* dst, const uint64_t* src, int64_t words, int lane) {
   // blocks start on 16 bytes and hold an even number of words
@@ -173,165 +154,472 @@ __device__ __forceinline__ void copy_words(uint64_t* dst, const uint64_t* src, i
   for (int64_t k = lane; k < words / 2; k += 32) d4[k] = s4[k];
 }
 
-template <int TILE>
-__global__ void __launch_bounds__(ExpandCfg<TILE>::WARPS * 32) k_expand_level(ExpandLevelArgs A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int S = ExpandCfg<TILE>::STRIDE;
-  constexpr int MW = ExpandCfg<TILE>::MW;
-  constexpr int RPL = (TILE + 31) / 32;
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  int64_t* T = reinterpret_cast<int64_t*>(smem_raw) + (size_t)wib * TILE * S;
-  const int64_t nwarps = (int64_t)gridDim.x * ExpandCfg<TILE>::WARPS;
-  for (int64_t p = (int64_t)blockIdx.x * ExpandCfg<TILE>::WARPS + wib; p < A.np; p += nwarps) {
-    __syncwarp();  // the previous parent's tile reads are done
-    const int m = A.parent.m[p];
-    const int nnz = A.parent.nnz[p];
-    const int64_t off = A.parent.off[p];
-    const int dl = A.parent.depth_left[p];
-    const int64_t pw = blk_words(m, nnz);
-    const int64_t cbase = A.child_off_base[p];
-    CsrView v = csr_view(A.arena_in, off, m, nnz);
-    // dense tile and line counts
-    for (int k = lane; k < m * S; k += 32) T[k] = 0;
-    __syncwarp();
-    int rcount[RPL];
+// Offset of a child's block: lane 0 allocates, the warp gets it back.  -1 if
+// the arena is full (bump mode; the caller's capacity rule excludes it).
+__device__ __forceinline__ int64_t child_block(const ExpandCtx& X, int64_t p, int c, int64_t pw, int64_t words,
+                                               int lane) {
+  if (X.child_off_base) return X.child_off_base[p] + c * pw;
+  unsigned long long o = 0;
+  if (lane == 0) o = atomicAdd(X.bump, (unsigned long long)words);
+  o = __shfl_sync(0xffffffffu, o, 0);
+  if ((int64_t)o + words > X.cap_words) {
+    if (lane == 0) atomicCAS(X.err, 0, PERM_ENOMEM);
+    return -1;
+  }
+  return (int64_t)o;
+}
+
+// Divide parent p (one warp).  ccnt: the warp's shared-memory column counts
+// (RPL * 32 entries); stage: its kStageWords-word copy of the parent block.
+template <int RPL>
+__device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* ccnt, uint64_t* stage) {
+  const int m = X.parent.m[p];
+  const int nnz = X.parent.nnz[p];
+  const int64_t off = X.parent.off[p];
+  const int dl = X.parent.depth_left[p];
+  const int64_t pw = blk_words(m, nnz);
+  __syncwarp();  // the previous parent's reads of stage and ccnt are done
+  const uint64_t* src = X.arena_in + off;
+  if (pw <= kStageWords) {
+    copy_words(stage, src, pw, lane);
+    src = stage;
+  }
+  // line counts: rows from rowptr, columns by shared-memory atomics
+  for (int c = lane; c < m; c += 32) ccnt[c] = 0;
+  __syncwarp();
+  const CsrView v = csr_view(src, 0, m, nnz);
+  unsigned long long key = ~0ull;
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) {
+    const int r = lane + 32 * k;
+    if (r < m) {
+      const int b = v.rowptr[r], e = v.rowptr[r + 1];
+      key = min(key, ((unsigned long long)(e - b) << 17) | (unsigned long long)r);
+      for (int t = b; t < e; ++t) atomicAdd(&ccnt[v.col[t]], 1);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) {
+    const int c = lane + 32 * k;
+    if (c < m) key = min(key, ((unsigned long long)ccnt[c] << 17) | (1ull << 16) | (unsigned long long)c);
+  }
+  __syncwarp();  // counts read before the next parent clears them
+  key = warp_min_u64(key);
+  const int s = (int)(key >> 17);
+  const bool is_col = (key >> 16) & 1;
+  const int idx = (int)(key & 0xffff);
+  const int cut = X.leaf_size > 2 ? X.leaf_size : 2;
+  if (s == 0) {  // zero line: nothing to emit
+    if (lane == 0) X.valid[2 * p] = X.valid[2 * p + 1] = 0;
+    return;
+  }
+  if (dl <= 0 || m <= cut || s >= 5) {
+    const int64_t o = child_block(X, p, 0, pw, pw, lane);
+    if (o >= 0) copy_words(X.arena_out + o, src, pw, lane);
+    if (lane == 0) {
+      const int64_t c0 = 2 * p;
+      X.valid[c0] = o >= 0 ? 1 : 0;
+      X.valid[c0 + 1] = 0;
+      if (o >= 0) {
+        X.child.m[c0] = m;
+        X.child.nnz[c0] = nnz;
+        X.child.off[c0] = o;
+        X.child.mat[c0] = X.parent.mat[p];
+        X.child.depth_left[c0] = 0;
+        for (int w = 0; w < 4; ++w) X.child.coef[4 * c0 + w] = X.parent.coef[4 * p + w];
+        if (X.max_order) atomicMax(X.max_order, m);
+      }
+    }
+    return;
+  }
+  // pivot line's nonzero positions (ascending) and values
+  int pos[4];
+  int64_t pv[4];
+  if (!is_col) {
+    const int b = v.rowptr[idx];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      pos[k] = k < s ? v.col[b + k] : 0;
+      pv[k] = k < s ? v.val[b + k] : 0;
+    }
+  } else {
+    int n = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      pos[k] = 0;
+      pv[k] = 0;
+    }
 #pragma unroll
     for (int k = 0; k < RPL; ++k) {
       const int r = lane + 32 * k;
-      rcount[k] = 0;
+      int64_t x = 0;
       if (r < m) {
         const int b = v.rowptr[r], e = v.rowptr[r + 1];
-        rcount[k] = e - b;
-        for (int q = b; q < e; ++q) T[r * S + v.col[q]] = v.val[q];
+        for (int t = b; t < e; ++t)
+          if (v.col[t] == idx) x = v.val[t];
       }
-    }
-    __syncwarp();
-    unsigned long long key = ~0ull;
+      unsigned bal = __ballot_sync(0xffffffffu, x != 0);
+      while (bal) {
+        const int l = __ffs(bal) - 1;
+        bal &= bal - 1;
+        const long long xv = __shfl_sync(0xffffffffu, (long long)x, l);
 #pragma unroll
-    for (int k = 0; k < RPL; ++k) {
-      const int r = lane + 32 * k;
-      if (r < m) key = min(key, ((unsigned long long)rcount[k] << 17) | (unsigned long long)r);
-    }
-#pragma unroll
-    for (int k = 0; k < RPL; ++k) {
-      const int c = lane + 32 * k;
-      if (c < m) {
-        int cnt = 0;
-        for (int r = 0; r < m; ++r) cnt += T[r * S + c] != 0;
-        key = min(key, ((unsigned long long)cnt << 17) | (1ull << 16) | (unsigned long long)c);
-      }
-    }
-    key = warp_min_u64(key);
-    const int s = (int)(key >> 17);
-    const bool is_col = (key >> 16) & 1;
-    const int idx = (int)(key & 0xffff);
-    const int cut = A.leaf_size > 2 ? A.leaf_size : 2;
-    uint64_t* out0 = A.arena_out + cbase;
-    if (s == 0) {  // zero line: nothing to emit
-      if (lane == 0) A.valid[2 * p] = A.valid[2 * p + 1] = 0;
-      continue;
-    }
-    if (dl <= 0 || m <= cut || s >= 5) {
-      copy_words(out0, A.arena_in + off, pw, lane);
-      if (lane == 0) {
-        const int64_t c0 = 2 * p;
-        A.child.m[c0] = m;
-        A.child.nnz[c0] = nnz;
-        A.child.off[c0] = cbase;
-        A.child.mat[c0] = A.parent.mat[p];
-        A.child.depth_left[c0] = 0;
-        for (int w = 0; w < 4; ++w) A.child.coef[4 * c0 + w] = A.parent.coef[4 * p + w];
-        A.valid[c0] = 1;
-        A.valid[c0 + 1] = 0;
-      }
-      continue;
-    }
-    // pivot line's nonzero positions (ascending) and values
-    int pos[4];
-    int64_t pv[4];
-    {
-      int k = 0;
-      for (int t = 0; t < m && k < 4; ++t) {
-        int64_t x = is_col ? T[t * S + idx] : T[idx * S + t];
-        if (x != 0) {
-          pos[k] = t;
-          pv[k] = x;
-          ++k;
-        }
-      }
-    }
-    u256 pcoef;
-    for (int w = 0; w < 4; ++w) pcoef.w[w] = A.parent.coef[4 * p + w];
-    for (int c = 0; c < 2; ++c) {
-      const int64_t slot = 2 * p + c;
-      ChildSpec cs;
-      cs.fac = 1;
-      cs.merge = 0;
-      cs.p = cs.q = 0;
-      cs.a = cs.b = 0;
-      bool exists = true;
-      int kind = 0;  // 1 merge(pos[x], pos[x+1]), 2 minor(pos[x])
-      int x = 0;
-      if (c == 0) {
-        kind = s == 1 ? 2 : 1;
-        x = 0;
-      } else if (s == 3) {
-        kind = 2;
-        x = 2;
-      } else if (s == 4) {
-        kind = 1;
-        x = 2;
-      } else {
-        exists = false;
-      }
-      bool keep = false;
-      int cnnz = 0;
-      if (exists) {
-        if (!is_col) {
-          cs.del_row = idx;
-          if (kind == 1) {
-            cs.merge = 1;
-            cs.p = pos[x];
-            cs.q = pos[x + 1];
-            cs.a = pv[x];
-            cs.b = pv[x + 1];
-            cs.del_col = cs.q;
-          } else {
-            cs.del_col = pos[x];
-            cs.fac = pv[x];
+        for (int u = 0; u < 4; ++u)
+          if (u == n) {
+            pos[u] = l + 32 * k;
+            pv[u] = xv;
           }
-        } else {
-          cs.del_col = idx;
-          if (kind == 1) {
-            cs.merge = 2;
-            cs.p = pos[x];
-            cs.q = pos[x + 1];
-            cs.a = pv[x];
-            cs.b = pv[x + 1];
-            cs.del_row = cs.q;
-          } else {
-            cs.del_row = pos[x];
-            cs.fac = pv[x];
-          }
-        }
-        write_child<TILE>(T, m, cs, lane, out0 + c * pw, cnnz, keep, A.err);
-      }
-      if (lane == 0) {
-        A.valid[slot] = keep ? 1 : 0;
-        if (keep) {
-          A.child.m[slot] = m - 1;
-          A.child.nnz[slot] = cnnz;
-          A.child.off[slot] = cbase + c * pw;
-          A.child.mat[slot] = A.parent.mat[p];
-          A.child.depth_left[slot] = dl - 1;
-          u256 cc = cs.fac == 1 ? pcoef : u256_mul_s64(pcoef, cs.fac);
-          for (int w = 0; w < 4; ++w) A.child.coef[4 * slot + w] = cc.w[w];
-        }
+        ++n;
       }
     }
-    __syncwarp();
   }
+  u256 pcoef;
+  for (int w = 0; w < 4; ++w) pcoef.w[w] = X.parent.coef[4 * p + w];
+  const int mc = m - 1;
+  for (int c = 0; c < 2; ++c) {
+    const int64_t slot = 2 * p + c;
+    int kind;  // 1 merge(pos[x], pos[x+1]), 2 minor(pos[x])
+    int x;
+    if (c == 0) {
+      kind = s == 1 ? 2 : 1;
+      x = 0;
+    } else if (s == 3) {
+      kind = 2;
+      x = 2;
+    } else if (s == 4) {
+      kind = 1;
+      x = 2;
+    } else {
+      if (lane == 0) X.valid[slot] = 0;
+      continue;
+    }
+    ChildSpec cs;
+    cs.fac = 1;
+    cs.merge = 0;
+    cs.p = cs.q = 0;
+    cs.a = cs.b = 0;
+    const int xp = x == 0 ? pos[0] : pos[2], xq = x == 0 ? pos[1] : pos[3];
+    const int64_t va = x == 0 ? pv[0] : pv[2], vb = x == 0 ? pv[1] : pv[3];
+    if (kind == 1) {
+      cs.merge = is_col ? 2 : 1;
+      cs.p = xp;
+      cs.q = xq;
+      cs.a = va;
+      cs.b = vb;
+    } else {
+      cs.fac = va;
+    }
+    if (!is_col) {
+      cs.del_row = idx;
+      cs.del_col = kind == 1 ? xq : xp;
+    } else {
+      cs.del_col = idx;
+      cs.del_row = kind == 1 ? xq : xp;
+    }
+    // pass 1: row lengths, the union of nonzero columns, overflow
+    int cnt[RPL];
+    uint64_t cm0 = 0, cm1 = 0;
+    bool ovf = false;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      const int rc = lane + 32 * k;
+      int n = 0;
+      if (rc < mc) {
+        const int r = rc + (rc >= cs.del_row);
+        if (!child_row(v, cs, r, [&](int cc, int64_t) {
+              ++n;
+              if (cc < 64)
+                cm0 |= 1ull << cc;
+              else
+                cm1 |= 1ull << (cc - 64);
+            }))
+          ovf = true;
+      }
+      cnt[k] = n;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      cm0 |= __shfl_xor_sync(0xffffffffu, cm0, d);
+      cm1 |= __shfl_xor_sync(0xffffffffu, cm1, d);
+    }
+    bool zero_row = false;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k)
+      if (lane + 32 * k < mc && cnt[k] == 0) zero_row = true;
+    zero_row = __any_sync(0xffffffffu, zero_row);
+    ovf = __any_sync(0xffffffffu, ovf);
+    if (ovf && lane == 0) atomicCAS(X.err, 0, PERM_EOVERFLOW);
+    const int ncols = __popcll(cm0) + __popcll(cm1);
+    bool keep = !ovf && !zero_row && ncols == mc;
+    int offs[RPL];
+    int cnnz = 0;
+    int64_t o = -1;
+    if (keep) {
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) {
+        int tot;
+        offs[k] = cnnz + warp_excl_scan(cnt[k], lane, tot);
+        cnnz += tot;
+      }
+      o = child_block(X, p, c, pw, blk_words(mc, cnnz), lane);
+      keep = o >= 0;
+    }
+    if (keep) {
+      // pass 2: write rows
+      uint64_t* blk = X.arena_out + o;
+      uint16_t* rowptr = reinterpret_cast<uint16_t*>(blk);
+      uint8_t* col = reinterpret_cast<uint8_t*>(blk + blk_rp_words(mc));
+      int64_t* val = reinterpret_cast<int64_t*>(blk + blk_rp_words(mc) + blk_col_words(cnnz));
+      if (lane == 0) rowptr[mc] = (uint16_t)cnnz;
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) {
+        const int rc = lane + 32 * k;
+        if (rc < mc) {
+          const int r = rc + (rc >= cs.del_row);
+          rowptr[rc] = (uint16_t)offs[k];
+          int w = offs[k];
+          child_row(v, cs, r, [&](int cc, int64_t xv) {
+            col[w] = (uint8_t)cc;
+            val[w] = xv;
+            ++w;
+          });
+        }
+      }
+    }
+    if (lane == 0) {
+      X.valid[slot] = keep ? 1 : 0;
+      if (keep) {
+        X.child.m[slot] = mc;
+        X.child.nnz[slot] = cnnz;
+        X.child.off[slot] = o;
+        X.child.mat[slot] = X.parent.mat[p];
+        X.child.depth_left[slot] = dl - 1;
+        u256 cc = cs.fac == 1 ? pcoef : u256_mul_s64(pcoef, cs.fac);
+        for (int w = 0; w < 4; ++w) X.child.coef[4 * slot + w] = cc.w[w];
+        if (X.max_order) atomicMax(X.max_order, mc);
+      }
+    }
+  }
+}
+
+template <int RPL>
+__global__ void __launch_bounds__(kLevelWarps * 32) k_expand_level(ExpandLevelArgs A) {
+  __shared__ int32_t ccnt[kLevelWarps][RPL * 32];
+  extern __shared__ __align__(16) uint64_t stage[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  ExpandCtx X;
+  X.parent = A.parent;
+  X.arena_in = A.arena_in;
+  X.child = A.child;
+  X.arena_out = A.arena_out;
+  X.child_off_base = A.child_off_base;
+  X.bump = nullptr;
+  X.cap_words = 0;
+  X.max_order = nullptr;
+  X.valid = A.valid;
+  X.leaf_size = A.leaf_size;
+  X.err = A.err;
+  const int64_t nwarps = (int64_t)gridDim.x * kLevelWarps;
+  for (int64_t p = (int64_t)blockIdx.x * kLevelWarps + wib; p < A.np; p += nwarps)
+    expand_parent<RPL>(X, p, lane, ccnt[wib], stage + wib * kStageWords);
+}
+
+// ---- multi-level driver ---------------------------------------------------------
+
+__device__ __forceinline__ long long ld_cg(const long long* p) { return __ldcg(p); }
+
+// Sum over the block; every thread gets the total.  red: kFrontWarps entries.
+__device__ __forceinline__ long long block_sum(long long v, long long* red) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  long long t = 0;
+#pragma unroll
+  for (int w = 0; w < kFrontWarps; ++w) t += red[w];
+  return t;
+}
+
+// Exclusive scan of 0/1 flags over the block; total in *tot.  red:
+// kFrontWarps entries.
+__device__ __forceinline__ int block_excl_scan(int v, int* red, int& tot) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int wt;
+  const int x = warp_excl_scan(v, lane, wt);
+  __syncthreads();
+  if (lane == 0) red[wib] = wt;
+  __syncthreads();
+  int before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < kFrontWarps; ++w) {
+    if (w < wib) before += red[w];
+    all += red[w];
+  }
+  tot = all;
+  return before + x;
+}
+
+// Grid-wide barrier of a cooperative launch: a monotone arrival counter,
+// target = (barriers passed) * gridDim.x.  Thread 0 waits with a time
+// limit; on expiry the first error becomes PERM_ETIMEOUT and the whole
+// block returns false.
+__device__ bool grid_barrier(unsigned long long* bar, unsigned long long& target, int32_t* err) {
+  __syncthreads();
+  int failed = 0;
+  if (threadIdx.x == 0) {
+    target += gridDim.x;
+    __threadfence();
+    atomicAdd(bar, 1ull);
+    const uint64_t t0 = globaltimer_ns();
+    unsigned spins = 0;
+    while (*(volatile unsigned long long*)bar < target) {
+      __nanosleep(64);
+      if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > (uint64_t)kBarrierTimeoutNs) {
+        atomicCAS(err, 0, PERM_ETIMEOUT);
+        failed = 1;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  return __syncthreads_or(failed) == 0;
+}
+
+template <int RPL>
+__global__ void __launch_bounds__(kFrontThreads) k_expand_front(ExpandFrontArgs F) {
+  __shared__ int32_t ccnt[kFrontWarps][RPL * 32];
+  extern __shared__ __align__(16) uint64_t stage[];
+  __shared__ long long red64[kFrontWarps];
+  __shared__ int red32[kFrontWarps];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int64_t G = gridDim.x, b = blockIdx.x;
+  unsigned long long target = 0;
+  ExpandFrontState S = *F.state;
+  bool failed = false;  // an error flag raised during the last level
+  for (;;) {
+    // the same decision in every block: S and the error flag were read
+    // between the same two barriers (the flag is only raised while
+    // children are built, before the first barrier of a level)
+    bool stop = failed || S.level >= F.max_levels || S.ncur <= 0 || S.max_order > RPL * 32 ||
+                2 * S.ncur > F.cap_jobs || 2 * S.used_words > F.cap_words;
+    if (!stop && F.adaptive) {
+      const bool big = S.max_order > F.big_order;
+      const bool more = S.ncur < F.target_jobs && S.max_order > F.leaf_size;
+      stop = !big && !more;
+    }
+    if (stop) break;
+    const int cb = S.cb;
+    ExpandCtx X;
+    X.parent = F.buf[cb];
+    X.arena_in = F.arena[cb];
+    X.child = F.slots;
+    X.arena_out = F.arena[cb ^ 1];
+    X.child_off_base = nullptr;
+    X.bump = F.lvl_words + S.level;
+    X.cap_words = F.cap_words;
+    X.max_order = F.lvl_maxo + S.level;
+    X.valid = F.valid;
+    X.leaf_size = F.leaf_size;
+    X.err = F.err;
+    const int64_t p0 = S.ncur * b / G, p1 = S.ncur * (b + 1) / G;
+    for (int64_t p = p0 + wib; p < p1; p += kFrontWarps) expand_parent<RPL>(X, p, lane, ccnt[wib], stage + wib * kStageWords);
+    __syncthreads();
+    long long kept = 0;
+    for (int64_t t = 2 * p0 + threadIdx.x; t < 2 * p1; t += kFrontThreads) kept += F.valid[t];
+    kept = block_sum(kept, red64);
+    if (threadIdx.x == 0) __stcg(F.partial + b, kept);
+    if (!grid_barrier(F.bar, target, F.err)) return;
+    failed = __syncthreads_or(threadIdx.x == 0 && __ldcg(F.err) != 0) != 0;
+    long long before = 0, total = 0;
+    for (int64_t t = threadIdx.x; t < G; t += kFrontThreads) {
+      const long long x = ld_cg(F.partial + t);
+      total += x;
+      if (t < b) before += x;
+    }
+    before = block_sum(before, red64);
+    total = block_sum(total, red64);
+    // compaction of this block's slots, natural order kept
+    const JobArrays src = F.slots, dst = F.buf[cb ^ 1];
+    int64_t base = before;
+    for (int64_t t0 = 2 * p0; t0 < 2 * p1; t0 += kFrontThreads) {
+      const int64_t t = t0 + threadIdx.x;
+      const int keep = t < 2 * p1 ? F.valid[t] : 0;
+      int tot;
+      const int64_t d = base + block_excl_scan(keep, red32, tot);
+      if (keep) {
+        dst.m[d] = src.m[t];
+        dst.nnz[d] = src.nnz[t];
+        dst.off[d] = src.off[t];
+        dst.mat[d] = src.mat[t];
+        dst.depth_left[d] = src.depth_left[t];
+        for (int w = 0; w < 4; ++w) dst.coef[4 * d + w] = src.coef[4 * t + w];
+      }
+      base += tot;
+    }
+    if (!grid_barrier(F.bar, target, F.err)) return;
+    S.ncur = total;
+    S.used_words = (int64_t)__ldcg(F.lvl_words + S.level);
+    S.max_order = __ldcg(F.lvl_maxo + S.level);
+    S.cb ^= 1;
+    S.level += 1;
+  }
+  if (b == 0 && threadIdx.x == 0) *F.state = S;
+}
+
+template <int RPL>
+cudaError_t launch_level_rpl(const ExpandLevelArgs& a, cudaStream_t s) {
+  int64_t blocks = (a.np + kLevelWarps - 1) / kLevelWarps;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_expand_level<RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kLevelSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_expand_level<RPL><<<(unsigned)blocks, kLevelWarps * 32, kLevelSmem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int RPL>
+cudaError_t launch_front_rpl(ExpandFrontArgs a, int* grid, cudaStream_t s) {
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_expand_front<RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFrontSmem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand_front<RPL>, kFrontThreads, kFrontSmem);
+  if (e != cudaSuccess) return e;
+  *grid = 0;
+  if (!coop || per_sm <= 0) return cudaSuccess;  // not available: per-level launches only
+  int g = sms * (per_sm < 2 ? per_sm : 2);
+  if (g > PERM_FRONT_MAX_BLOCKS) g = PERM_FRONT_MAX_BLOCKS;
+  void* args[] = {&a};
+  e = cudaLaunchCooperativeKernel((const void*)k_expand_front<RPL>, dim3((unsigned)g), dim3(kFrontThreads), args,
+                                  kFrontSmem, s);
+  if (e == cudaSuccess) *grid = g;
+  return e;
+}
+
+}  // namespace
+
+cudaError_t launch_expand_level(const ExpandLevelArgs& a, int max_order, cudaStream_t s) {
+  if (a.np <= 0) return cudaSuccess;
+  if (max_order <= 32) return launch_level_rpl<1>(a, s);
+  if (max_order <= 64) return launch_level_rpl<2>(a, s);
+  return launch_level_rpl<4>(a, s);
+}
+
+cudaError_t launch_expand_front(const ExpandFrontArgs& a, int max_order, int* grid, cudaStream_t s) {
+  if (max_order <= 32) return launch_front_rpl<1>(a, grid, s);
+  if (max_order <= 64) return launch_front_rpl<2>(a, grid, s);
+  return launch_front_rpl<4>(a, grid, s);
 }
 
 __global__ void k_child_capacity(JobArrays parent, int64_t np, int64_t* words) {
@@ -365,32 +653,6 @@ __global__ void k_compact(JobArrays src, const int32_t* valid, const int32_t* po
     atomicAdd(reinterpret_cast<unsigned long long*>(stat + 1), (unsigned long long)sw);
     atomicAdd(reinterpret_cast<unsigned long long*>(stat + 2), (unsigned long long)nk);
   }
-}
-
-template <int TILE>
-cudaError_t launch_tile(const ExpandLevelArgs& a, cudaStream_t s) {
-  typedef ExpandCfg<TILE> C;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_expand_level<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  int64_t blocks = (a.np + C::WARPS - 1) / C::WARPS;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  k_expand_level<TILE><<<(unsigned)blocks, C::WARPS * 32, C::SMEM, s>>>(a);
-  return cudaGetLastError();
-}
-
-}  // namespace
-
-cudaError_t launch_expand_level(const ExpandLevelArgs& a, int max_order, cudaStream_t s) {
-  if (a.np <= 0) return cudaSuccess;
-  if (max_order <= 16) return launch_tile<16>(a, s);
-  if (max_order <= 32) return launch_tile<32>(a, s);
-  if (max_order <= 64) return launch_tile<64>(a, s);
-  return launch_tile<128>(a, s);
 }
 
 cudaError_t launch_child_capacity(const JobArrays& parent, int64_t np, int64_t* words, cudaStream_t s) {

@@ -22,16 +22,40 @@ size_t scan_tmp_bytes_i32(int64_t n);
 cudaError_t sort_desc_f32(const float* keys_in, float* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
                           int64_t n, void* tmp, size_t tmp_bytes, cudaStream_t s);
 size_t sort_tmp_bytes_f32(int64_t n);
+// Stable sort of (key, value) pairs by ascending key bits [0, end_bit).
+cudaError_t sort_asc_u32(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+                         int64_t n, int end_bit, void* tmp, size_t tmp_bytes, cudaStream_t s);
+size_t sort_tmp_bytes_u32(int64_t n, int end_bit);
+// *out = min over jobs j < n with status s not in {0, DFS_RETRY} of j * 256 + s
+// (unchanged when there is none; set it to ~0 first).
+cudaError_t launch_status_summary(const int32_t* status, int64_t n, unsigned long long* out, cudaStream_t s);
+// Stable compaction of the depth-first queue's jobs whose status is
+// DFS_RETRY into rq; counts[0] = those among the first n2 entries, counts[1]
+// = all.  flags and pos hold n + 1 entries each.
+cudaError_t launch_retry_collect(const uint32_t* dq, int64_t n, int64_t n2, const int32_t* status, int32_t* flags,
+                                 int32_t* pos, void* scan_tmp, size_t scan_tmp_bytes, uint32_t* rq,
+                                 unsigned long long* counts, cudaStream_t s);
 
 // ---- K2 leaf batch -----------------------------------------------------------
-// Kernel variant of every queued leaf job (register width, ring width, path).
-cudaError_t launch_leaf_classify(const uint32_t* queue, int64_t nq, const JobArrays& jobs, const uint64_t* arena,
-                                 const int32_t* mat_w, int32_t* cls, cudaStream_t stream);
-// One variant group of leaf jobs in queue order.
-cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int cls, const JobArrays& jobs,
-                              const uint64_t* arena, int chunk_log2, uint64_t* counts_scratch, uint64_t* prefix,
-                              void* scan_tmp, size_t scan_tmp_bytes, unsigned long long* task_counter,
-                              const JobOut& out, int num_sms, cudaStream_t stream);
+// Evaluation keys of a queue: leaf jobs (order <= leaf_max) get their kernel
+// variant (nmax index | W bit | path << 3, < 64), the others
+// EVAL_KEY_DFS + (ring width 4); hist[key] counts them (zero it first,
+// EVAL_KEYS entries).
+#define EVAL_KEY_DFS 64
+#define EVAL_KEYS 66
+cudaError_t launch_eval_keys(const uint32_t* queue, int64_t n, const JobArrays& jobs, const uint64_t* arena,
+                             const int32_t* mat_w, int leaf_max, uint32_t* keys, uint32_t* vals,
+                             unsigned long long* hist, cudaStream_t stream);
+// Ryser tasks of every queued leaf job and their exclusive scan (nq + 1 entries).
+cudaError_t launch_leaf_tasks(const uint32_t* queue, int64_t nq, const JobArrays& jobs, int chunk_log2,
+                              uint64_t* counts_scratch, uint64_t* prefix, void* scan_tmp, size_t scan_tmp_bytes,
+                              cudaStream_t stream);
+// One variant group of leaf jobs in queue order; prefix is the group's slice
+// of the task scan (nq + 1 entries).
+cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int cls, const uint64_t* prefix,
+                              const JobArrays& jobs, const uint64_t* arena, int chunk_log2,
+                              unsigned long long* task_counter, const JobOut& out, int num_sms,
+                              cudaStream_t stream);
 // Sigma -> coef * per for every leaf job, summed into the matrix accumulators.
 cudaError_t launch_leaf_finalize(const uint32_t* queue, int64_t nq, const JobArrays& jobs, const JobOut& out,
                                  unsigned long long* mat_acc, cudaStream_t stream);
@@ -52,6 +76,46 @@ struct ExpandLevelArgs {
   int32_t* err;     // device flag: first error status
 };
 cudaError_t launch_expand_level(const ExpandLevelArgs& a, int max_order, cudaStream_t s);
+
+// Consecutive levels in one cooperative launch.  The current jobs are
+// buf[state.cb] with their blocks in arena[state.cb] (state.used_words
+// words).  Runs a level while: level < max_levels, 0 < ncur, 2 * ncur <=
+// cap_jobs, 2 * used_words <= cap_words, and (when adaptive) max_order >
+// big_order or (ncur < target_jobs and max_order > leaf_size).  The state
+// is updated in place; the children of a level are compacted in natural
+// order into the other buffer.  bar, lvl_words and lvl_maxo (max_levels
+// entries) must be zero; partial holds PERM_FRONT_MAX_BLOCKS entries.
+struct ExpandFrontState {
+  int64_t ncur;
+  int64_t used_words;
+  int32_t level;
+  int32_t max_order;
+  int32_t cb;
+  int32_t pad;
+};
+#define PERM_FRONT_MAX_BLOCKS 1024
+struct ExpandFrontArgs {
+  JobArrays buf[2];
+  uint64_t* arena[2];
+  int64_t cap_jobs;
+  int64_t cap_words;
+  JobArrays slots;  // 2 * cap_jobs
+  int32_t* valid;   // 2 * cap_jobs
+  int32_t leaf_size;
+  int32_t max_levels;
+  int32_t adaptive;
+  int32_t big_order;
+  int64_t target_jobs;
+  ExpandFrontState* state;
+  long long* partial;
+  unsigned long long* bar;
+  unsigned long long* lvl_words;
+  int32_t* lvl_maxo;
+  int32_t* err;
+};
+// *grid = blocks launched, 0 when the device has no cooperative launch (the
+// caller then runs every level with launch_expand_level).
+cudaError_t launch_expand_front(const ExpandFrontArgs& a, int max_order, int* grid, cudaStream_t s);
 // words[p] = 2 * blk_words(parent p) (capacity for its two children)
 cudaError_t launch_child_capacity(const JobArrays& parent, int64_t np, int64_t* words, cudaStream_t s);
 // Compact valid slots into dst (natural order kept).  Accumulates into

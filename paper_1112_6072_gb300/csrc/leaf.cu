@@ -74,13 +74,9 @@ __global__ void k_leaf_task_counts(const uint32_t* __restrict__ queue, int64_t n
   counts[q] = tasks;
 }
 
-// One thread per queued leaf job: variant code (nmax index) | W | path << 8.
-__global__ void k_leaf_classify(const uint32_t* __restrict__ queue, int64_t nq, JobArrays jobs,
-                                const uint64_t* __restrict__ arena, const int32_t* __restrict__ mat_w,
-                                int32_t* __restrict__ cls) {
-  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= nq) return;
-  const uint32_t job = queue[q];
+// Kernel variant of a leaf job: nmax index | W (4 -> bit 2) | path << 3.
+__device__ int leaf_class(uint32_t job, const JobArrays& jobs, const uint64_t* __restrict__ arena,
+                          const int32_t* __restrict__ mat_w) {
   const int m = jobs.m[job];
   const int nnz = jobs.nnz[job];
   CsrView v = csr_view(arena, jobs.off[job], m, nnz);
@@ -117,7 +113,32 @@ __global__ void k_leaf_classify(const uint32_t* __restrict__ queue, int64_t nq, 
       else if (k <= 16 && m > 8) path = P_F16;
     }
   }
-  cls[q] = nmi | ((W == 4) ? 4 : 0) | (path << 8);
+  return nmi | ((W == 4) ? 4 : 0) | (path << 3);
+}
+
+// One thread per queue position: the sort key of its job -- the leaf
+// variant (< 64) for jobs of order <= leaf_max, else 64 + (W == 4) for the
+// depth-first evaluator -- and a histogram of the keys.
+__global__ void k_eval_keys(const uint32_t* __restrict__ queue, int64_t n, JobArrays jobs,
+                            const uint64_t* __restrict__ arena, const int32_t* __restrict__ mat_w, int leaf_max,
+                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                            unsigned long long* __restrict__ hist) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool act = q < n;
+  uint32_t key = 0xffffffffu;
+  if (act) {
+    const uint32_t job = queue[q];
+    const int m = jobs.m[job];
+    if (m <= leaf_max)
+      key = (uint32_t)leaf_class(job, jobs, arena, mat_w);
+    else
+      key = EVAL_KEY_DFS + (mat_w[jobs.mat[job]] == 4 ? 1u : 0u);
+    keys[q] = key;
+    vals[q] = job;
+  }
+  // one atomic per distinct key in the warp
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  if (act && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(hist + key, (unsigned long long)__popc(peers));
 }
 
 // Load a leaf for the plain walk: rows in order, Gray column j = column j,
@@ -209,7 +230,9 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32)
   const int wib = threadIdx.x >> 5;
   int32_t* delta = sm.delta[wib];
   int32_t* rho0 = sm.rho0[wib];
-  const uint64_t total = prefix[nq];
+  // prefix may be a slice of a longer scan: tasks [prefix[0], prefix[nq])
+  const uint64_t base = prefix[0];
+  const uint64_t total = prefix[nq] - base;
   int64_t cur_q = -1;
   int m = 0;
   for (;;) {
@@ -217,6 +240,7 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32)
     if (lane == 0) t = atomicAdd(task_counter, 1ull);
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= total) break;
+    t += base;
     // queue entry holding task t: last q with prefix[q] <= t
     int64_t lo = 0, hi = nq - 1;
     while (lo < hi) {
@@ -340,29 +364,38 @@ cudaError_t launch_path(int path, const uint32_t* queue, int64_t nq, const uint6
 
 }  // namespace
 
-cudaError_t launch_leaf_classify(const uint32_t* queue, int64_t nq, const JobArrays& jobs, const uint64_t* arena,
-                                 const int32_t* mat_w, int32_t* cls, cudaStream_t stream) {
-  if (nq <= 0) return cudaSuccess;
-  k_leaf_classify<<<(unsigned)((nq + 127) / 128), 128, 0, stream>>>(queue, nq, jobs, arena, mat_w, cls);
+cudaError_t launch_eval_keys(const uint32_t* queue, int64_t n, const JobArrays& jobs, const uint64_t* arena,
+                             const int32_t* mat_w, int leaf_max, uint32_t* keys, uint32_t* vals,
+                             unsigned long long* hist, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  k_eval_keys<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(queue, n, jobs, arena, mat_w, leaf_max, keys, vals,
+                                                               hist);
   return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int cls, const JobArrays& jobs,
-                              const uint64_t* arena, int chunk_log2, uint64_t* counts_scratch, uint64_t* prefix,
-                              void* scan_tmp, size_t scan_tmp_bytes, unsigned long long* task_counter,
-                              const JobOut& out, int num_sms, cudaStream_t stream) {
+cudaError_t launch_leaf_tasks(const uint32_t* queue, int64_t nq, const JobArrays& jobs, int chunk_log2,
+                              uint64_t* counts_scratch, uint64_t* prefix, void* scan_tmp, size_t scan_tmp_bytes,
+                              cudaStream_t stream) {
   if (nq <= 0) return cudaSuccess;
-  const int path = cls >> 8;
+  const int tb = 256;
+  k_leaf_task_counts<<<(unsigned)((nq + 1 + tb - 1) / tb), tb, 0, stream>>>(queue, nq, jobs.m, chunk_log2,
+                                                                              counts_scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return scan_exclusive_u64(counts_scratch, prefix, nq + 1, scan_tmp, scan_tmp_bytes, stream);
+}
+
+cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int cls, const uint64_t* prefix,
+                              const JobArrays& jobs, const uint64_t* arena, int chunk_log2,
+                              unsigned long long* task_counter, const JobOut& out, int num_sms,
+                              cudaStream_t stream) {
+  if (nq <= 0) return cudaSuccess;
+  const int path = cls >> 3;
   if (path == P_BAD) {
     k_leaf_reject<<<(unsigned)((nq + 255) / 256), 256, 0, stream>>>(queue, nq, out);
     return cudaGetLastError();
   }
-  const int tb = 256;
-  k_leaf_task_counts<<<(unsigned)((nq + 1 + tb - 1) / tb), tb, 0, stream>>>(queue, nq, jobs.m, chunk_log2,
-                                                                              counts_scratch);
-  cudaError_t e = scan_exclusive_u64(counts_scratch, prefix, nq + 1, scan_tmp, scan_tmp_bytes, stream);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(task_counter, 0, sizeof(unsigned long long), stream);
+  cudaError_t e = cudaMemsetAsync(task_counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
   const int nmi = cls & 3;
   if ((cls & 4) == 0) {

@@ -46,6 +46,72 @@ size_t sort_tmp_bytes_f32(int64_t n) {
   return b;
 }
 
+cudaError_t sort_asc_u32(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+                         int64_t n, int end_bit, void* tmp, size_t tmp_bytes, cudaStream_t s) {
+  return cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys_in, keys_out, vals_in, vals_out, n, 0, end_bit, s);
+}
+size_t sort_tmp_bytes_u32(int64_t n, int end_bit) {
+  size_t b = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, b, (const uint32_t*)nullptr, (uint32_t*)nullptr, (const uint32_t*)nullptr,
+                                  (uint32_t*)nullptr, n, 0, end_bit);
+  return b;
+}
+
+// ---- evaluation bookkeeping on the device (no per-job host copies) -----------
+
+__global__ void k_status_summary(const int32_t* __restrict__ status, int64_t n, unsigned long long* out) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned long long key = ~0ull;
+  if (j < n) {
+    const int32_t s = status[j];
+    if (s != 0 && s != DFS_RETRY) key = (unsigned long long)j * 256ull + (unsigned long long)(s & 255);
+  }
+  // lowest key of the warp, then one atomic per warp
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, d);
+    key = o < key ? o : key;
+  }
+  if ((threadIdx.x & 31) == 0 && key != ~0ull) atomicMin(out, key);
+}
+
+cudaError_t launch_status_summary(const int32_t* status, int64_t n, unsigned long long* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_status_summary<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(status, n, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_retry_flags(const uint32_t* __restrict__ dq, int64_t n, const int32_t* __restrict__ status,
+                              int32_t* __restrict__ flags) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n) flags[k] = status[dq[k]] == DFS_RETRY ? 1 : 0;
+  if (k == n) flags[k] = 0;  // the scan's last entry is the total
+}
+
+__global__ void k_retry_scatter(const uint32_t* __restrict__ dq, int64_t n, int64_t n2,
+                                const int32_t* __restrict__ flags, const int32_t* __restrict__ pos,
+                                uint32_t* __restrict__ rq, unsigned long long* counts) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n && flags[k]) rq[pos[k]] = dq[k];
+  if (k == n) {
+    counts[0] = (unsigned long long)pos[n2];
+    counts[1] = (unsigned long long)pos[n];
+  }
+}
+
+cudaError_t launch_retry_collect(const uint32_t* dq, int64_t n, int64_t n2, const int32_t* status, int32_t* flags,
+                                 int32_t* pos, void* scan_tmp, size_t scan_tmp_bytes, uint32_t* rq,
+                                 unsigned long long* counts, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((n + 1 + 255) / 256);
+  k_retry_flags<<<blocks, 256, 0, s>>>(dq, n, status, flags);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = scan_exclusive_i32(flags, pos, n + 1, scan_tmp, scan_tmp_bytes, s);
+  if (e != cudaSuccess) return e;
+  k_retry_scatter<<<blocks, 256, 0, s>>>(dq, n, n2, flags, pos, rq, counts);
+  return cudaGetLastError();
+}
+
 // 16 independent dependency chains of 32-bit multiply-adds per thread, so
 // the issue rate rather than the latency limits the throughput.
 __global__ void k_ubench_imad(int iters, uint32_t* sink) {

@@ -125,10 +125,11 @@ def test_invalid_arguments_rejected():
 
 
 # ---------------------------------------------------------------- expansion (K1)
+@pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("n,seed,d,L", [(10, 1, 3, 2), (16, 2, 6, 4), (24, 3, 10, 8), (36, 1, 20, 16)])
-def test_job_list_matches_oracle(n, seed, d, L):
+def test_job_list_matches_oracle(n, seed, d, L, fused):
     a = W.regular3(n, seed)
-    with pk.Plan([a], split_depth=d, leaf_size=L) as plan:
+    with pk.Plan([a], split_depth=d, leaf_size=L, fused_levels=fused) as plan:
         plan.expand()
         got = plan.jobs_export()
     want = oracle.jobs(a, d, L)
@@ -139,16 +140,45 @@ def test_job_list_matches_oracle(n, seed, d, L):
         assert gc == wc % (1 << 256)
 
 
-def test_job_list_signed_sparse():
+@pytest.mark.parametrize("fused", [True, False])
+def test_job_list_signed_sparse(fused):
     a = W.random_small(14, 77, lo=-2, hi=2, density=0.25)
     a[np.arange(14), np.arange(14)] = 1  # no zero line
-    with pk.Plan([a], split_depth=5, leaf_size=3) as plan:
+    with pk.Plan([a], split_depth=5, leaf_size=3, fused_levels=fused) as plan:
         plan.expand()
         got = plan.jobs_export()
     want = oracle.jobs(a, 5, 3)
     assert len(got) == len(want)
     for (_, gm, gc), (wm, wc) in zip(got, want):
         assert (gm == wm).all() and gc == wc % (1 << 256)
+
+
+def _export(mats, fused, **kw):
+    with pk.Plan(mats, fused_levels=fused, **kw) as plan:
+        plan.expand()
+        return plan.jobs_export()
+
+
+@pytest.mark.parametrize("case", ["c60", "batch", "regular80", "signed30"])
+def test_fused_levels_same_jobs(case):
+    """The single-launch multi-level expansion (with its buffer growth and
+    hand-over to per-level launches) yields the per-level job list."""
+    if case == "c60":
+        mats, kw = [W.c60(60)], dict(leaf_size=12)
+    elif case == "batch":
+        mats = [W.regular3(n, s) for n, s in ((20, 1), (28, 2), (40, 3), (12, 4))] + [W.sparse_rows(24, 5)]
+        kw = dict(split_depth=9, leaf_size=6)
+    elif case == "regular80":  # frontier beyond the first buffers: growth and copies
+        mats, kw = [W.regular3(80, 3)], dict(split_depth=19, leaf_size=10)
+    else:
+        a = W.random_small(30, 9, lo=-3, hi=3, density=0.15)
+        a[np.arange(30), (np.arange(30) * 7) % 30] = 2
+        mats, kw = [a], dict(split_depth=12, leaf_size=5)
+    got = _export(mats, True, **kw)
+    want = _export(mats, False, **kw)
+    assert len(got) == len(want) > 0
+    for (gi, gm, gc), (wi, wm, wc) in zip(got, want):
+        assert gi == wi and gm.shape == wm.shape and (gm == wm).all() and gc == wc
 
 
 # ---------------------------------------------------------------- hybrid end to end (K1+K3+K2+K6)
