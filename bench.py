@@ -314,6 +314,70 @@ def run_single(pk, torch, a, args):
             "nodes": int(sum(r.nodes for r in rec)), "leaves": int(sum(r.leaves for r in rec))}
 
 
+MIXED_SEED = 5
+
+
+def run_mixed(pk, torch, args):
+    """Config 5: 128 random 3-regular adjacencies (n in [40, 90]) and 128
+    sparse matrices with 3-5 nonzeros per row (n in [40, 70]) in one plan.
+    The leaf order is tuned on a sample of the batch; the learned model
+    (without the KKLLL feature, so ordering costs no estimate) is trained on
+    the job times of the n = 36 and C60 whole paths.  Orders: natural, the
+    learned one (also replayed as one CUDA graph) and KKLLL-LPT with 32
+    trials per job (m^2 trials on ~10^7 jobs would take minutes)."""
+    from paper_1112_6072_gb300 import autotune, learned
+
+    def log(*a):
+        print(*a, file=sys.stderr, flush=True)
+
+    mats = W.mixed_batch(seed=MIXED_SEED)
+    Xs, ts = [], []
+    for a, kw in ((W.regular3(36, 1), dict(split_depth=20, leaf_size=16)), (W.c60(C60_SEED), dict(leaf_size=12))):
+        with pk.Plan([a], model_uses_estimate=False, **kw) as p:
+            p.expand()
+            X, t, _ = learned.collect(p, "natural")
+        Xs.append(X)
+        ts.append(t)
+    params, loss = learned.train(np.concatenate(Xs), np.concatenate(ts), steps=600)
+    log("mixed: model trained, loss", loss)
+    tune = autotune.tune_batch(mats)
+    L = tune["leaf_size"]
+    log("mixed: tuned", tune)
+    out = {"workload": f"mixed batch seed {MIXED_SEED}: 128 3-regular n in [40,90] + 128 sparse rows 3-5 nz "
+                       f"n in [40,70]",
+           "tune": tune, "model_loss": loss}
+    ref = None
+    for order, trials in (("natural", 0), ("learned", 0), ("lpt", 32)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        with pk.Plan(mats, leaf_size=L, order=order, kklll_trials=trials, model_uses_estimate=False,
+                     timeout_ns=3600 * 10**9) as p:
+            nj = p.expand()
+            if order == "learned":
+                p.attach_model(params)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            p.order(order)
+            torch.cuda.synchronize()
+            order_ms = (time.perf_counter() - t1) * 1e3
+            rec = p.evaluate(records="array")
+            vals = p.results()
+            wall = time.perf_counter() - t
+            ev = p.last_eval_ms
+            rep = None
+            if order == "learned":
+                p.replay()
+                rep = p.last_eval_ms
+        leaves = int(rec["leaves"].sum())
+        if ref is None:
+            ref = vals
+        out[order] = {"jobs": nj, "wall_s": wall, "eval_ms": ev, "graph_replay_ms": rep, "order_ms": order_ms,
+                      "leaves": leaves, "leaves_per_s": leaves / (ev / 1e3), "kklll_trials": trials or None,
+                      "same_permanents": vals == ref, "nonzero": sum(1 for v in vals if v)}
+        log("mixed:", order, out[order])
+    return out
+
+
 def run_reference(args):
     """The oracle (plain CPU) on a bounded sample of the same workload."""
     import oracle
@@ -375,6 +439,8 @@ def main():
                     help="run only the C60 whole-path leg and print its timings")
     ap.add_argument("--c100", action="store_true",
                     help="per(A) of the paper's C100 adjacency (Appendix) against its printed total")
+    ap.add_argument("--mixed", action="store_true",
+                    help="the mixed batch of 256 matrices (3-regular and sparse rows), three orders")
     ap.add_argument("--leaf-size", type=int, default=12)
     ap.add_argument("--regular", type=int, default=0,
                     help="per(A) of one random 3-regular graph of this order (seed 1), natural order")
@@ -385,6 +451,12 @@ def main():
         import paper_1112_6072_gb300 as pk
         torch.cuda.set_device(0)
         print(json.dumps({"c60": run_c60(pk, torch, args)}))
+        return
+    if args.mixed:
+        import torch
+        import paper_1112_6072_gb300 as pk
+        torch.cuda.set_device(0)
+        print(json.dumps({"mixed": run_mixed(pk, torch, args)}))
         return
     if args.c100 or args.regular:
         import torch

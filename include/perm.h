@@ -77,8 +77,11 @@ typedef void* (*perm_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*perm_free_fn)(void* ptr, void* stream, void* ctx);
 
 typedef struct {
-  int32_t split_depth;     /* d of Algorithm PH; -1 = choose so jobs have order <= PERM_MAX_JOB_N
-                              and about 2^17 jobs per matrix */
+  int32_t split_depth;     /* d of Algorithm PH; -1 = choose: expand while a job has order
+                              > PERM_MAX_JOB_N, or order > 32 with fewer than 2^25 jobs, or
+                              while there are fewer than 2^17 jobs per matrix (2^21 for batches
+                              of 16 or more) and a job above order L; each level then splits
+                              only the jobs within 2 orders of the largest one (largest first) */
   int32_t leaf_size;       /* L: a node of order <= L is evaluated by Ryser; 0 = choose */
   int32_t order;           /* perm_order_kind used by perm_eval_batch when no order is given */
   int32_t kklll_trials;    /* KKLLL trials per job; 0 = m^2 for a job of order m (Table T5 note) */

@@ -296,17 +296,22 @@ class Plan:
             optr = oa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
         res = (perm_job_result * max(self.njobs, 1))() if records else None
         _ck(lib.perm_eval_batch(self._jobs, optr, res), "perm_eval_batch")
-        if not records:
-            return None
-        return [JobRecord(r.matrix, r.order, r.nnz, r.status, _words_to_int(r.value), r.t_start_ns,
-                          r.t_end_ns, r.sm, r.queue_pos, r.leaves, r.nodes) for r in res[:self.njobs]]
+        return self._records(res, records)
 
     def replay(self, records=False):
         """Repeat the last evaluation as a captured CUDA graph."""
         res = (perm_job_result * max(self.njobs, 1))() if records else None
         _ck(_lib().perm_eval_replay(self._jobs, res), "perm_eval_replay")
+        return self._records(res, records)
+
+    def _records(self, res, records):
+        """records=True: a list of JobRecord; records="array": the raw
+        perm_job_result array as a numpy structured array (fields as in
+        include/perm.h; value holds the four little-endian words)."""
         if not records:
             return None
+        if records == "array":
+            return np.ctypeslib.as_array(res)[:self.njobs].copy()
         return [JobRecord(r.matrix, r.order, r.nnz, r.status, _words_to_int(r.value), r.t_start_ns,
                           r.t_end_ns, r.sm, r.queue_pos, r.leaves, r.nodes) for r in res[:self.njobs]]
 

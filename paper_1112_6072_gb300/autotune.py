@@ -107,3 +107,21 @@ def tune_leaf_batch(mats, chunks=(6, 8, 10, 12), cache_file: str | None = None) 
     if cache_file:
         json.dump(_CACHE, open(cache_file, "w"), indent=1)
     return dict(best)
+
+
+def tune_batch(mats, leaf_sizes=(12, 14, 16), sample=16, order="lpt") -> dict:
+    """Best leaf order L for a batch, timed on a sample of it: the whole path
+    (automatic split depth) over every k-th matrix by order, so the sample
+    spans the batch's sizes without its most expensive members."""
+    by_n = sorted(range(len(mats)), key=lambda k: (np.asarray(mats[k]).shape[0], k))
+    step = max(1, len(by_n) // sample)
+    picked = [mats[k] for k in by_n[: len(by_n) - step][::step]][:sample] or list(mats)
+    key = f"batch_{len(mats)}_{sum(np.asarray(m).shape[0] for m in mats)}_{_gpu_name()}"
+    if key in _CACHE:
+        return dict(_CACHE[key])
+    results = [(_time_path(picked, reps=1, leaf_size=L, order=order), L) for L in leaf_sizes]
+    t, L = min(results)
+    best = {"leaf_size": L, "sample_seconds": t, "sample": len(picked),
+            "tried": {str(l): round(s, 4) for s, l in results}}
+    _CACHE[key] = best
+    return dict(best)

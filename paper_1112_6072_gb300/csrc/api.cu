@@ -210,8 +210,19 @@ struct JobBuf {
 // depth-first queues, leaf kernel variants, and the device buffers the
 // launches use.  Kept with the job set so the launch sequence can be
 // captured once into a CUDA graph and replayed.
+// E.sum layout: status summary, retry positions, evaluation key histogram
+#define SUM_STATUS 0
+#define SUM_RETRY 1
+#define SUM_HIST (SUM_RETRY + EVAL_DFS_GROUPS + 1)
+#define SUM_WORDS (SUM_HIST + EVAL_KEYS)
+
+// depth-first group g of the grouped queue: tile 64 first, ring width 2 then 4
+static inline int dfs_group_tile(int g) { return g >= 2 ? 32 : 64; }
+static inline int dfs_group_w(int g) { return (g & 1) ? 4 : 2; }
+
 struct EvalState {
-  int64_t nl = 0, nd = 0, nd_w2 = 0;
+  int64_t nl = 0, nd = 0;
+  int64_t db[EVAL_DFS_GROUPS + 1] = {0, 0, 0, 0, 0};  // depth-first group bounds in d_dq
   std::vector<std::pair<int64_t, int64_t>> groups;  // (offset, count) in the grouped leaf queue
   std::vector<int32_t> group_cls;
   uint32_t* d_q = nullptr;   // the queue as evaluated
@@ -225,12 +236,11 @@ struct EvalState {
   uint64_t* prefix = nullptr;
   void* stmp = nullptr;
   size_t stb = 0;
-  unsigned long long* ctr = nullptr;
-  // [0] status summary, [1] [2] retry counts, [3 ..] evaluation key histogram
-  unsigned long long* sum = nullptr;
+  unsigned long long* ctr = nullptr;  // [0] leaf tasks, [1 + g] depth-first group g
+  unsigned long long* sum = nullptr;  // SUM_WORDS entries
   int64_t* undo = nullptr;
   int64_t undo_w = 0;
-  int tile = 32, wps = 0, chunk = 10;
+  int chunk = 10;
   bool wide_first = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -488,6 +498,14 @@ extern "C" void perm_plan_destroy(perm_plan_t* P) {
 
 // ---------------------------------------------------------------- a2, a3: expansion
 static const int64_t kTargetJobs = 1ll << 17;
+// automatic depth: a level splits the jobs within this many orders of the
+// largest job still to split
+static const int kSplitBand = 2;
+// automatic depth: jobs above this order are split further while the job
+// count is below kSoftCapJobs (the depth-first evaluator holds three times
+// as many warps per SM for jobs of order <= 32)
+static const int kSoftOrder = 32;
+static const int64_t kSoftCapJobs = 1ll << 25;
 // fused (single-launch) expansion buffers: initial and largest capacities
 static const int64_t kFusedJobs0 = 1ll << 15;
 static const int64_t kFusedWords0 = 1ll << 21;
@@ -504,6 +522,7 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
   std::vector<int32_t> rm, rnnz, rmat, rdl;
   std::vector<int64_t> roff;
   int maxn = 0, maxd = 0;
+  int max_open = 0;  // largest order of a job still to split
   bool adaptive = false;
   for (int i = 0; i < P->count; ++i) {
     if (P->trivial[i]) continue;
@@ -519,6 +538,7 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
     rdl.push_back(d);
     maxn = std::max(maxn, P->n[i]);
     maxd = std::max(maxd, d);
+    if (d > 0 && P->n[i] > std::max(P->L, 2)) max_open = std::max(max_open, P->n[i]);
   }
   const int64_t nroots = (int64_t)rm.size();
   perm_jobs* J = new perm_jobs();
@@ -547,21 +567,31 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
     CK(cudaMemcpyAsync(cur.coef, coef.data(), 32 * nroots, cudaMemcpyHostToDevice, s));
   }
   // stat[0]: first error status (int32 in the low half), [1]: largest kept
-  // order, [2]: words of the kept blocks, [3]: kept jobs
-  long long* d_stat = dget<long long>(M, 4);
+  // order, [2]: words of the kept blocks, [3]: kept jobs, [4]: largest
+  // order of a kept job still to split
+  long long* d_stat = dget<long long>(M, 5);
   if (!d_stat) return PERM_ENOMEM;
-  CK(cudaMemsetAsync(d_stat, 0, 32, s));
+  CK(cudaMemsetAsync(d_stat, 0, 40, s));
   int max_order = maxn;
   int64_t cur_arena_words = (int64_t)P->h_arena.size();  // roots sit back to back
   int64_t used_words = cur_arena_words;                    // words of the current jobs' blocks
-  const int64_t target = kTargetJobs * std::max<int64_t>(1, nroots);
-  auto levels_left = [&](int level, int64_t n, int mo) {
+  // about 2^17 jobs per matrix, at most 2^21 for a batch (enough queue for
+  // every worker many times over)
+  const int64_t target = kTargetJobs * std::min<int64_t>(16, std::max<int64_t>(1, nroots));
+  // automatic depth: split while a job still to split is above
+  // PERM_MAX_JOB_N, or above kSoftOrder while the jobs number fewer than
+  // kSoftCapJobs, or while there are fewer jobs than the target; each
+  // level splits only the jobs within kSplitBand orders of the largest one
+  // still to split (the largest jobs first, so the matrices of a batch end
+  // with jobs of similar order), the others wait
+  auto levels_left = [&](int level, int64_t n, int mopen) {
     if (level >= maxd || n <= 0) return false;
     if (!adaptive) return true;
-    return mo > PERM_MAX_JOB_N || (n < target && mo > P->L);
+    return mopen > PERM_MAX_JOB_N || (mopen > kSoftOrder && n < kSoftCapJobs) || (n < target && mopen > 0);
   };
+  auto split_floor = [&](int mopen) { return adaptive ? mopen - kSplitBand : 0; };
   int level0 = 0;
-  if (P->opts.fused_levels && levels_left(0, ncur, max_order)) {
+  if (P->opts.fused_levels && levels_left(0, ncur, max_open)) {
     // consecutive levels in one cooperative launch; buffers start small and
     // grow by 4x (the current level copied over) when the frontier outgrows
     // them, up to kFusedMaxJobs / kFusedMaxWords
@@ -572,7 +602,9 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
     unsigned long long* d_bar = dget<unsigned long long>(M, 1);
     unsigned long long* d_lw = dget<unsigned long long>(M, maxd);
     int32_t* d_lm = dget<int32_t>(M, maxd);
-    if (!d_state || !d_partial || !d_bar || !d_lw || !d_lm) return PERM_ENOMEM;
+    int32_t* d_lo = dget<int32_t>(M, maxd);
+    if (!d_state || !d_partial || !d_bar || !d_lw || !d_lm || !d_lo) return PERM_ENOMEM;
+    CK(cudaMemsetAsync(d_lo, 0, 4 * (size_t)maxd, s));
     CK(cudaMemsetAsync(d_lw, 0, 8 * (size_t)maxd, s));
     CK(cudaMemsetAsync(d_lm, 0, 4 * (size_t)maxd, s));
     ExpandFrontState S;
@@ -580,8 +612,8 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
     S.used_words = used_words;
     S.level = 0;
     S.max_order = max_order;
+    S.max_open = max_open;
     S.cb = 0;
-    S.pad = 0;
     for (;;) {
       const int ob = S.cb ^ 1;
       if (!jb[ob].ensure(M, cap_jobs) || !grow(M, ar[ob], 8 * (size_t)cap_words) || !slots.ensure(M, 2 * cap_jobs) ||
@@ -614,12 +646,16 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
       F.max_levels = maxd;
       F.adaptive = adaptive ? 1 : 0;
       F.big_order = PERM_MAX_JOB_N;
+      F.band = kSplitBand;
+      F.soft_order = kSoftOrder;
+      F.soft_cap_jobs = kSoftCapJobs;
       F.target_jobs = target;
       F.state = d_state;
       F.partial = d_partial;
       F.bar = d_bar;
       F.lvl_words = d_lw;
       F.lvl_maxo = d_lm;
+      F.lvl_maxopen = d_lo;
       F.err = reinterpret_cast<int32_t*>(d_stat);
       CK(cudaMemcpyAsync(d_state, &S, sizeof(S), cudaMemcpyHostToDevice, s));
       CK(cudaMemsetAsync(d_bar, 0, 8, s));
@@ -632,7 +668,7 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
       CK(cudaStreamSynchronize(s));
       const int32_t herr = (int32_t)(st0 & 0xffffffff);
       if (herr != 0) return (perm_status)herr;
-      if (!levels_left(S.level, S.ncur, S.max_order)) break;
+      if (!levels_left(S.level, S.ncur, S.max_open)) break;
       // stopped for room: grow, or hand over to the per-level loop
       if (cap_jobs >= kFusedMaxJobs || cap_words >= kFusedMaxWords) break;
       if (2 * S.ncur > cap_jobs) cap_jobs = std::min<int64_t>(kFusedMaxJobs, 4 * cap_jobs);
@@ -644,16 +680,18 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
     M.put(d_bar);
     M.put(d_lw);
     M.put(d_lm);
+    M.put(d_lo);
     cb = S.cb;
     cur = jb[cb].view();
     cur_arena = reinterpret_cast<uint64_t*>(ar[cb].p);
     ncur = S.ncur;
     max_order = S.max_order;
+    max_open = S.max_open;
     used_words = S.used_words;
     cur_arena_words = S.used_words;
     level0 = S.level;
   }
-  for (int level = level0; levels_left(level, ncur, max_order); ++level) {
+  for (int level = level0; levels_left(level, ncur, max_open); ++level) {
     // every parent reserves two child slots of its own block size
     const int64_t out_words = 2 * used_words;
     const int nb = cb ^ 1;
@@ -678,15 +716,16 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
     A.child_off_base = base;
     A.valid = valid;
     A.leaf_size = P->L;
+    A.split_floor = split_floor(max_open);
     A.err = reinterpret_cast<int32_t*>(d_stat);
     CK(launch_expand_level(A, max_order, s));
     CK(scan_exclusive_i32(valid, pos, 2 * ncur, g_tmp.p, g_tmp.cap, s));
     // the kept children: at most 2 * ncur; size the next arrays for that bound
     if (!jb[nb].ensure(M, 2 * ncur)) return PERM_ENOMEM;
-    CK(cudaMemsetAsync(d_stat + 1, 0, 24, s));
-    CK(launch_compact_jobs(slots.view(), valid, pos, 2 * ncur, jb[nb].view(), d_stat + 1, s));
-    long long st[4] = {0, 0, 0, 0};
-    CK(cudaMemcpyAsync(st, d_stat, 32, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(d_stat + 1, 0, 32, s));
+    CK(launch_compact_jobs(slots.view(), valid, pos, 2 * ncur, jb[nb].view(), std::max(P->L, 2), d_stat + 1, s));
+    long long st[5] = {0, 0, 0, 0, 0};
+    CK(cudaMemcpyAsync(st, d_stat, 40, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const int32_t herr = (int32_t)(st[0] & 0xffffffff);
     if (herr != 0) return (perm_status)herr;
@@ -697,6 +736,7 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
     ncur = st[3];
     max_order = (int)st[1];  // carried jobs keep their order
     used_words = st[2];
+    max_open = (int)st[4];
   }
   M.put(d_stat);
   // the current buffers become the job set; the rest is released
@@ -848,6 +888,12 @@ extern "C" perm_status perm_order(perm_jobs_t* J, int32_t kind, uint32_t* order_
 
 // ---------------------------------------------------------------- a7, a8: evaluate
 // prepare: split the queue, classify leaf variants, upload, size buffers.
+// resident depth-first warps per SM for a tile width
+static int dfs_wps(const perm_plan* P, int tile) {
+  if (P->opts.workers_per_sm > 0) return P->opts.workers_per_sm;
+  return tile <= 32 ? 24 : 10;
+}
+
 static perm_status eval_prepare(perm_jobs* J, const uint32_t* order) {
   perm_plan* P = J->plan;
   cudaStream_t s = P->s;
@@ -859,8 +905,8 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order) {
   J->ev = new EvalState();
   EvalState& E = *J->ev;
   E.d_q = dget<uint32_t>(M, n);
-  E.sum = dget<unsigned long long>(M, 3 + EVAL_KEYS);
-  E.ctr = dget<unsigned long long>(M, 2);
+  E.sum = dget<unsigned long long>(M, SUM_WORDS);
+  E.ctr = dget<unsigned long long>(M, 1 + EVAL_DFS_GROUPS);
   if (!E.d_q || !E.sum || !E.ctr) return PERM_ENOMEM;
   if (order) {
     std::vector<uint8_t> seen(n, 0);
@@ -878,7 +924,7 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order) {
   }
   // group the queue on the device: leaf jobs by kernel variant, then the
   // depth-first jobs by ring width, queue order kept inside every group
-  unsigned long long* hist = E.sum + 3;
+  unsigned long long* hist = E.sum + SUM_HIST;
   CK(cudaMemsetAsync(hist, 0, 8 * EVAL_KEYS, s));
   E.d_g = dget<uint32_t>(M, n);
   uint32_t* keys = dget<uint32_t>(M, 2 * n);
@@ -904,8 +950,9 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order) {
     nl += (int64_t)h[k];
   }
   E.nl = nl;
-  E.nd_w2 = (int64_t)h[EVAL_KEY_DFS];
-  E.nd = E.nd_w2 + (int64_t)h[EVAL_KEY_DFS + 1];
+  E.db[0] = 0;
+  for (int g = 0; g < EVAL_DFS_GROUPS; ++g) E.db[g + 1] = E.db[g] + (int64_t)h[EVAL_KEY_DFS + g];
+  E.nd = E.db[EVAL_DFS_GROUPS];
   E.d_lq = E.d_g;
   E.d_dq = E.d_g + nl;
   const int64_t nd = E.nd;
@@ -916,34 +963,38 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order) {
   E.d_rq = dget<uint32_t>(M, nd);
   E.rflags = dget<int32_t>(M, nd + 1);
   E.rpos = dget<int32_t>(M, nd + 1);
-  E.tile = J->max_order <= 32 ? 32 : 64;
   // the narrow variant (int32 tile, leaves <= 16 rows) unless the leaf order needs the wide one
   E.wide_first = P->L > 16;
-  E.wps = P->opts.workers_per_sm > 0 ? P->opts.workers_per_sm : (E.tile <= 32 ? 24 : 10);
   E.chunk = P->opts.chunk_log2 > 0 ? P->opts.chunk_log2 : 10;
-  int dfs_warps = 0;
-  for (bool w : {false, true}) {
-    const int wpb = dfs_warps_per_block(E.tile, w);
-    dfs_warps = std::max(dfs_warps, P->sms * ((E.wps + wpb - 1) / wpb) * wpb);
+  int dfs_warps = 0, max_tile = 32;
+  for (int g = 0; g < EVAL_DFS_GROUPS; ++g) {
+    if (E.db[g + 1] == E.db[g]) continue;
+    const int tile = dfs_group_tile(g);
+    max_tile = std::max(max_tile, tile);
+    for (bool w : {false, true}) {
+      const int wpb = dfs_warps_per_block(tile, w);
+      dfs_warps = std::max(dfs_warps, P->sms * ((dfs_wps(P, tile) + wpb - 1) / wpb) * wpb);
+    }
   }
-  E.undo_w = dfs_undo_words(E.tile);
+  E.undo_w = dfs_undo_words(max_tile);
   E.undo = nd > 0 ? dget<int64_t>(M, E.undo_w * dfs_warps) : nullptr;
   if (!E.counts || !E.prefix || !E.stmp || !E.d_rq || !E.rflags || !E.rpos || (nd > 0 && !E.undo))
     return PERM_ENOMEM;
   return PERM_OK;
 }
 
-static DfsArgs dfs_args(perm_jobs* J) {
+// arguments of depth-first group g over queue[0, nq)
+static DfsArgs dfs_args(perm_jobs* J, int g, const uint32_t* queue, int64_t nq) {
   perm_plan* P = J->plan;
   EvalState& E = *J->ev;
   DfsArgs D{};
-  D.queue = E.d_dq;
-  D.nq = E.nd_w2;
+  D.queue = queue;
+  D.nq = nq;
   D.jobs = J->a;
   D.arena = J->arena;
   D.mat_w = P->d_mat_w;
   D.leaf_size = P->L;
-  D.job_counter = E.ctr + 1;
+  D.job_counter = E.ctr + 1 + g;
   D.out = J->out;
   D.mat_acc = P->d_mat_acc;
   D.undo = E.undo;
@@ -971,17 +1022,16 @@ static cudaError_t eval_enqueue(perm_jobs* J, cudaStream_t s) {
   EQ(cudaMemsetAsync(J->out.leaves, 0, 8 * nj, s));
   EQ(cudaMemsetAsync(J->out.nodes, 0, 8 * nj, s));
   EQ(cudaMemsetAsync(P->d_mat_acc, 0, 32ull * P->count, s));
-  EQ(cudaMemsetAsync(E.ctr, 0, 16, s));
-  EQ(cudaMemsetAsync(E.sum, 0xff, 8, s));
-  if (E.nd > 0) {
-    // ring width 2 then 4; each launch has its own job counter
-    DfsArgs D = dfs_args(J);
-    EQ(launch_dfs(D, E.tile, E.wide_first, 2, P->sms, E.wps, s));
-    D.queue = E.d_dq + E.nd_w2;
-    D.nq = E.nd - E.nd_w2;
-    D.job_counter = E.ctr;
-    EQ(launch_dfs(D, E.tile, E.wide_first, 4, P->sms, E.wps, s));
-    launches += 2;
+  EQ(cudaMemsetAsync(E.ctr, 0, 8 * (1 + EVAL_DFS_GROUPS), s));
+  EQ(cudaMemsetAsync(E.sum + SUM_STATUS, 0xff, 8, s));
+  // depth-first groups: tile 64 (the largest jobs) first; each its own job counter
+  for (int g = 0; g < EVAL_DFS_GROUPS; ++g) {
+    const int64_t nq = E.db[g + 1] - E.db[g];
+    if (nq == 0) continue;
+    const int tile = dfs_group_tile(g);
+    EQ(launch_dfs(dfs_args(J, g, E.d_dq + E.db[g], nq), tile, E.wide_first, dfs_group_w(g), P->sms,
+                  dfs_wps(P, tile), s));
+    ++launches;
   }
   if (E.nl > 0) {
     // one task scan for the grouped leaf queue, then one persistent grid per
@@ -999,12 +1049,14 @@ static cudaError_t eval_enqueue(perm_jobs* J, cudaStream_t s) {
   }
   if (E.nd > 0 && !E.wide_first) {
     // jobs the narrow depth-first variant handed on, for the wide one
-    EQ(launch_retry_collect(E.d_dq, E.nd, E.nd_w2, J->out.status, E.rflags, E.rpos, E.stmp, E.stb, E.d_rq,
-                            E.sum + 1, s));
+    RetryBounds rb;
+    for (int g = 0; g <= EVAL_DFS_GROUPS; ++g) rb.b[g] = E.db[g];
+    EQ(launch_retry_collect(E.d_dq, E.nd, rb, J->out.status, E.rflags, E.rpos, E.stmp, E.stb, E.d_rq,
+                            E.sum + SUM_RETRY, s));
     launches += 4;
   }
   if (J->n > 0) {
-    EQ(launch_status_summary(J->out.status, J->n, E.sum, s));
+    EQ(launch_status_summary(J->out.status, J->n, E.sum + SUM_STATUS, s));
     ++launches;
   }
 #undef EQ
@@ -1021,31 +1073,32 @@ static perm_status eval_finish(perm_jobs* J, perm_job_result* results) {
   const int64_t n = J->n;
   CK(cudaEventSynchronize(P->ev1));
   CK(cudaEventElapsedTime(&P->last_ms, P->ev0, P->ev1));
-  unsigned long long sum[3] = {~0ull, 0ull, 0ull};
+  unsigned long long sum[SUM_HIST];
+  for (int k = 0; k < SUM_HIST; ++k) sum[k] = k == SUM_STATUS ? ~0ull : 0ull;
   if (n) CK(cudaMemcpyAsync(sum, E.sum, sizeof(sum), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (n && E.nd > 0 && !E.wide_first && sum[2] > 0) {
-    const int64_t nr2 = (int64_t)sum[1], nr = (int64_t)sum[2];
-    CK(cudaMemsetAsync(E.ctr, 0, 16, s));
+  const unsigned long long* at = sum + SUM_RETRY;
+  if (n && E.nd > 0 && !E.wide_first && at[EVAL_DFS_GROUPS] > 0) {
+    // jobs the narrow variant handed on run again on the wide one, by group
+    CK(cudaMemsetAsync(E.ctr, 0, 8 * (1 + EVAL_DFS_GROUPS), s));
     float ms2 = 0.f;
-    DfsArgs D = dfs_args(J);
     CK(cudaEventRecord(P->ev0, s));
-    D.queue = E.d_rq;
-    D.nq = nr2;
-    CK(launch_dfs(D, E.tile, true, 2, P->sms, E.wps, s));
-    D.queue = E.d_rq + nr2;
-    D.nq = nr - nr2;
-    D.job_counter = E.ctr;
-    CK(launch_dfs(D, E.tile, true, 4, P->sms, E.wps, s));
+    for (int g = 0; g < EVAL_DFS_GROUPS; ++g) {
+      const int64_t nr = (int64_t)(at[g + 1] - at[g]);
+      if (nr == 0) continue;
+      const int tile = dfs_group_tile(g);
+      CK(launch_dfs(dfs_args(J, g, E.d_rq + at[g], nr), tile, true, dfs_group_w(g), P->sms, dfs_wps(P, tile), s));
+      P->last_launches += 1;
+    }
     CK(cudaEventRecord(P->ev1, s));
-    CK(cudaMemsetAsync(E.sum, 0xff, 8, s));
-    CK(launch_status_summary(J->out.status, n, E.sum, s));
-    CK(cudaMemcpyAsync(sum, E.sum, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(E.sum + SUM_STATUS, 0xff, 8, s));
+    CK(launch_status_summary(J->out.status, n, E.sum + SUM_STATUS, s));
+    CK(cudaMemcpyAsync(sum + SUM_STATUS, E.sum + SUM_STATUS, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaEventSynchronize(P->ev1));
     CK(cudaEventElapsedTime(&ms2, P->ev0, P->ev1));
     CK(cudaStreamSynchronize(s));
     P->last_ms += ms2;
-    P->last_launches += 3;
+    P->last_launches += 1;
   }
   if (results && n) {
     std::vector<unsigned long long> acc(4 * n), t0(n), t1(n), lv(n), nd_(n);
@@ -1080,7 +1133,7 @@ static perm_status eval_finish(perm_jobs* J, perm_job_result* results) {
     }
   }
   // the lowest job index with a failed status decides the call's status
-  if (sum[0] != ~0ull) return (perm_status)(sum[0] & 255);
+  if (sum[SUM_STATUS] != ~0ull) return (perm_status)(sum[SUM_STATUS] & 255);
   P->evaluated = true;
   return PERM_OK;
 }

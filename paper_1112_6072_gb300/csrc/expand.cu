@@ -16,7 +16,9 @@
 // q; a column pivot does the same with rows.  A scalar factor multiplies the
 // child's coefficient.  Children holding a zero line are not emitted.  A
 // parent of order <= max(L, 2), with s >= 5, or with no levels left is
-// carried unchanged to slot 2p.
+// carried unchanged to slot 2p.  With a split floor (automatic depth), a
+// parent still to split whose order is below the floor waits: it is carried
+// with its levels left, so the largest jobs of a batch are split first.
 //
 // Two drivers share the per-parent routine:
 //  - k_expand_level: one level per launch; the host reserves two blocks of
@@ -142,8 +144,10 @@ struct ExpandCtx {
   unsigned long long* bump;       // bump mode: words used in arena_out
   int64_t cap_words;              // bump mode: arena_out capacity
   int32_t* max_order;             // bump mode: largest kept order
+  int32_t* max_open;              // bump mode: largest order of a kept job still to split
   int32_t* valid;
   int32_t leaf_size;
+  int32_t split_floor;            // parents of a lower order wait for a later level
   int32_t* err;
 };
 
@@ -169,6 +173,28 @@ __device__ __forceinline__ int64_t child_block(const ExpandCtx& X, int64_t p, in
   return (int64_t)o;
 }
 
+// Parent p unchanged into slot 2p with depth_left dl_out.
+__device__ void carry_parent(const ExpandCtx& X, int64_t p, const uint64_t* src, int64_t pw, int m, int nnz,
+                             int dl_out, int lane) {
+  const int64_t o = child_block(X, p, 0, pw, pw, lane);
+  if (o >= 0) copy_words(X.arena_out + o, src, pw, lane);
+  if (lane == 0) {
+    const int64_t c0 = 2 * p;
+    X.valid[c0] = o >= 0 ? 1 : 0;
+    X.valid[c0 + 1] = 0;
+    if (o >= 0) {
+      X.child.m[c0] = m;
+      X.child.nnz[c0] = nnz;
+      X.child.off[c0] = o;
+      X.child.mat[c0] = X.parent.mat[p];
+      X.child.depth_left[c0] = dl_out;
+      for (int w = 0; w < 4; ++w) X.child.coef[4 * c0 + w] = X.parent.coef[4 * p + w];
+      if (X.max_order) atomicMax(X.max_order, m);
+      if (X.max_open && dl_out > 0) atomicMax(X.max_open, m);
+    }
+  }
+}
+
 // Divide parent p (one warp).  ccnt: the warp's shared-memory column counts
 // (RPL * 32 entries); stage: its kStageWords-word copy of the parent block.
 template <int RPL>
@@ -178,7 +204,12 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
   const int64_t off = X.parent.off[p];
   const int dl = X.parent.depth_left[p];
   const int64_t pw = blk_words(m, nnz);
+  const int cut = X.leaf_size > 2 ? X.leaf_size : 2;
   __syncwarp();  // the previous parent's reads of stage and ccnt are done
+  if (dl > 0 && m > cut && m < X.split_floor) {
+    carry_parent(X, p, X.arena_in + off, pw, m, nnz, dl, lane);
+    return;
+  }
   const uint64_t* src = X.arena_in + off;
   if (pw <= kStageWords) {
     copy_words(stage, src, pw, lane);
@@ -209,28 +240,12 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
   const int s = (int)(key >> 17);
   const bool is_col = (key >> 16) & 1;
   const int idx = (int)(key & 0xffff);
-  const int cut = X.leaf_size > 2 ? X.leaf_size : 2;
   if (s == 0) {  // zero line: nothing to emit
     if (lane == 0) X.valid[2 * p] = X.valid[2 * p + 1] = 0;
     return;
   }
   if (dl <= 0 || m <= cut || s >= 5) {
-    const int64_t o = child_block(X, p, 0, pw, pw, lane);
-    if (o >= 0) copy_words(X.arena_out + o, src, pw, lane);
-    if (lane == 0) {
-      const int64_t c0 = 2 * p;
-      X.valid[c0] = o >= 0 ? 1 : 0;
-      X.valid[c0 + 1] = 0;
-      if (o >= 0) {
-        X.child.m[c0] = m;
-        X.child.nnz[c0] = nnz;
-        X.child.off[c0] = o;
-        X.child.mat[c0] = X.parent.mat[p];
-        X.child.depth_left[c0] = 0;
-        for (int w = 0; w < 4; ++w) X.child.coef[4 * c0 + w] = X.parent.coef[4 * p + w];
-        if (X.max_order) atomicMax(X.max_order, m);
-      }
-    }
+    carry_parent(X, p, src, pw, m, nnz, 0, lane);
     return;
   }
   // pivot line's nonzero positions (ascending) and values
@@ -398,6 +413,7 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
         u256 cc = cs.fac == 1 ? pcoef : u256_mul_s64(pcoef, cs.fac);
         for (int w = 0; w < 4; ++w) X.child.coef[4 * slot + w] = cc.w[w];
         if (X.max_order) atomicMax(X.max_order, mc);
+        if (X.max_open && dl - 1 > 0 && mc > cut) atomicMax(X.max_open, mc);
       }
     }
   }
@@ -418,8 +434,10 @@ __global__ void __launch_bounds__(kLevelWarps * 32) k_expand_level(ExpandLevelAr
   X.bump = nullptr;
   X.cap_words = 0;
   X.max_order = nullptr;
+  X.max_open = nullptr;
   X.valid = A.valid;
   X.leaf_size = A.leaf_size;
+  X.split_floor = A.split_floor;
   X.err = A.err;
   const int64_t nwarps = (int64_t)gridDim.x * kLevelWarps;
   for (int64_t p = (int64_t)blockIdx.x * kLevelWarps + wib; p < A.np; p += nwarps)
@@ -507,9 +525,10 @@ __global__ void __launch_bounds__(kFrontThreads) k_expand_front(ExpandFrontArgs 
     bool stop = failed || S.level >= F.max_levels || S.ncur <= 0 || S.max_order > RPL * 32 ||
                 2 * S.ncur > F.cap_jobs || 2 * S.used_words > F.cap_words;
     if (!stop && F.adaptive) {
-      const bool big = S.max_order > F.big_order;
-      const bool more = S.ncur < F.target_jobs && S.max_order > F.leaf_size;
-      stop = !big && !more;
+      const bool big = S.max_open > F.big_order;
+      const bool soft = S.max_open > F.soft_order && S.ncur < F.soft_cap_jobs;
+      const bool more = S.ncur < F.target_jobs && S.max_open > 0;
+      stop = !big && !soft && !more;
     }
     if (stop) break;
     const int cb = S.cb;
@@ -522,8 +541,10 @@ __global__ void __launch_bounds__(kFrontThreads) k_expand_front(ExpandFrontArgs 
     X.bump = F.lvl_words + S.level;
     X.cap_words = F.cap_words;
     X.max_order = F.lvl_maxo + S.level;
+    X.max_open = F.lvl_maxopen + S.level;
     X.valid = F.valid;
     X.leaf_size = F.leaf_size;
+    X.split_floor = F.adaptive ? S.max_open - F.band : 0;
     X.err = F.err;
     const int64_t p0 = S.ncur * b / G, p1 = S.ncur * (b + 1) / G;
     for (int64_t p = p0 + wib; p < p1; p += kFrontWarps) expand_parent<RPL>(X, p, lane, ccnt[wib], stage + wib * kStageWords);
@@ -564,6 +585,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_expand_front(ExpandFrontArgs 
     S.ncur = total;
     S.used_words = (int64_t)__ldcg(F.lvl_words + S.level);
     S.max_order = __ldcg(F.lvl_maxo + S.level);
+    S.max_open = __ldcg(F.lvl_maxopen + S.level);
     S.cb ^= 1;
     S.level += 1;
   }
@@ -628,15 +650,17 @@ __global__ void k_child_capacity(JobArrays parent, int64_t np, int64_t* words) {
 }
 
 // stat[0]: largest kept order, stat[1]: words of the kept blocks, stat[2]:
-// kept jobs -- reduced per warp, one atomic per warp.
+// kept jobs, stat[3]: largest order of a kept job still to split (depth
+// left and order above cut) -- reduced per warp, one atomic per warp.
 __global__ void k_compact(JobArrays src, const int32_t* valid, const int32_t* pos, int64_t nslots, JobArrays dst,
-                          long long* stat) {
+                          int cut, long long* stat) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool keep = s < nslots && valid[s];
-  unsigned m = 0, words = 0;
+  unsigned m = 0, words = 0, mo = 0;
   if (keep) {
     const int64_t d = pos[s];
     m = (unsigned)src.m[s];
+    mo = src.depth_left[s] > 0 && src.m[s] > cut ? m : 0u;
     words = (unsigned)blk_words(src.m[s], src.nnz[s]);
     dst.m[d] = src.m[s];
     dst.nnz[d] = src.nnz[s];
@@ -646,12 +670,14 @@ __global__ void k_compact(JobArrays src, const int32_t* valid, const int32_t* po
     for (int w = 0; w < 4; ++w) dst.coef[4 * d + w] = src.coef[4 * s + w];
   }
   const unsigned mx = __reduce_max_sync(0xffffffffu, m);
+  const unsigned mox = __reduce_max_sync(0xffffffffu, mo);
   const unsigned sw = __reduce_add_sync(0xffffffffu, words);
   const unsigned nk = __reduce_add_sync(0xffffffffu, keep ? 1u : 0u);
   if ((threadIdx.x & 31) == 0 && nk) {
     atomicMax(stat, (long long)mx);
     atomicAdd(reinterpret_cast<unsigned long long*>(stat + 1), (unsigned long long)sw);
     atomicAdd(reinterpret_cast<unsigned long long*>(stat + 2), (unsigned long long)nk);
+    atomicMax(stat + 3, (long long)mox);
   }
 }
 
@@ -662,8 +688,8 @@ cudaError_t launch_child_capacity(const JobArrays& parent, int64_t np, int64_t* 
 }
 
 cudaError_t launch_compact_jobs(const JobArrays& src, const int32_t* valid, const int32_t* pos, int64_t nslots,
-                                JobArrays dst, long long* stat, cudaStream_t s) {
+                                JobArrays dst, int cut, long long* stat, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
-  k_compact<<<(unsigned)((nslots + 255) / 256), 256, 0, s>>>(src, valid, pos, nslots, dst, stat);
+  k_compact<<<(unsigned)((nslots + 255) / 256), 256, 0, s>>>(src, valid, pos, nslots, dst, cut, stat);
   return cudaGetLastError();
 }

@@ -8,6 +8,14 @@
 #include "../../include/perm.h"
 #include "jobs.cuh"
 
+// Evaluation keys of a queue: leaf jobs (order <= leaf_max) get their kernel
+// variant (nmax index | W bit | path << 3, < 64), the others the
+// depth-first group EVAL_KEY_DFS + g, g = 2 * (order <= 32) + (ring width
+// 4): tile 64 before tile 32; hist[key] counts them.
+#define EVAL_KEY_DFS 64
+#define EVAL_DFS_GROUPS 4
+#define EVAL_KEYS (EVAL_KEY_DFS + EVAL_DFS_GROUPS)
+
 // ---- scans and sorts (CUB, header source) --------------------------------
 cudaError_t scan_exclusive_u64(const uint64_t* in, uint64_t* out, int64_t n, void* tmp, size_t tmp_bytes,
                                cudaStream_t s);
@@ -30,19 +38,19 @@ size_t sort_tmp_bytes_u32(int64_t n, int end_bit);
 // (unchanged when there is none; set it to ~0 first).
 cudaError_t launch_status_summary(const int32_t* status, int64_t n, unsigned long long* out, cudaStream_t s);
 // Stable compaction of the depth-first queue's jobs whose status is
-// DFS_RETRY into rq; counts[0] = those among the first n2 entries, counts[1]
-// = all.  flags and pos hold n + 1 entries each.
-cudaError_t launch_retry_collect(const uint32_t* dq, int64_t n, int64_t n2, const int32_t* status, int32_t* flags,
-                                 int32_t* pos, void* scan_tmp, size_t scan_tmp_bytes, uint32_t* rq,
-                                 unsigned long long* counts, cudaStream_t s);
+// DFS_RETRY into rq; at[g] = retried jobs before queue position bounds.b[g]
+// (g <= EVAL_DFS_GROUPS), so the retry queue keeps the queue's groups.
+// flags and pos hold n + 1 entries each.
+struct RetryBounds {
+  int64_t b[EVAL_DFS_GROUPS + 1];
+};
+cudaError_t launch_retry_collect(const uint32_t* dq, int64_t n, RetryBounds bounds, const int32_t* status,
+                                 int32_t* flags, int32_t* pos, void* scan_tmp, size_t scan_tmp_bytes, uint32_t* rq,
+                                 unsigned long long* at, cudaStream_t s);
 
 // ---- K2 leaf batch -----------------------------------------------------------
-// Evaluation keys of a queue: leaf jobs (order <= leaf_max) get their kernel
-// variant (nmax index | W bit | path << 3, < 64), the others
-// EVAL_KEY_DFS + (ring width 4); hist[key] counts them (zero it first,
-// EVAL_KEYS entries).
-#define EVAL_KEY_DFS 64
-#define EVAL_KEYS 66
+// Evaluation key (see EVAL_KEY_DFS) of every queue position, the queue's
+// jobs in vals, and the key histogram (zero it first, EVAL_KEYS entries).
 cudaError_t launch_eval_keys(const uint32_t* queue, int64_t n, const JobArrays& jobs, const uint64_t* arena,
                              const int32_t* mat_w, int leaf_max, uint32_t* keys, uint32_t* vals,
                              unsigned long long* hist, cudaStream_t stream);
@@ -73,6 +81,7 @@ struct ExpandLevelArgs {
   const int64_t* child_off_base;
   int32_t* valid;   // 2*np
   int32_t leaf_size;
+  int32_t split_floor;  // parents of a lower order (with depth left, above the leaf order) wait
   int32_t* err;     // device flag: first error status
 };
 cudaError_t launch_expand_level(const ExpandLevelArgs& a, int max_order, cudaStream_t s);
@@ -80,18 +89,21 @@ cudaError_t launch_expand_level(const ExpandLevelArgs& a, int max_order, cudaStr
 // Consecutive levels in one cooperative launch.  The current jobs are
 // buf[state.cb] with their blocks in arena[state.cb] (state.used_words
 // words).  Runs a level while: level < max_levels, 0 < ncur, 2 * ncur <=
-// cap_jobs, 2 * used_words <= cap_words, and (when adaptive) max_order >
-// big_order or (ncur < target_jobs and max_order > leaf_size).  The state
-// is updated in place; the children of a level are compacted in natural
-// order into the other buffer.  bar, lvl_words and lvl_maxo (max_levels
-// entries) must be zero; partial holds PERM_FRONT_MAX_BLOCKS entries.
+// cap_jobs, 2 * used_words <= cap_words, and (when adaptive) max_open >
+// big_order, or max_open > soft_order and ncur < soft_cap_jobs, or (ncur <
+// target_jobs and max_open > 0), where max_open is the
+// largest order of a job still to split; adaptive levels split only parents
+// of order >= max_open - band.  The state is updated in place; the children
+// of a level are compacted in natural order into the other buffer.  bar,
+// lvl_words, lvl_maxo and lvl_maxopen (max_levels entries) must be zero;
+// partial holds PERM_FRONT_MAX_BLOCKS entries.
 struct ExpandFrontState {
   int64_t ncur;
   int64_t used_words;
   int32_t level;
   int32_t max_order;
+  int32_t max_open;
   int32_t cb;
-  int32_t pad;
 };
 #define PERM_FRONT_MAX_BLOCKS 1024
 struct ExpandFrontArgs {
@@ -105,12 +117,16 @@ struct ExpandFrontArgs {
   int32_t max_levels;
   int32_t adaptive;
   int32_t big_order;
+  int32_t band;
+  int32_t soft_order;
+  int64_t soft_cap_jobs;
   int64_t target_jobs;
   ExpandFrontState* state;
   long long* partial;
   unsigned long long* bar;
   unsigned long long* lvl_words;
   int32_t* lvl_maxo;
+  int32_t* lvl_maxopen;
   int32_t* err;
 };
 // *grid = blocks launched, 0 when the device has no cooperative launch (the
@@ -119,10 +135,11 @@ cudaError_t launch_expand_front(const ExpandFrontArgs& a, int max_order, int* gr
 // words[p] = 2 * blk_words(parent p) (capacity for its two children)
 cudaError_t launch_child_capacity(const JobArrays& parent, int64_t np, int64_t* words, cudaStream_t s);
 // Compact valid slots into dst (natural order kept).  Accumulates into
-// stat[0] the largest kept order, stat[1] the kept blocks' words and
-// stat[2] the kept job count (zero them first).
+// stat[0] the largest kept order, stat[1] the kept blocks' words, stat[2]
+// the kept job count and stat[3] the largest order of a kept job with depth
+// left and order above cut (zero them first).
 cudaError_t launch_compact_jobs(const JobArrays& src, const int32_t* valid, const int32_t* pos, int64_t nslots,
-                                JobArrays dst, long long* stat, cudaStream_t s);
+                                JobArrays dst, int cut, long long* stat, cudaStream_t s);
 
 // ---- K3 depth-first evaluator --------------------------------------------------
 struct DfsArgs {

@@ -117,8 +117,8 @@ __device__ int leaf_class(uint32_t job, const JobArrays& jobs, const uint64_t* _
 }
 
 // One thread per queue position: the sort key of its job -- the leaf
-// variant (< 64) for jobs of order <= leaf_max, else 64 + (W == 4) for the
-// depth-first evaluator -- and a histogram of the keys.
+// variant (< 64) for jobs of order <= leaf_max, else the depth-first group
+// EVAL_KEY_DFS + 2 * (order <= 32) + (W == 4) -- and a histogram of the keys.
 __global__ void k_eval_keys(const uint32_t* __restrict__ queue, int64_t n, JobArrays jobs,
                             const uint64_t* __restrict__ arena, const int32_t* __restrict__ mat_w, int leaf_max,
                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
@@ -132,7 +132,7 @@ __global__ void k_eval_keys(const uint32_t* __restrict__ queue, int64_t n, JobAr
     if (m <= leaf_max)
       key = (uint32_t)leaf_class(job, jobs, arena, mat_w);
     else
-      key = EVAL_KEY_DFS + (mat_w[jobs.mat[job]] == 4 ? 1u : 0u);
+      key = EVAL_KEY_DFS + (m <= 32 ? 2u : 0u) + (mat_w[jobs.mat[job]] == 4 ? 1u : 0u);
     keys[q] = key;
     vals[q] = job;
   }

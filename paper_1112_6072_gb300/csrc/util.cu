@@ -88,27 +88,26 @@ __global__ void k_retry_flags(const uint32_t* __restrict__ dq, int64_t n, const 
   if (k == n) flags[k] = 0;  // the scan's last entry is the total
 }
 
-__global__ void k_retry_scatter(const uint32_t* __restrict__ dq, int64_t n, int64_t n2,
+__global__ void k_retry_scatter(const uint32_t* __restrict__ dq, int64_t n, RetryBounds bounds,
                                 const int32_t* __restrict__ flags, const int32_t* __restrict__ pos,
-                                uint32_t* __restrict__ rq, unsigned long long* counts) {
+                                uint32_t* __restrict__ rq, unsigned long long* at) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k < n && flags[k]) rq[pos[k]] = dq[k];
   if (k == n) {
-    counts[0] = (unsigned long long)pos[n2];
-    counts[1] = (unsigned long long)pos[n];
+    for (int g = 0; g <= EVAL_DFS_GROUPS; ++g) at[g] = (unsigned long long)pos[bounds.b[g]];
   }
 }
 
-cudaError_t launch_retry_collect(const uint32_t* dq, int64_t n, int64_t n2, const int32_t* status, int32_t* flags,
-                                 int32_t* pos, void* scan_tmp, size_t scan_tmp_bytes, uint32_t* rq,
-                                 unsigned long long* counts, cudaStream_t s) {
+cudaError_t launch_retry_collect(const uint32_t* dq, int64_t n, RetryBounds bounds, const int32_t* status,
+                                 int32_t* flags, int32_t* pos, void* scan_tmp, size_t scan_tmp_bytes, uint32_t* rq,
+                                 unsigned long long* at, cudaStream_t s) {
   const unsigned blocks = (unsigned)((n + 1 + 255) / 256);
   k_retry_flags<<<blocks, 256, 0, s>>>(dq, n, status, flags);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = scan_exclusive_i32(flags, pos, n + 1, scan_tmp, scan_tmp_bytes, s);
   if (e != cudaSuccess) return e;
-  k_retry_scatter<<<blocks, 256, 0, s>>>(dq, n, n2, flags, pos, rq, counts);
+  k_retry_scatter<<<blocks, 256, 0, s>>>(dq, n, bounds, flags, pos, rq, at);
   return cudaGetLastError();
 }
 
