@@ -197,8 +197,12 @@ __device__ void carry_parent(const ExpandCtx& X, int64_t p, const uint64_t* src,
 
 // Divide parent p (one warp).  ccnt: the warp's shared-memory column counts
 // (RPL * 32 entries); stage: its kStageWords-word copy of the parent block.
+// only_child 0 or 1: build that child alone (two warps share a parent when
+// the frontier is small; the child-0 warp also writes the carried and
+// dropped cases); -1: both.
 template <int RPL>
-__device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* ccnt, uint64_t* stage) {
+__device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* ccnt, uint64_t* stage,
+                              int only_child = -1) {
   const int m = X.parent.m[p];
   const int nnz = X.parent.nnz[p];
   const int64_t off = X.parent.off[p];
@@ -207,7 +211,7 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
   const int cut = X.leaf_size > 2 ? X.leaf_size : 2;
   __syncwarp();  // the previous parent's reads of stage and ccnt are done
   if (dl > 0 && m > cut && m < X.split_floor) {
-    carry_parent(X, p, X.arena_in + off, pw, m, nnz, dl, lane);
+    if (only_child != 1) carry_parent(X, p, X.arena_in + off, pw, m, nnz, dl, lane);
     return;
   }
   const uint64_t* src = X.arena_in + off;
@@ -241,11 +245,11 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
   const bool is_col = (key >> 16) & 1;
   const int idx = (int)(key & 0xffff);
   if (s == 0) {  // zero line: nothing to emit
-    if (lane == 0) X.valid[2 * p] = X.valid[2 * p + 1] = 0;
+    if (lane == 0 && only_child != 1) X.valid[2 * p] = X.valid[2 * p + 1] = 0;
     return;
   }
   if (dl <= 0 || m <= cut || s >= 5) {
-    carry_parent(X, p, src, pw, m, nnz, 0, lane);
+    if (only_child != 1) carry_parent(X, p, src, pw, m, nnz, 0, lane);
     return;
   }
   // pivot line's nonzero positions (ascending) and values
@@ -293,6 +297,7 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
   for (int w = 0; w < 4; ++w) pcoef.w[w] = X.parent.coef[4 * p + w];
   const int mc = m - 1;
   for (int c = 0; c < 2; ++c) {
+    if (only_child >= 0 && c != only_child) continue;
     const int64_t slot = 2 * p + c;
     int kind;  // 1 merge(pos[x], pos[x+1]), 2 minor(pos[x])
     int x;
@@ -547,7 +552,14 @@ __global__ void __launch_bounds__(kFrontThreads) k_expand_front(ExpandFrontArgs 
     X.split_floor = F.adaptive ? S.max_open - F.band : 0;
     X.err = F.err;
     const int64_t p0 = S.ncur * b / G, p1 = S.ncur * (b + 1) / G;
-    for (int64_t p = p0 + wib; p < p1; p += kFrontWarps) expand_parent<RPL>(X, p, lane, ccnt[wib], stage + wib * kStageWords);
+    if (2 * S.ncur <= G * kFrontWarps) {
+      // small frontier: a warp per child, halving the level's latency
+      for (int64_t t = 2 * p0 + wib; t < 2 * p1; t += kFrontWarps)
+        expand_parent<RPL>(X, t >> 1, lane, ccnt[wib], stage + wib * kStageWords, (int)(t & 1));
+    } else {
+      for (int64_t p = p0 + wib; p < p1; p += kFrontWarps)
+        expand_parent<RPL>(X, p, lane, ccnt[wib], stage + wib * kStageWords);
+    }
     __syncthreads();
     long long kept = 0;
     for (int64_t t = 2 * p0 + threadIdx.x; t < 2 * p1; t += kFrontThreads) kept += F.valid[t];

@@ -304,23 +304,37 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32)
 // job's matrix accumulator (Algorithm PH, Step 4).
 __global__ void k_leaf_finalize(const uint32_t* __restrict__ queue, int64_t nq, JobArrays jobs,
                                 JobOut out, unsigned long long* __restrict__ mat_acc) {
-  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= nq) return;
-  const uint32_t job = queue[q];
-  if (out.status[job] != 0) return;
-  const int m = jobs.m[job];
-  u256 s;
-  for (int k = 0; k < 4; ++k) s.w[k] = out.acc[4ll * job + k];
-  if (m >= 2) {
-    s = u256_shr(s, m - 1);
-    if ((m - 1) & 1) s = u256_neg(s);
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  u256 v = u256_zero();
+  int mat = -1;
+  if (q < nq) {
+    const uint32_t job = queue[q];
+    mat = jobs.mat[job];
+    if (out.status[job] == 0) {
+      const int m = jobs.m[job];
+      u256 s;
+      for (int k = 0; k < 4; ++k) s.w[k] = out.acc[4ll * job + k];
+      if (m >= 2) {
+        s = u256_shr(s, m - 1);
+        if ((m - 1) & 1) s = u256_neg(s);
+      }
+      u256 c;
+      for (int k = 0; k < 4; ++k) c.w[k] = jobs.coef[4ll * job + k];
+      v = u256_mul(s, c);
+      for (int k = 0; k < 4; ++k) out.acc[4ll * job + k] = v.w[k];
+      out.nodes[job] = 1;
+    }
   }
-  u256 c;
-  for (int k = 0; k < 4; ++k) c.w[k] = jobs.coef[4ll * job + k];
-  u256 v = u256_mul(s, c);
-  for (int k = 0; k < 4; ++k) out.acc[4ll * job + k] = v.w[k];
-  out.nodes[job] = 1;
-  atomic_add_words(mat_acc + 4ll * jobs.mat[job], v.w, 4);
+  // one accumulator update per warp when the whole warp serves one matrix
+  // (failed jobs add zero), else one per job
+  if (__match_any_sync(0xffffffffu, mat) == 0xffffffffu) {
+    if (mat < 0) return;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v = u256_add(v, shfl_down_u256(v, d));
+    if ((threadIdx.x & 31) == 0) atomic_add_words(mat_acc + 4ll * mat, v.w, 4);
+  } else if (mat >= 0) {
+    atomic_add_words(mat_acc + 4ll * mat, v.w, 4);
+  }
 }
 
 __global__ void k_leaf_reject(const uint32_t* __restrict__ queue, int64_t nq, JobOut out) {
