@@ -378,6 +378,138 @@ def run_mixed(pk, torch, args):
     return out
 
 
+KENDALL_SEED = 7000
+
+
+def _train_cost_model(pk):
+    """The learned cost model (no KKLLL feature) on the job times of the
+    n = 36 and C60 whole paths."""
+    from paper_1112_6072_gb300 import learned
+
+    Xs, ts = [], []
+    for a, kw in ((W.regular3(36, 1), dict(split_depth=20, leaf_size=16)), (W.c60(C60_SEED), dict(leaf_size=12))):
+        with pk.Plan([a], model_uses_estimate=False, **kw) as p:
+            p.expand()
+            X, t, _ = learned.collect(p, "natural")
+        Xs.append(X)
+        ts.append(t)
+    return learned.train(np.concatenate(Xs), np.concatenate(ts), steps=600)
+
+
+def _whole_path(pk, torch, a, leaf):
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    with pk.Plan([a], leaf_size=leaf, order="natural", timeout_ns=3600 * 10**9) as p:
+        p.expand()
+        p.order("natural")
+        p.evaluate()
+        v = p.result(0)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t, v
+
+
+def _estimates(pk, mats, params):
+    """KKLLL log AP (T = m^2 trials), the job features (KKLLL feature
+    included) and the pretrained cost model's predicted log time of each
+    matrix as one job (that model does not use the KKLLL feature)."""
+    from paper_1112_6072_gb300 import learned
+
+    with pk.Plan(mats, split_depth=0, leaf_size=14) as p:
+        nj = p.expand()
+        assert nj == len(mats)
+        ap = p.estimate()
+        feats = p.features()
+    f0 = feats.copy()
+    f0[:, 10] = 0.0
+    return ap.astype(float).tolist(), feats, learned.predict_log_time(params, f0).astype(float).tolist()
+
+
+def _cross_validated(feats, times):
+    """Predictions of a cost model trained on the other half of the group
+    (even / odd positions), for each half."""
+    from paper_1112_6072_gb300 import learned
+
+    n = len(times)
+    t = np.asarray(times, dtype=np.float64) * 1e9
+    pred = np.zeros(n)
+    idx = np.arange(n)
+    for fold in (0, 1):
+        te = idx % 2 == fold
+        prm, _ = learned.train(feats[~te], t[~te], steps=600)
+        pred[te] = learned.predict_log_time(prm, feats[te])
+    return pred.tolist()
+
+
+def run_kendall(pk, torch, args):
+    """Tables T2-T4 analog (Section 3.2): Kendall tau-b of the computing time
+    T_i of each matrix or sub-matrix (whole path on the GPU, the matrix alone)
+    against its exact permanent P_i, its KKLLL estimate AP_i and the learned
+    cost model's prediction (pretrained on the n = 36 and C60 job times, and
+    cross-validated: trained on the other half of the same group).  T2: 100 random 0/1 matrices, n = 60, S = 4n
+    nonzeros (no zero line).  T3: C100 divided by Eq. 2 at depth 20 (jobs of
+    order 80).  T4: I + A of C60 (coordinates, shuffle seed 60) divided at
+    depth 8 (jobs of order 52)."""
+    from paper_1112_6072_gb300 import kendall
+
+    def log(*a):
+        print(*a, file=sys.stderr, flush=True)
+
+    params, loss = _train_cost_model(pk)
+    out = {"model_loss": loss}
+    groups = {"T2": [W.random01(60, 240, KENDALL_SEED + i) for i in range(100)]}
+    coefs_of = {}
+    for name, a, d in (("T3", W.paper_adjacency("c100"), 20),
+                       ("T4", W.c60(C60_SEED) + np.eye(60, dtype=np.int64), 8)):
+        with pk.Plan([a], split_depth=d, leaf_size=14) as p:
+            p.expand()
+            jobs = p.jobs_export()
+        groups[name] = [m for _, m, _ in jobs]
+        coefs_of[name] = [c for _, _, c in jobs]
+        # the jobs' coefficients multiply their permanents into per(A)
+        out[name + "_split"] = {"depth": d, "jobs": len(jobs), "order": int(jobs[0][1].shape[0]) if jobs else 0}
+    for name, mats in groups.items():
+        ap, feats, pred = _estimates(pk, mats, params)
+        times, pers = [], []
+        for k, a in enumerate(mats):
+            t, v = _whole_path(pk, torch, a, 14)
+            times.append(t)
+            pers.append(v)
+        row_cv = _cross_validated(feats, times)
+        row = kendall.table(times, per=pers, ap=ap, mlp=pred, mlp_cv=row_cv)
+        row["seconds"] = sum(times)
+        if name != "T2":
+            # Tables T5-T7 (and T8-T10) analog: list scheduling of the jobs on m
+            # workers with their measured times, in natural order, exact-time
+            # LPT, KKLLL-LPT and learned order; efficiency T1 / (m Tm)
+            row["per_total"] = str(sum(kendall.signed_mod(c, 256) * v for c, v in zip(coefs_of[name], pers)))
+            row["schedules"] = _schedules(times, ap, pred, row_cv)
+        out[name] = row
+        log("kendall:", name, row)
+    # per(I + A) of C60 again from the paper's own adjacency list (another
+    # vertex order, so another job tree): the totals must agree
+    _, v = _whole_path(pk, torch, W.paper_adjacency("c60") + np.eye(60, dtype=np.int64), 14)
+    out["T4"]["per_total_paper_c60"] = str(v)
+    out["T4"]["per_totals_agree"] = str(v) == out["T4"]["per_total"]
+    return out
+
+
+def _schedules(times, ap, pred, pred_cv, workers=(1, 2, 4, 8, 16, 32)):
+    from paper_1112_6072_gb300 import learned
+
+    n = len(times)
+    orders = {"natural": np.arange(n), "exact_lpt": learned.order_by(times), "kklll_lpt": learned.order_by(ap),
+              "learned": learned.order_by(pred), "learned_cv": learned.order_by(pred_cv)}
+    t1 = float(sum(times))
+    out = {}
+    for name, q in orders.items():
+        rows = []
+        for m in workers:
+            tm = learned.list_makespan(times, q, m)
+            rows.append({"m": m, "makespan_s": tm, "efficiency": t1 / (m * tm)})
+        out[name] = rows
+    return out
+
+
 def run_reference(args):
     """The oracle (plain CPU) on a bounded sample of the same workload."""
     import oracle
@@ -439,6 +571,8 @@ def main():
                     help="run only the C60 whole-path leg and print its timings")
     ap.add_argument("--c100", action="store_true",
                     help="per(A) of the paper's C100 adjacency (Appendix) against its printed total")
+    ap.add_argument("--kendall", action="store_true",
+                    help="Kendall tau-b of times against per, KKLLL and the cost model (Tables T2-T4 analog)")
     ap.add_argument("--mixed", action="store_true",
                     help="the mixed batch of 256 matrices (3-regular and sparse rows), three orders")
     ap.add_argument("--leaf-size", type=int, default=12)
@@ -451,6 +585,12 @@ def main():
         import paper_1112_6072_gb300 as pk
         torch.cuda.set_device(0)
         print(json.dumps({"c60": run_c60(pk, torch, args)}))
+        return
+    if args.kendall:
+        import torch
+        import paper_1112_6072_gb300 as pk
+        torch.cuda.set_device(0)
+        print(json.dumps({"kendall": run_kendall(pk, torch, args)}))
         return
     if args.mixed:
         import torch

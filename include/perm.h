@@ -143,7 +143,8 @@ void perm_plan_destroy(perm_plan_t* plan);
  * replaces it).  *njobs receives the job count. */
 perm_status perm_expand(perm_plan_t* plan, perm_jobs_t** jobs, int64_t* njobs);
 
-/* a4 -- Algorithm KKLLL (Section 2.3) on each job's 0/1 pattern (Section 3):
+/* a4 -- Algorithm KKLLL (Section 2.3) on each job's 0/1 pattern (Section 3),
+ * jobs of any order up to PERM_MAX_N:
  * log of the mean over trials of |det W|^2, W_ij a cube root of unity drawn
  * from SplitMix64(seed ^ job*0xD1B54A32D192ED03 ^ trial*0xABC98388FB8FAC03 ^
  * (i*m+j)*0x8CB92BA72F3D8DD7).  FP32 on the device; -inf when every trial is

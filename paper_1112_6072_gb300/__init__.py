@@ -349,6 +349,22 @@ class Plan:
             out.append(v - (1 << 256) if v >> 255 else v)
         return out
 
+    def job_coefs(self):
+        """Orders, coefficients (Python ints, mod 2^256) and source matrices
+        of the jobs, without the dense job matrices."""
+        self._need_jobs()
+        lib = _lib()
+        tot = ctypes.c_int64()
+        n = self.njobs
+        sizes = np.zeros(max(n, 1), dtype=np.int32)
+        coef = np.zeros(4 * max(n, 1), dtype=np.uint64)
+        mid = np.zeros(max(n, 1), dtype=np.int32)
+        _ck(lib.perm_jobs_export(self._jobs, ctypes.byref(tot),
+                                 sizes.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), None,
+                                 coef.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                 mid.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "perm_jobs_export")
+        return sizes[:n].copy(), [_words_to_int(coef[4 * j:4 * j + 4]) for j in range(n)], mid[:n].copy()
+
     def jobs_export(self):
         """The job list as (matrix index, dense job, coefficient mod 2^256)."""
         self._need_jobs()

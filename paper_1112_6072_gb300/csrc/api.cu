@@ -786,7 +786,7 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
 extern "C" perm_status perm_estimate(perm_jobs_t* J, float* log_ap) {
   if (!J) return PERM_EINVAL;
   perm_plan* P = J->plan;
-  if (J->max_order > PERM_MAX_JOB_N) return PERM_EINVAL;
+  if (J->max_order > PERM_MAX_N) return PERM_EINVAL;
   void* scratch = P->M.get(kklll_scratch_bytes(J->n, J->max_order, P->opts.kklll_trials));
   if (!scratch) return PERM_ENOMEM;
   CK(launch_kklll(J->a, J->n, J->arena, P->opts.kklll_trials, P->opts.seed, J->d_logap, J->max_order, scratch,
@@ -1269,12 +1269,12 @@ extern "C" perm_status perm_jobs_export(perm_jobs_t* J, int64_t* total_entries, 
   for (int64_t j = 0; j < n; ++j) tot += (int64_t)J->h_m[j] * J->h_m[j];
   *total_entries = tot;
   if (!sizes) return PERM_OK;
-  std::vector<uint64_t> arena((size_t)std::max<int64_t>(J->arena_words, 1));
+  std::vector<uint64_t> arena(mats ? (size_t)std::max<int64_t>(J->arena_words, 1) : 1);
   std::vector<int64_t> off(n);
   std::vector<int32_t> nnz(n), mat(n);
   std::vector<uint64_t> cf(4 * n);
   if (n) {
-    CK(cudaMemcpyAsync(arena.data(), J->arena, 8 * J->arena_words, cudaMemcpyDeviceToHost, P->s));
+    if (mats) CK(cudaMemcpyAsync(arena.data(), J->arena, 8 * J->arena_words, cudaMemcpyDeviceToHost, P->s));
     CK(cudaMemcpyAsync(off.data(), J->a.off, 8 * n, cudaMemcpyDeviceToHost, P->s));
     CK(cudaMemcpyAsync(nnz.data(), J->a.nnz, 4 * n, cudaMemcpyDeviceToHost, P->s));
     CK(cudaMemcpyAsync(mat.data(), J->a.mat, 4 * n, cudaMemcpyDeviceToHost, P->s));

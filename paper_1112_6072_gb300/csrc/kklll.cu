@@ -31,8 +31,9 @@ __device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
 template <int TILE>
 struct KCfg {
   static constexpr int STRIDE = TILE + 1;
-  static constexpr int WARPS = TILE <= 32 ? 8 : 4;
-  static constexpr size_t WARP_BYTES = sizeof(float2) * TILE * STRIDE + sizeof(uint64_t) * TILE;
+  static constexpr int MW = (TILE + 63) / 64;  // pattern words per row
+  static constexpr int WARPS = TILE <= 32 ? 8 : (TILE <= 64 ? 4 : 1);
+  static constexpr size_t WARP_BYTES = sizeof(float2) * TILE * STRIDE + sizeof(uint64_t) * TILE * MW;
   static constexpr size_t SMEM = WARPS * WARP_BYTES;
 };
 
@@ -42,6 +43,7 @@ __global__ void __launch_bounds__(KCfg<TILE>::WARPS * 32)
             float* __restrict__ log_ap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int S = KCfg<TILE>::STRIDE;
+  constexpr int MW = KCfg<TILE>::MW;
   constexpr int RPL = TILE / 32;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -60,9 +62,17 @@ __global__ void __launch_bounds__(KCfg<TILE>::WARPS * 32)
     }
     CsrView v = csr_view(arena, jobs.off[job], m, jobs.nnz[job]);
     for (int r = lane; r < m; r += 32) {
-      uint64_t b = 0;
-      for (int q = v.rowptr[r]; q < v.rowptr[r + 1]; ++q) b |= 1ull << v.col[q];
-      pat[r] = b;
+      uint64_t b[MW];
+#pragma unroll
+      for (int w = 0; w < MW; ++w) b[w] = 0;
+      for (int q = v.rowptr[r]; q < v.rowptr[r + 1]; ++q) {
+        const int c = v.col[q];
+#pragma unroll
+        for (int w = 0; w < MW; ++w)
+          if ((c >> 6) == w) b[w] |= 1ull << (c & 63);
+      }
+#pragma unroll
+      for (int w = 0; w < MW; ++w) pat[r * MW + w] = b[w];
     }
     __syncwarp();
     const int T = trials > 0 ? trials : m * m;
@@ -72,12 +82,12 @@ __global__ void __launch_bounds__(KCfg<TILE>::WARPS * 32)
       const uint64_t tkey = jkey ^ ((uint64_t)t * K_TRIAL);
       // trial matrix
       for (int r = 0; r < m; ++r) {
-        const uint64_t b = pat[r];
 #pragma unroll
         for (int u = 0; u < RPL; ++u) {
           const int c = lane + 32 * u;
+          const uint64_t b = pat[r * MW + (u >> 1)];  // column c lies in word c / 64 = u / 2
           float2 z = make_float2(0.f, 0.f);
-          if (c < m && ((b >> c) & 1)) {
+          if (c < m && ((b >> (c & 63)) & 1)) {
             const uint64_t h = splitmix64_mix(tkey ^ ((uint64_t)(r * m + c) * K_ENTRY));
             const int w = (int)(((h >> 32) * 3ull) >> 32);
             z = make_float2(RE[w], IM[w]);
@@ -520,5 +530,6 @@ cudaError_t launch_kklll(const JobArrays& jobs, int64_t njobs, const uint64_t* a
   if (max_order <= 12) return launch_thread<12>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
   if (max_order <= 16) return launch_thread<16>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
   if (max_order <= 32) return launch_rows<32>(jobs, njobs, arena, trials, seed, log_ap, s);
-  return launch_k<64>(jobs, njobs, arena, trials, seed, log_ap, s);
+  if (max_order <= 64) return launch_k<64>(jobs, njobs, arena, trials, seed, log_ap, s);
+  return launch_k<128>(jobs, njobs, arena, trials, seed, log_ap, s);
 }

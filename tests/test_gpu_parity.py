@@ -281,10 +281,12 @@ def test_batch_of_matrices_one_launch():
 
 
 # ---------------------------------------------------------------- estimator (K4) and order
-@pytest.mark.parametrize("n,d,trials", [(30, 14, 0), (20, 12, 0), (40, 16, 0), (50, 8, 300)])
+@pytest.mark.parametrize("n,d,trials", [(30, 14, 0), (20, 12, 0), (40, 16, 0), (50, 8, 300), (80, 0, 12),
+                                         (96, 10, 6)])
 def test_kklll_matches_oracle(n, d, trials):
     """Register kernels for job orders <= 8, 16, 32 and the shared-memory
-    kernel above 32; relative 1e-5 on the mean (FP32 against fp64)."""
+    kernels above 32 (two pattern words per row above 64); relative 1e-5 on
+    the mean (FP32 against fp64)."""
     a = W.regular3(n, 4)
     with pk.Plan([a], split_depth=d, leaf_size=4, kklll_trials=trials, seed=1234) as plan:
         plan.expand()

@@ -183,3 +183,17 @@ def random_small(n: int, seed: int, lo: int = -3, hi: int = 3,
     v = rng.integers(lo, hi + 1, size=(n, n))
     keep = rng.random((n, n)) < density
     return np.where(keep, v, 0).astype(np.int64)
+
+
+def random01(n: int, nonzeros: int, seed: int) -> np.ndarray:
+    """n x n 0/1 matrix with ``nonzeros`` ones at uniformly random distinct
+    positions, redrawn until every row and every column holds a one (the
+    random (n, S) groups of the paper's Section 3.1 with S = nonzeros)."""
+    rng = np.random.default_rng(seed)
+    while True:
+        flat = rng.choice(n * n, size=nonzeros, replace=False)
+        a = np.zeros(n * n, dtype=np.int64)
+        a[flat] = 1
+        a = a.reshape(n, n)
+        if (a.sum(axis=0) > 0).all() and (a.sum(axis=1) > 0).all():
+            return a
