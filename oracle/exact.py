@@ -29,11 +29,11 @@ def _lib():
         i32p = ctypes.POINTER(ctypes.c_int32)
         ip = ctypes.POINTER(ctypes.c_int)
         lib.oracle_ryser.argtypes = [ctypes.c_int, i64p, u32p, ctypes.c_int, ip, ip]
-        lib.oracle_permanent.argtypes = [ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int,
+        lib.oracle_permanent.argtypes = [ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, u32p, ctypes.c_int, ip, ip]
-        lib.oracle_jobs.argtypes = [ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int,
+        lib.oracle_jobs.argtypes = [ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     i64p, i64p, i32p, i64p, u32p, ctypes.c_int, i32p]
-        lib.oracle_job_permanents.argtypes = [ctypes.c_int64, i32p, i64p, ctypes.c_int,
+        lib.oracle_job_permanents.argtypes = [ctypes.c_int64, i32p, i64p, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, u32p, ctypes.c_int, i32p, i32p]
         for f in (lib.oracle_ryser, lib.oracle_permanent, lib.oracle_jobs,
                   lib.oracle_job_permanents):
@@ -121,22 +121,24 @@ def ryser(a) -> int:
     return _limbs_to_int(limbs, nl.value, sg.value)
 
 
-def permanent(a, d: int = 0, L: int = 0, threads: int | None = None) -> int:
+def permanent(a, d: int = 0, L: int = 0, threads: int | None = None, three: bool = False) -> int:
     """per(A) by Algorithm PH: d levels of Eq. 2, then H_per on every job
-    (leaf cut-off L; L <= 2 is the paper's own rule), then the sum."""
+    (leaf cut-off L; L <= 2 is the paper's own rule), then the sum.  three:
+    split nodes with s >= 5 by Eq. 2's three children instead of sending
+    them to Ryser."""
     a = _as_matrix(a)
     if threads is None:
         threads = os.cpu_count() or 1
     cap = 96
     limbs = np.zeros(cap, dtype=np.uint32)
     nl, sg = ctypes.c_int(0), ctypes.c_int(0)
-    _check(_lib().oracle_permanent(a.shape[0], _ptr(a, ctypes.c_int64), int(d), int(L), int(threads),
+    _check(_lib().oracle_permanent(a.shape[0], _ptr(a, ctypes.c_int64), int(d), int(L), int(three), int(threads),
                                    _ptr(limbs, ctypes.c_uint32), cap, ctypes.byref(nl),
                                    ctypes.byref(sg)))
     return _limbs_to_int(limbs, nl.value, sg.value)
 
 
-def jobs(a, d: int, L: int = 0):
+def jobs(a, d: int, L: int = 0, three: bool = False):
     """Job list after d levels of Algorithm PH, Step 2, in natural order.
 
     Returns a list of (matrix, coefficient) pairs; the permanent of the input
@@ -148,7 +150,7 @@ def jobs(a, d: int, L: int = 0):
     null32 = ctypes.POINTER(ctypes.c_int32)()
     null64 = ctypes.POINTER(ctypes.c_int64)()
     nullu = ctypes.POINTER(ctypes.c_uint32)()
-    _check(lib.oracle_jobs(a.shape[0], _ptr(a, ctypes.c_int64), int(d), int(L), ctypes.byref(nj),
+    _check(lib.oracle_jobs(a.shape[0], _ptr(a, ctypes.c_int64), int(d), int(L), int(three), ctypes.byref(nj),
                            ctypes.byref(ne), null32, null64, nullu, 0, null32))
     nj, ne = nj.value, ne.value
     cap = 96
@@ -156,7 +158,8 @@ def jobs(a, d: int, L: int = 0):
     mats = np.zeros(max(ne, 1), dtype=np.int64)
     climbs = np.zeros(max(nj, 1) * cap, dtype=np.uint32)
     csign = np.zeros(max(nj, 1), dtype=np.int32)
-    _check(lib.oracle_jobs(a.shape[0], _ptr(a, ctypes.c_int64), int(d), int(L), ctypes.byref(ctypes.c_int64()),
+    _check(lib.oracle_jobs(a.shape[0], _ptr(a, ctypes.c_int64), int(d), int(L), int(three),
+                           ctypes.byref(ctypes.c_int64()),
                            ctypes.byref(ctypes.c_int64()), _ptr(sizes, ctypes.c_int32),
                            _ptr(mats, ctypes.c_int64), _ptr(climbs, ctypes.c_uint32), cap,
                            _ptr(csign, ctypes.c_int32)))
@@ -174,7 +177,7 @@ def jobs(a, d: int, L: int = 0):
     return out
 
 
-def job_permanents(mats, L: int = 0, threads: int | None = None):
+def job_permanents(mats, L: int = 0, threads: int | None = None, three: bool = False):
     """per(M) for each dense matrix in ``mats`` by H_per (leaf cut-off L)."""
     if threads is None:
         threads = os.cpu_count() or 1
@@ -187,7 +190,7 @@ def job_permanents(mats, L: int = 0, threads: int | None = None):
     nl = np.zeros(max(count, 1), dtype=np.int32)
     sg = np.zeros(max(count, 1), dtype=np.int32)
     _check(_lib().oracle_job_permanents(count, _ptr(sizes, ctypes.c_int32), _ptr(flat, ctypes.c_int64),
-                                        int(L), int(threads), _ptr(limbs, ctypes.c_uint32), cap,
+                                        int(L), int(three), int(threads), _ptr(limbs, ctypes.c_uint32), cap,
                                         _ptr(nl, ctypes.c_int32), _ptr(sg, ctypes.c_int32)))
     return [_limbs_to_int(limbs[w * cap:(w + 1) * cap], nl[w], sg[w]) for w in range(count)]
 

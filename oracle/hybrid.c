@@ -26,7 +26,12 @@
  *   - a child holding a zero row or zero column is not emitted (its permanent
  *     is 0);
  *   - in the level-by-level expansion a node that is a leaf (n <= max(L, 2),
- *     or s >= 5) is carried unchanged to the next level, in place.
+ *     or s >= 5) is carried unchanged to the next level, in place;
+ *   - option "three" (s >= 5 split, not in Algorithm H_per, which sends such
+ *     a node to R-NW): Eq. 2 with all three children -- A1 = merge(j1, j2),
+ *     A2 = merge(j3, j4) (c*y4 + d*y3 in column j3, column j4 deleted), A3 =
+ *     the node with the pivot line's entries at j1..j4 set to 0 (same order);
+ *     then only n <= max(L, 2) makes a leaf.
  *
  * Exactness: matrix entries are int64 and every multiply/add on them is
  * overflow-checked (an overflow makes the call fail with ORACLE_EOVERFLOW);
@@ -312,8 +317,9 @@ static void make_minor(const mat* src, int i, int p, mat* child) {
   child->n = n - 1;
 }
 
-/* One step of Eq. 2 on a node that is not a leaf.  Fills up to 2 children
- * (already transposed back for a column pivot) and their scalar factors.
+/* One step of Eq. 2 on a node that is not a leaf.  Fills up to 3 children
+ * (already transposed back for a column pivot) and their scalar factors:
+ * two for k < 5 (the readings above), three for k >= 5 (option "three").
  * Children with a zero line are dropped.  Returns the number kept, or a
  * negative error code. */
 static int e2_children(const mat* node, const pivot_t* pv, mat* ch, int64_t* fac) {
@@ -332,30 +338,43 @@ static int e2_children(const mat* node, const pivot_t* pv, mat* ch, int64_t* fac
     if (AT(src, i, j) != 0) js[k++] = j;
   /* k == pv->s here */
   int nout = 0;
-  if ((e = mat_alloc(&work, n - 1))) { if (pv->is_col) mat_free(&t); return -e; }
-  for (int c = 0; c < 2; c++) {
-    int kind = 0; /* 1 merge, 2 minor */
+  if ((e = mat_alloc(&work, n))) { if (pv->is_col) mat_free(&t); return -e; }
+  for (int c = 0; c < 3; c++) {
+    int kind = 0; /* 1 merge, 2 minor, 3 pivot row's first four entries cleared */
     int p = 0, q = 0;
     int64_t f = 1;
     if (c == 0) {
       if (k == 1) { kind = 2; p = js[0]; f = AT(src, i, p); }
       else { kind = 1; p = js[0]; q = js[1]; }
-    } else {
+    } else if (c == 1) {
       if (k == 3) { kind = 2; p = js[2]; f = AT(src, i, p); }
-      else if (k == 4) { kind = 1; p = js[2]; q = js[3]; }
+      else if (k >= 4) { kind = 1; p = js[2]; q = js[3]; }
+      else break;
+    } else {
+      if (k >= 5) kind = 3;
       else break;
     }
+    int cn = n - 1;
     work.n = n;
     if (kind == 1) {
       if ((e = make_merge(src, i, p, q, &work))) { nout = -e; break; }
-    } else {
+    } else if (kind == 2) {
       make_minor(src, i, p, &work);
+    } else {
+      cn = n;
+      memcpy(work.a, src->a, sizeof(int64_t) * (size_t)n * n);
+      for (int u = 0; u < 4; u++) work.a[(size_t)i * n + js[u]] = 0;
     }
     mat* out = &ch[nout];
-    if ((e = mat_alloc(out, n - 1))) { nout = -e; break; }
-    if (pv->is_col) transpose_into(&work, out); else memcpy(out->a, work.a, sizeof(int64_t) * (size_t)(n - 1) * (n - 1));
+    if ((e = mat_alloc(out, cn))) { nout = -e; break; }
+    if (pv->is_col) {
+      work.n = cn;
+      transpose_into(&work, out);
+    } else {
+      memcpy(out->a, work.a, sizeof(int64_t) * (size_t)cn * cn);
+    }
     int rc[MAXN], cc[MAXN];
-    if (n - 1 > 0 && line_counts(out, rc, cc)) { mat_free(out); continue; }
+    if (cn > 0 && line_counts(out, rc, cc)) { mat_free(out); continue; }
     fac[nout] = f;
     nout++;
   }
@@ -364,28 +383,28 @@ static int e2_children(const mat* node, const pivot_t* pv, mat* ch, int64_t* fac
   return nout;
 }
 
-static int is_leaf(const mat* m, int L, const pivot_t* pv) {
+static int is_leaf(const mat* m, int L, int three, const pivot_t* pv) {
   int cut = L > 2 ? L : 2;
-  return m->n <= cut || pv->s >= 5;
+  return m->n <= cut || (pv->s >= 5 && !three);
 }
 
 /* Algorithm H_per (Section 2.1), recursive, with coefficient. */
-static int hper_rec(const mat* m, int L, bigint* out) {
+static int hper_rec(const mat* m, int L, int three, bigint* out) {
   int n = m->n;
   bi_zero(out);
   if (n == 0) { bi_from_i64(out, 1); return 0; }
   int rc[MAXN], cc[MAXN];
   if (line_counts(m, rc, cc)) return 0;
   pivot_t pv = choose_pivot(rc, cc, n);
-  if (is_leaf(m, L, &pv)) return ryser_textbook(m, out);
-  mat ch[2];
-  int64_t fac[2];
+  if (is_leaf(m, L, three, &pv)) return ryser_textbook(m, out);
+  mat ch[3];
+  int64_t fac[3];
   int k = e2_children(m, &pv, ch, fac);
   if (k < 0) return -k;
   int err = 0;
   for (int c = 0; c < k; c++) {
     bigint sub;
-    if (!err) err = hper_rec(&ch[c], L, &sub);
+    if (!err) err = hper_rec(&ch[c], L, three, &sub);
     if (!err && fac[c] != 1) err = bi_mul_i64(&sub, &sub, fac[c]);
     if (!err) err = bi_add(out, out, &sub);
     mat_free(&ch[c]);
@@ -424,7 +443,7 @@ static void jl_free(joblist* l) {
 }
 
 /* Expand d levels.  The root is dropped if it has a zero line. */
-static int expand_levels(const int64_t* a, int n, int d, int L, joblist* out) {
+static int expand_levels(const int64_t* a, int n, int d, int L, int three, joblist* out) {
   joblist cur = {0}, nxt = {0};
   job_t root;
   int e;
@@ -443,14 +462,14 @@ static int expand_levels(const int64_t* a, int n, int d, int L, joblist* out) {
         line_counts(&jb->m, rc, cc);
         pv = choose_pivot(rc, cc, m);
       }
-      if (m == 0 || is_leaf(&jb->m, L, &pv)) {
+      if (m == 0 || is_leaf(&jb->m, L, three, &pv)) {
         job_t keep = *jb;
         jb->m.a = NULL;
         if ((e = jl_push(&nxt, &keep))) goto fail;
         continue;
       }
-      mat ch[2];
-      int64_t fac[2];
+      mat ch[3];
+      int64_t fac[3];
       int k = e2_children(&jb->m, &pv, ch, fac);
       if (k < 0) { e = -k; goto fail; }
       for (int c = 0; c < k; c++) {
@@ -478,6 +497,7 @@ fail:
 typedef struct {
   joblist* jobs;
   int L;
+  int three;
   int64_t next;
   pthread_mutex_t mu;
   bigint* per_job;   /* per(job) without coefficient */
@@ -492,7 +512,7 @@ static void* worker(void* arg) {
     int stop = P->err;
     pthread_mutex_unlock(&P->mu);
     if (stop || w >= P->jobs->n) break;
-    int e = hper_rec(&P->jobs->v[w].m, P->L, &P->per_job[w]);
+    int e = hper_rec(&P->jobs->v[w].m, P->L, P->three, &P->per_job[w]);
     if (e) {
       pthread_mutex_lock(&P->mu);
       if (!P->err) P->err = e;
@@ -502,10 +522,11 @@ static void* worker(void* arg) {
   return NULL;
 }
 
-static int eval_jobs(joblist* jobs, int L, int nthreads, bigint* per_job) {
+static int eval_jobs(joblist* jobs, int L, int three, int nthreads, bigint* per_job) {
   pool_t P;
   P.jobs = jobs;
   P.L = L;
+  P.three = three;
   P.next = 0;
   P.per_job = per_job;
   P.err = 0;
@@ -545,8 +566,9 @@ int oracle_ryser(int n, const int64_t* a, uint32_t* limbs, int cap, int* nlimbs,
 }
 
 /* per(A) by Algorithm PH: expand d levels (Step 2), evaluate every job by
- * H_per with leaf cut-off L (Step 3, nthreads workers), sum (Step 4). */
-int oracle_permanent(int n, const int64_t* a, int d, int L, int nthreads,
+ * H_per with leaf cut-off L (Step 3, nthreads workers), sum (Step 4).
+ * three: split s >= 5 nodes by Eq. 2's three children. */
+int oracle_permanent(int n, const int64_t* a, int d, int L, int three, int nthreads,
                      uint32_t* limbs, int cap, int* nlimbs, int* sign) {
   int e = check_input(n, a);
   if (e) return e;
@@ -556,10 +578,10 @@ int oracle_permanent(int n, const int64_t* a, int d, int L, int nthreads,
     return bi_export(&one, limbs, cap, nlimbs, sign);
   }
   joblist jobs = {0};
-  if ((e = expand_levels(a, n, d < 0 ? 0 : d, L, &jobs))) return e;
+  if ((e = expand_levels(a, n, d < 0 ? 0 : d, L, three, &jobs))) return e;
   bigint* pj = (bigint*)calloc((size_t)(jobs.n > 0 ? jobs.n : 1), sizeof(bigint));
   if (!pj) { jl_free(&jobs); return ORACLE_ENOMEM; }
-  e = eval_jobs(&jobs, L, nthreads, pj);
+  e = eval_jobs(&jobs, L, three, nthreads, pj);
   bigint tot;
   bi_zero(&tot);
   for (int64_t w = 0; !e && w < jobs.n; w++) {
@@ -577,13 +599,13 @@ int oracle_permanent(int n, const int64_t* a, int d, int L, int nthreads,
  * with sizes == NULL only *njobs and *total_entries are set.  Otherwise
  * sizes[w] = job order, mats gets the row-major dense jobs back to back,
  * coef_limbs[w*coef_cap ...] the |coef| limbs, coef_sign[w] its sign. */
-int oracle_jobs(int n, const int64_t* a, int d, int L, int64_t* njobs, int64_t* total_entries,
+int oracle_jobs(int n, const int64_t* a, int d, int L, int three, int64_t* njobs, int64_t* total_entries,
                 int32_t* sizes, int64_t* mats, uint32_t* coef_limbs, int coef_cap,
                 int32_t* coef_sign) {
   int e = check_input(n, a);
   if (e) return e;
   joblist jobs = {0};
-  if ((e = expand_levels(a, n, d < 0 ? 0 : d, L, &jobs))) return e;
+  if ((e = expand_levels(a, n, d < 0 ? 0 : d, L, three, &jobs))) return e;
   int64_t tot = 0;
   for (int64_t w = 0; w < jobs.n; w++) tot += (int64_t)jobs.v[w].m.n * jobs.v[w].m.n;
   *njobs = jobs.n;
@@ -607,7 +629,7 @@ int oracle_jobs(int n, const int64_t* a, int d, int L, int64_t* njobs, int64_t* 
 /* per(job) for each of count dense jobs (row-major, back to back), by H_per
  * with leaf cut-off L, nthreads workers.  Results as limbs per job
  * (cap limbs each), with nlimbs[w] and sign[w]. */
-int oracle_job_permanents(int64_t count, const int32_t* sizes, const int64_t* mats, int L,
+int oracle_job_permanents(int64_t count, const int32_t* sizes, const int64_t* mats, int L, int three,
                           int nthreads, uint32_t* limbs, int cap, int32_t* nlimbs,
                           int32_t* sign) {
   joblist jobs = {0};
@@ -625,7 +647,7 @@ int oracle_job_permanents(int64_t count, const int32_t* sizes, const int64_t* ma
   }
   bigint* pj = (bigint*)calloc((size_t)(count > 0 ? count : 1), sizeof(bigint));
   if (!pj) { jl_free(&jobs); return ORACLE_ENOMEM; }
-  e = eval_jobs(&jobs, L, nthreads, pj);
+  e = eval_jobs(&jobs, L, three, nthreads, pj);
   for (int64_t w = 0; !e && w < count; w++) {
     int nl, sg;
     e = bi_export(&pj[w], limbs + w * cap, cap, &nl, &sg);

@@ -108,6 +108,49 @@ def test_e2_three_regular_children_shape():
     assert [c for _, c in js] == [1, 1]
 
 
+# ---------------------------------------------------------------- Eq. 2 with three children (s >= 5)
+@pytest.mark.parametrize("seed", range(12))
+def test_three_child_split_matches_bruteforce(seed):
+    """Dense nodes (s >= 5) split by Eq. 2's three children down to order
+    2 give Eq. 1's value."""
+    n = 5 + seed % 4
+    a = W.random_small(n, 3000 + seed, lo=-2, hi=3, density=0.9)
+    want = oracle.per_bruteforce(a)
+    assert oracle.permanent(a, d=0, L=0, threads=2, three=True) == want
+    assert oracle.permanent(a, d=3, L=2, threads=2, three=True) == want
+
+
+@pytest.mark.parametrize("n", [5, 6, 7, 8])
+def test_three_child_split_closed_form(n):
+    assert oracle.permanent(np.ones((n, n), np.int64), three=True) == math.factorial(n)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_three_child_node_identity(seed):
+    """per(parent) = sum of coef * per(child) over the three-child job lists,
+    children by brute force; a level never leaves s >= 5 nodes unsplit."""
+    n = 6 + seed % 3
+    a = W.random_small(n, 4000 + seed, lo=0, hi=2, density=0.85)
+    want = oracle.per_bruteforce(a)
+    for d in (1, 2, 3):
+        js = oracle.jobs(a, d, three=True)
+        assert sum(c * oracle.per_bruteforce(m) for m, c in js) == want, d
+
+
+def test_three_child_first_level_shapes():
+    """A 7x7 matrix whose sparsest line is row 0 with six nonzeros: A1 and A2
+    lose a row and a column; A3 keeps the order with row 0's first four
+    nonzeros cleared and everything else unchanged."""
+    a = np.ones((7, 7), np.int64)
+    a[0, 6] = 0
+    a[1:, 0] = 2
+    js = oracle.jobs(a, 1, three=True)
+    assert [m.shape[0] for m, _ in js] == [6, 6, 7]
+    a3 = js[2][0]
+    assert (a3[0, :4] == 0).all() and (a3[0, 4:] == a[0, 4:]).all() and (a3[1:] == a[1:]).all()
+    assert len(oracle.jobs(a, 1)) == 1  # without the option the node is a leaf, carried
+
+
 def test_zero_line_and_empty():
     a = W.random_small(6, 3)
     a[2] = 0
