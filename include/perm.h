@@ -100,6 +100,10 @@ typedef struct {
                               while the frontier fits its buffers (grown to at most 2^20 jobs and
                               2^26 arena words), then one launch per level; 0 = one launch per
                               level throughout.  The job list is the same either way */
+  int32_t dense_split;     /* 0 = Algorithm H_per: a node whose sparsest line has s >= 5 nonzeros
+                              is a leaf (Ryser).  1 = such a node is split by Eq. 2 with all three
+                              children: merge(j1, j2), merge(j3, j4), and the node with the pivot
+                              line's entries at j1..j4 cleared (same order) */
 } perm_opts;
 
 /* Fill opts with the defaults above. */

@@ -66,7 +66,8 @@ class perm_opts(ctypes.Structure):
                 ("workers_per_sm", ctypes.c_int32), ("chunk_log2", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("alloc", alloc_fn_t), ("free", free_fn_t),
                 ("alloc_ctx", ctypes.c_void_p), ("timeout_ns", ctypes.c_int64),
-                ("model_uses_estimate", ctypes.c_int32), ("fused_levels", ctypes.c_int32)]
+                ("model_uses_estimate", ctypes.c_int32), ("fused_levels", ctypes.c_int32),
+                ("dense_split", ctypes.c_int32)]
 
 
 class perm_job_result(ctypes.Structure):
@@ -206,7 +207,7 @@ class Plan:
 
     def __init__(self, mats, split_depth=-1, leaf_size=0, order="lpt", kklll_trials=0, seed=0x5EED,
                  workers_per_sm=0, chunk_log2=0, stream=None, torch_allocator=False, timeout_ns=0,
-                 model_uses_estimate=True, fused_levels=True):
+                 model_uses_estimate=True, fused_levels=True, dense_split=False):
         lib = _lib()
         self._mats = [np.ascontiguousarray(np.asarray(m, dtype=np.int64)) for m in mats]
         for m in self._mats:
@@ -230,6 +231,7 @@ class Plan:
         o.timeout_ns = int(timeout_ns)
         o.model_uses_estimate = 1 if model_uses_estimate else 0
         o.fused_levels = 1 if fused_levels else 0
+        o.dense_split = 1 if dense_split else 0
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator()

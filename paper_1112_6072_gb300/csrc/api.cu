@@ -18,7 +18,6 @@
 #include "wide.cuh"
 
 size_t mlp_scratch_floats(int32_t count);
-int64_t dfs_undo_words(int tile);
 
 // ---------------------------------------------------------------- errors
 static thread_local std::string g_last_error;
@@ -66,6 +65,7 @@ extern "C" void perm_opts_default(perm_opts* o) {
   o->timeout_ns = 0;
   o->model_uses_estimate = 1;
   o->fused_levels = 1;
+  o->dense_split = 0;
 }
 
 // ---------------------------------------------------------------- memory
@@ -240,6 +240,7 @@ struct EvalState {
   unsigned long long* sum = nullptr;  // SUM_WORDS entries
   int64_t* undo = nullptr;
   int64_t undo_w = 0;
+  int frames = 64;
   int chunk = 10;
   bool wide_first = false;
   cudaGraph_t graph = nullptr;
@@ -590,13 +591,15 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
     return mopen > PERM_MAX_JOB_N || (mopen > kSoftOrder && n < kSoftCapJobs) || (n < target && mopen > 0);
   };
   auto split_floor = [&](int mopen) { return adaptive ? mopen - kSplitBand : 0; };
+  // child slots per parent: Eq. 2's third child needs a third slot
+  const int K = P->opts.dense_split ? 3 : 2;
   int level0 = 0;
   if (P->opts.fused_levels && levels_left(0, ncur, max_open)) {
     // consecutive levels in one cooperative launch; buffers start small and
     // grow by 4x (the current level copied over) when the frontier outgrows
     // them, up to kFusedMaxJobs / kFusedMaxWords
-    int64_t cap_jobs = std::max<int64_t>(kFusedJobs0, 2 * ncur);
-    int64_t cap_words = std::max<int64_t>(kFusedWords0, 2 * used_words);
+    int64_t cap_jobs = std::max<int64_t>(kFusedJobs0, K * ncur);
+    int64_t cap_words = std::max<int64_t>(kFusedWords0, K * used_words);
     ExpandFrontState* d_state = dget<ExpandFrontState>(M, 1);
     long long* d_partial = dget<long long>(M, PERM_FRONT_MAX_BLOCKS);
     unsigned long long* d_bar = dget<unsigned long long>(M, 1);
@@ -616,8 +619,8 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
     S.cb = 0;
     for (;;) {
       const int ob = S.cb ^ 1;
-      if (!jb[ob].ensure(M, cap_jobs) || !grow(M, ar[ob], 8 * (size_t)cap_words) || !slots.ensure(M, 2 * cap_jobs) ||
-          !grow(M, g_valid, 4 * (size_t)(2 * cap_jobs)))
+      if (!jb[ob].ensure(M, cap_jobs) || !grow(M, ar[ob], 8 * (size_t)cap_words) || !slots.ensure(M, cap_jobs) ||
+          !grow(M, g_valid, 4 * (size_t)cap_jobs))
         return PERM_ENOMEM;
       if (jb[S.cb].m.cap < 4 * (size_t)cap_jobs || ar[S.cb].cap < 8 * (size_t)cap_words) {
         // move the current level into the other (large) buffers
@@ -642,6 +645,7 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
       F.cap_words = cap_words;
       F.slots = slots.view();
       F.valid = reinterpret_cast<int32_t*>(g_valid.p);
+      F.kslots = K;
       F.leaf_size = P->L;
       F.max_levels = maxd;
       F.adaptive = adaptive ? 1 : 0;
@@ -671,9 +675,9 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
       if (!levels_left(S.level, S.ncur, S.max_open)) break;
       // stopped for room: grow, or hand over to the per-level loop
       if (cap_jobs >= kFusedMaxJobs || cap_words >= kFusedMaxWords) break;
-      if (2 * S.ncur > cap_jobs) cap_jobs = std::min<int64_t>(kFusedMaxJobs, 4 * cap_jobs);
-      if (2 * S.used_words > cap_words) cap_words = std::min<int64_t>(kFusedMaxWords, 4 * cap_words);
-      if (2 * S.ncur > cap_jobs || 2 * S.used_words > cap_words) break;
+      if (K * S.ncur > cap_jobs) cap_jobs = std::min<int64_t>(kFusedMaxJobs, 4 * cap_jobs);
+      if (K * S.used_words > cap_words) cap_words = std::min<int64_t>(kFusedMaxWords, 4 * cap_words);
+      if (K * S.ncur > cap_jobs || K * S.used_words > cap_words) break;
     }
     M.put(d_state);
     M.put(d_partial);
@@ -692,20 +696,20 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
     level0 = S.level;
   }
   for (int level = level0; levels_left(level, ncur, max_open); ++level) {
-    // every parent reserves two child slots of its own block size
-    const int64_t out_words = 2 * used_words;
+    // every parent reserves K child slots of its own block size
+    const int64_t out_words = K * used_words;
     const int nb = cb ^ 1;
-    const size_t tb = std::max(scan_tmp_bytes_i64(ncur), scan_tmp_bytes_i32(2 * ncur));
+    const size_t tb = std::max(scan_tmp_bytes_i64(ncur), scan_tmp_bytes_i32(K * ncur));
     if (!grow(M, g_words, 8 * (size_t)ncur) || !grow(M, g_base, 8 * (size_t)ncur) ||
-        !grow(M, g_valid, 8 * (size_t)ncur) || !grow(M, g_pos, 8 * (size_t)ncur) || !grow(M, g_tmp, tb) ||
-        !grow(M, ar[nb], 8 * (size_t)std::max<int64_t>(out_words, 2)) || !slots.ensure(M, 2 * ncur))
+        !grow(M, g_valid, 4 * (size_t)(K * ncur)) || !grow(M, g_pos, 4 * (size_t)(K * ncur)) || !grow(M, g_tmp, tb) ||
+        !grow(M, ar[nb], 8 * (size_t)std::max<int64_t>(out_words, 2)) || !slots.ensure(M, K * ncur))
       return PERM_ENOMEM;
     int64_t* words = reinterpret_cast<int64_t*>(g_words.p);
     int64_t* base = reinterpret_cast<int64_t*>(g_base.p);
     int32_t* valid = reinterpret_cast<int32_t*>(g_valid.p);
     int32_t* pos = reinterpret_cast<int32_t*>(g_pos.p);
     uint64_t* next_arena = reinterpret_cast<uint64_t*>(ar[nb].p);
-    CK(launch_child_capacity(cur, ncur, words, s));
+    CK(launch_child_capacity(cur, ncur, K, words, s));
     CK(scan_exclusive_i64(words, base, ncur, g_tmp.p, g_tmp.cap, s));
     ExpandLevelArgs A;
     A.parent = cur;
@@ -715,15 +719,16 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
     A.arena_out = next_arena;
     A.child_off_base = base;
     A.valid = valid;
+    A.kslots = K;
     A.leaf_size = P->L;
     A.split_floor = split_floor(max_open);
     A.err = reinterpret_cast<int32_t*>(d_stat);
     CK(launch_expand_level(A, max_order, s));
-    CK(scan_exclusive_i32(valid, pos, 2 * ncur, g_tmp.p, g_tmp.cap, s));
-    // the kept children: at most 2 * ncur; size the next arrays for that bound
-    if (!jb[nb].ensure(M, 2 * ncur)) return PERM_ENOMEM;
+    CK(scan_exclusive_i32(valid, pos, K * ncur, g_tmp.p, g_tmp.cap, s));
+    // the kept children: at most K * ncur; size the next arrays for that bound
+    if (!jb[nb].ensure(M, K * ncur)) return PERM_ENOMEM;
     CK(cudaMemsetAsync(d_stat + 1, 0, 32, s));
-    CK(launch_compact_jobs(slots.view(), valid, pos, 2 * ncur, jb[nb].view(), std::max(P->L, 2), d_stat + 1, s));
+    CK(launch_compact_jobs(slots.view(), valid, pos, K * ncur, jb[nb].view(), std::max(P->L, 2), d_stat + 1, s));
     long long st[5] = {0, 0, 0, 0, 0};
     CK(cudaMemcpyAsync(st, d_stat, 40, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -976,7 +981,9 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order) {
       dfs_warps = std::max(dfs_warps, P->sms * ((dfs_wps(P, tile) + wpb - 1) / wpb) * wpb);
     }
   }
-  E.undo_w = dfs_undo_words(max_tile);
+  // Eq. 2's third child keeps the order, so a path can hold more levels than rows
+  E.frames = P->opts.dense_split ? 4 * max_tile : max_tile;
+  E.undo_w = dfs_undo_words(max_tile, E.frames);
   E.undo = nd > 0 ? dget<int64_t>(M, E.undo_w * dfs_warps) : nullptr;
   if (!E.counts || !E.prefix || !E.stmp || !E.d_rq || !E.rflags || !E.rpos || (nd > 0 && !E.undo))
     return PERM_ENOMEM;
@@ -1000,6 +1007,8 @@ static DfsArgs dfs_args(perm_jobs* J, int g, const uint32_t* queue, int64_t nq) 
   D.undo = E.undo;
   D.undo_words_per_warp = E.undo_w;
   D.timeout_ns = P->opts.timeout_ns > 0 ? P->opts.timeout_ns : 10000000000ll;
+  D.three = P->opts.dense_split ? 1 : 0;
+  D.max_depth = E.frames;
   return D;
 }
 

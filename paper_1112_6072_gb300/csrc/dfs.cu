@@ -12,6 +12,11 @@
 // patterns are kept as bit masks per row (rowbits) and per column
 // (colbits), so a line count is one popcount against the active masks.
 //
+// With the three-child option a node whose sparsest line has s >= 5
+// nonzeros is not a leaf: Eq. 2's third child clears the pivot line's first
+// four entries in place (the frame holds their values for the undo), so a
+// path can hold more levels than the job has rows (max_depth frames).
+//
 // Variants: tile entries int32 (more warps per SM) or int64, and leaves of
 // up to 16 or up to 32 rows.  A job that the narrow variant cannot hold (an
 // entry leaving int32, a leaf above 16 rows) reports DFS_RETRY and the host
@@ -41,7 +46,6 @@ struct DfsCfg {
   static constexpr size_t SMEM = WARPS * WARP_BYTES;
   // undo stack words per level: meta (8 x int32 = 4 words), pv[4], coef[4], saved mask, line[TILE]
   static constexpr int FRAME_WORDS = 4 + 4 + 4 + 1 + TILE;
-  static constexpr int64_t UNDO_WORDS = (int64_t)FRAME_WORDS * TILE;
 };
 
 struct Frame {
@@ -167,22 +171,51 @@ struct Dfs {
     if (lane == 0) reinterpret_cast<int32_t*>(frame_words(lv))[3] = child;
   }
 
-  // child c of a frame: kind 1 = merge(pos[x], pos[x+1]), 2 = minor(pos[x])
+  // child c of a frame: kind 1 = merge(pos[x], pos[x+1]), 2 = minor(pos[x]),
+  // 3 = the pivot line's entries at pos[0..3] cleared (k >= 5)
   __device__ static void child_kind(int k, int c, int& kind, int& x) {
     if (c == 0) {
       kind = k == 1 ? 2 : 1;
       x = 0;
-    } else {
+    } else if (c == 1) {
       kind = k == 3 ? 2 : 1;
       x = 2;
+    } else {
+      kind = 3;
+      x = 0;
     }
   }
-  __device__ static int nchildren(int k) { return (k == 3 || k == 4) ? 2 : 1; }
+  __device__ static int nchildren(int k) { return k >= 5 ? 3 : ((k == 3 || k == 4) ? 2 : 1); }
+
+  // the pivot line's entries at pos[0..3] set to 0 (clear) or back to pv
+  __device__ void clear_four(const Frame& f, const int64_t* pv, bool restore) {
+    if (lane < 4) {
+      const int t = lane;
+      const int at = f.pos[t];
+      if (!f.is_col) {
+        T[f.idx * S + at] = restore ? (E)pv[t] : (E)0;
+        if (restore) colbits[at] |= bit64(f.idx); else colbits[at] &= ~bit64(f.idx);
+      } else {
+        T[at * S + f.idx] = restore ? (E)pv[t] : (E)0;
+        if (restore) rowbits[at] |= bit64(f.idx); else rowbits[at] &= ~bit64(f.idx);
+      }
+    }
+    if (lane == 0) {
+      const uint64_t m4 = bit64(f.pos[0]) | bit64(f.pos[1]) | bit64(f.pos[2]) | bit64(f.pos[3]);
+      uint64_t* line = f.is_col ? &colbits[f.idx] : &rowbits[f.idx];
+      *line = restore ? (*line | m4) : (*line & ~m4);
+    }
+    __syncwarp();
+  }
 
   // Apply child c; returns false when a merged entry leaves E.
   __device__ bool apply(int lv, const Frame& f, const int64_t* pv, int c) {
     int kind, x;
     child_kind(f.k, c, kind, x);
+    if (kind == 3) {
+      clear_four(f, pv, false);
+      return true;
+    }
     int64_t* saved = frame_words(lv) + 13;
     bool ok = true;
     if (!f.is_col) {
@@ -256,11 +289,15 @@ struct Dfs {
     return __all_sync(0xffffffffu, ok);
   }
 
-  __device__ void undo_child(int lv, const Frame& f, const u256& pcoef, int c) {
+  __device__ void undo_child(int lv, const Frame& f, const int64_t* pv, const u256& pcoef, int c) {
     int kind, x;
     child_kind(f.k, c, kind, x);
-    const int64_t* saved = frame_words(lv) + 13;
     coef = pcoef;
+    if (kind == 3) {
+      clear_four(f, pv, true);
+      return;
+    }
+    const int64_t* saved = frame_words(lv) + 13;
     if (!f.is_col) {
       const int i = f.idx;
       R |= bit64(i);
@@ -526,11 +563,11 @@ __global__ void __launch_bounds__(DfsCfg<TILE, E>::WARPS * 32, DfsCfg<TILE, E>::
         const int mact = __popcll(D.R);
         bool descend = false;
         if (s > 0) {
-          if (mact <= cut || s >= 5) {
+          if (mact <= cut || (s >= 5 && !A.three)) {
             ++leaves;
             status = D.leaf(acc);
             if (status != 0) break;
-          } else if (depth >= TILE - 1) {
+          } else if (depth >= A.max_depth - 1) {
             status = PERM_EINVAL;
             break;
           } else {
@@ -572,7 +609,7 @@ __global__ void __launch_bounds__(DfsCfg<TILE, E>::WARPS * 32, DfsCfg<TILE, E>::
           int64_t pv[4];
           u256 pc;
           D.load_frame(depth - 1, f, pv, pc);
-          D.undo_child(depth - 1, f, pc, f.child);
+          D.undo_child(depth - 1, f, pv, pc, f.child);
           if (f.child + 1 < Dfs<TILE, E, LN, W>::nchildren(f.k)) {
             f.child += 1;
             D.set_child(depth - 1, f.child);
@@ -628,7 +665,9 @@ int dfs_warps_per_block(int tile, bool wide) {
   if (wide) return tile <= 32 ? DfsCfg<32, int64_t>::WARPS : DfsCfg<64, int64_t>::WARPS;
   return tile <= 32 ? DfsCfg<32, int32_t>::WARPS : DfsCfg<64, int32_t>::WARPS;
 }
-int64_t dfs_undo_words(int tile) { return tile <= 32 ? DfsCfg<32, int32_t>::UNDO_WORDS : DfsCfg<64, int32_t>::UNDO_WORDS; }
+int64_t dfs_undo_words(int tile, int frames) {
+  return (int64_t)frames * (tile <= 32 ? DfsCfg<32, int32_t>::FRAME_WORDS : DfsCfg<64, int32_t>::FRAME_WORDS);
+}
 
 template <int W>
 cudaError_t launch_dfs_w(const DfsArgs& a, int tile, bool wide, int num_sms, int warps_per_sm, cudaStream_t s) {

@@ -16,7 +16,10 @@
 // q; a column pivot does the same with rows.  A scalar factor multiplies the
 // child's coefficient.  Children holding a zero line are not emitted.  A
 // parent of order <= max(L, 2), with s >= 5, or with no levels left is
-// carried unchanged to slot 2p.  With a split floor (automatic depth), a
+// carried unchanged to slot Kp (K = 2 child slots per parent).  With the
+// three-child option (K = 3), a parent with s >= 5 is split by Eq. 2 in
+// full: merge(j1, j2), merge(j3, j4), and the parent with the pivot line's
+// entries at j1..j4 cleared (same order).  With a split floor (automatic depth), a
 // parent still to split whose order is below the floor waits: it is carried
 // with its levels left, so the largest jobs of a batch are split first.
 //
@@ -75,12 +78,17 @@ __device__ __forceinline__ bool mad2_checked(int64_t a, int64_t x, int64_t b, in
 }
 
 struct ChildSpec {
-  int del_row, del_col;
-  int merge;      // 0 none, 1 column p merged (row pivot), 2 row p merged (column pivot)
+  int del_row, del_col;  // kNone for the cleared child
+  int merge;      // 0 none, 1 column p merged (row pivot), 2 row p merged (column pivot),
+                  // 3 the pivot line's entries at zp[0..3] cleared (nothing deleted)
   int p, q;       // merged line and its partner (deleted), p < q
   int64_t a, b;   // merged line = a * line_q + b * line_p
   int64_t fac;    // scalar factor (minor)
+  int zcol, zidx; // merge 3: pivot is a column (1) or a row (0), and its index
+  int zp[4];      // merge 3: the cleared positions along the pivot line
 };
+
+constexpr int kNone = 1 << 30;
 
 // The nonzeros of one child row (parent row r), in ascending child column
 // order, passed to emit(col, value).  False on int64 overflow.
@@ -109,6 +117,17 @@ __device__ __forceinline__ bool child_row(const CsrView& v, const ChildSpec& cs,
       emit(c - (c > cs.q), v.val[t]);
     }
     if (!done && mv != 0) emit(cs.p, mv);
+  } else if (cs.merge == 3) {
+    // the cleared child: row zidx loses columns zp (row pivot), or rows zp
+    // lose column zidx (column pivot)
+    const bool rowhit = !cs.zcol && r == cs.zidx;
+    const bool colhit = cs.zcol && (r == cs.zp[0] || r == cs.zp[1] || r == cs.zp[2] || r == cs.zp[3]);
+    for (int t = b; t < e; ++t) {
+      const int c = v.col[t];
+      if (rowhit && (c == cs.zp[0] || c == cs.zp[1] || c == cs.zp[2] || c == cs.zp[3])) continue;
+      if (colhit && c == cs.zidx) continue;
+      emit(c, v.val[t]);
+    }
   } else if (cs.merge == 2 && r == cs.p) {
     const int bq = v.rowptr[cs.q], eq = v.rowptr[cs.q + 1];
     int i = b, j = bq;
@@ -148,6 +167,7 @@ struct ExpandCtx {
   int32_t* valid;
   int32_t leaf_size;
   int32_t split_floor;            // parents of a lower order wait for a later level
+  int32_t kslots;                 // child slots per parent: 2, or 3 with the three-child option
   int32_t* err;
 };
 
@@ -173,15 +193,15 @@ __device__ __forceinline__ int64_t child_block(const ExpandCtx& X, int64_t p, in
   return (int64_t)o;
 }
 
-// Parent p unchanged into slot 2p with depth_left dl_out.
+// Parent p unchanged into slot Kp with depth_left dl_out.
 __device__ void carry_parent(const ExpandCtx& X, int64_t p, const uint64_t* src, int64_t pw, int m, int nnz,
                              int dl_out, int lane) {
   const int64_t o = child_block(X, p, 0, pw, pw, lane);
   if (o >= 0) copy_words(X.arena_out + o, src, pw, lane);
   if (lane == 0) {
-    const int64_t c0 = 2 * p;
+    const int64_t c0 = (int64_t)X.kslots * p;
     X.valid[c0] = o >= 0 ? 1 : 0;
-    X.valid[c0 + 1] = 0;
+    for (int c = 1; c < X.kslots; ++c) X.valid[c0 + c] = 0;
     if (o >= 0) {
       X.child.m[c0] = m;
       X.child.nnz[c0] = nnz;
@@ -197,9 +217,9 @@ __device__ void carry_parent(const ExpandCtx& X, int64_t p, const uint64_t* src,
 
 // Divide parent p (one warp).  ccnt: the warp's shared-memory column counts
 // (RPL * 32 entries); stage: its kStageWords-word copy of the parent block.
-// only_child 0 or 1: build that child alone (two warps share a parent when
-// the frontier is small; the child-0 warp also writes the carried and
-// dropped cases); -1: both.
+// only_child >= 0: build that child alone (one warp per child when the
+// frontier is small; the child-0 warp also writes the carried and dropped
+// cases); -1: all.
 template <int RPL>
 __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* ccnt, uint64_t* stage,
                               int only_child = -1) {
@@ -211,7 +231,7 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
   const int cut = X.leaf_size > 2 ? X.leaf_size : 2;
   __syncwarp();  // the previous parent's reads of stage and ccnt are done
   if (dl > 0 && m > cut && m < X.split_floor) {
-    if (only_child != 1) carry_parent(X, p, X.arena_in + off, pw, m, nnz, dl, lane);
+    if (only_child <= 0) carry_parent(X, p, X.arena_in + off, pw, m, nnz, dl, lane);
     return;
   }
   const uint64_t* src = X.arena_in + off;
@@ -244,12 +264,14 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
   const int s = (int)(key >> 17);
   const bool is_col = (key >> 16) & 1;
   const int idx = (int)(key & 0xffff);
+  const bool three = X.kslots == 3;
   if (s == 0) {  // zero line: nothing to emit
-    if (lane == 0 && only_child != 1) X.valid[2 * p] = X.valid[2 * p + 1] = 0;
+    if (lane == 0 && only_child <= 0)
+      for (int c = 0; c < X.kslots; ++c) X.valid[(int64_t)X.kslots * p + c] = 0;
     return;
   }
-  if (dl <= 0 || m <= cut || s >= 5) {
-    if (only_child != 1) carry_parent(X, p, src, pw, m, nnz, 0, lane);
+  if (dl <= 0 || m <= cut || (s >= 5 && !three)) {
+    if (only_child <= 0) carry_parent(X, p, src, pw, m, nnz, 0, lane);
     return;
   }
   // pivot line's nonzero positions (ascending) and values
@@ -295,30 +317,35 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
   }
   u256 pcoef;
   for (int w = 0; w < 4; ++w) pcoef.w[w] = X.parent.coef[4 * p + w];
-  const int mc = m - 1;
-  for (int c = 0; c < 2; ++c) {
+  for (int c = 0; c < X.kslots; ++c) {
     if (only_child >= 0 && c != only_child) continue;
-    const int64_t slot = 2 * p + c;
-    int kind;  // 1 merge(pos[x], pos[x+1]), 2 minor(pos[x])
-    int x;
+    const int64_t slot = (int64_t)X.kslots * p + c;
+    int kind;  // 1 merge(pos[x], pos[x+1]), 2 minor(pos[x]), 3 pivot line's first four entries cleared
+    int x = 0;
     if (c == 0) {
       kind = s == 1 ? 2 : 1;
-      x = 0;
-    } else if (s == 3) {
+    } else if (c == 1 && s == 3) {
       kind = 2;
       x = 2;
-    } else if (s == 4) {
+    } else if (c == 1 && s >= 4) {
       kind = 1;
       x = 2;
+    } else if (c == 2 && s >= 5) {
+      kind = 3;
     } else {
       if (lane == 0) X.valid[slot] = 0;
       continue;
     }
+    const int mc = kind == 3 ? m : m - 1;
     ChildSpec cs;
     cs.fac = 1;
     cs.merge = 0;
     cs.p = cs.q = 0;
     cs.a = cs.b = 0;
+    cs.zcol = is_col ? 1 : 0;
+    cs.zidx = idx;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cs.zp[u] = pos[u];
     const int xp = x == 0 ? pos[0] : pos[2], xq = x == 0 ? pos[1] : pos[3];
     const int64_t va = x == 0 ? pv[0] : pv[2], vb = x == 0 ? pv[1] : pv[3];
     if (kind == 1) {
@@ -327,10 +354,14 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
       cs.q = xq;
       cs.a = va;
       cs.b = vb;
-    } else {
+    } else if (kind == 2) {
       cs.fac = va;
+    } else {
+      cs.merge = 3;
     }
-    if (!is_col) {
+    if (kind == 3) {
+      cs.del_row = cs.del_col = kNone;
+    } else if (!is_col) {
       cs.del_row = idx;
       cs.del_col = kind == 1 ? xq : xp;
     } else {
@@ -443,6 +474,7 @@ __global__ void __launch_bounds__(kLevelWarps * 32) k_expand_level(ExpandLevelAr
   X.valid = A.valid;
   X.leaf_size = A.leaf_size;
   X.split_floor = A.split_floor;
+  X.kslots = A.kslots;
   X.err = A.err;
   const int64_t nwarps = (int64_t)gridDim.x * kLevelWarps;
   for (int64_t p = (int64_t)blockIdx.x * kLevelWarps + wib; p < A.np; p += nwarps)
@@ -527,8 +559,9 @@ __global__ void __launch_bounds__(kFrontThreads) k_expand_front(ExpandFrontArgs 
     // the same decision in every block: S and the error flag were read
     // between the same two barriers (the flag is only raised while
     // children are built, before the first barrier of a level)
+    const int K = F.kslots;
     bool stop = failed || S.level >= F.max_levels || S.ncur <= 0 || S.max_order > RPL * 32 ||
-                2 * S.ncur > F.cap_jobs || 2 * S.used_words > F.cap_words;
+                K * S.ncur > F.cap_jobs || K * S.used_words > F.cap_words;
     if (!stop && F.adaptive) {
       const bool big = S.max_open > F.big_order;
       const bool soft = S.max_open > F.soft_order && S.ncur < F.soft_cap_jobs;
@@ -550,19 +583,20 @@ __global__ void __launch_bounds__(kFrontThreads) k_expand_front(ExpandFrontArgs 
     X.valid = F.valid;
     X.leaf_size = F.leaf_size;
     X.split_floor = F.adaptive ? S.max_open - F.band : 0;
+    X.kslots = F.kslots;
     X.err = F.err;
     const int64_t p0 = S.ncur * b / G, p1 = S.ncur * (b + 1) / G;
-    if (2 * S.ncur <= G * kFrontWarps) {
-      // small frontier: a warp per child, halving the level's latency
-      for (int64_t t = 2 * p0 + wib; t < 2 * p1; t += kFrontWarps)
-        expand_parent<RPL>(X, t >> 1, lane, ccnt[wib], stage + wib * kStageWords, (int)(t & 1));
+    if (K * S.ncur <= G * kFrontWarps) {
+      // small frontier: a warp per child, cutting the level's latency
+      for (int64_t t = K * p0 + wib; t < K * p1; t += kFrontWarps)
+        expand_parent<RPL>(X, t / K, lane, ccnt[wib], stage + wib * kStageWords, (int)(t % K));
     } else {
       for (int64_t p = p0 + wib; p < p1; p += kFrontWarps)
         expand_parent<RPL>(X, p, lane, ccnt[wib], stage + wib * kStageWords);
     }
     __syncthreads();
     long long kept = 0;
-    for (int64_t t = 2 * p0 + threadIdx.x; t < 2 * p1; t += kFrontThreads) kept += F.valid[t];
+    for (int64_t t = K * p0 + threadIdx.x; t < K * p1; t += kFrontThreads) kept += F.valid[t];
     kept = block_sum(kept, red64);
     if (threadIdx.x == 0) __stcg(F.partial + b, kept);
     if (!grid_barrier(F.bar, target, F.err)) return;
@@ -578,9 +612,9 @@ __global__ void __launch_bounds__(kFrontThreads) k_expand_front(ExpandFrontArgs 
     // compaction of this block's slots, natural order kept
     const JobArrays src = F.slots, dst = F.buf[cb ^ 1];
     int64_t base = before;
-    for (int64_t t0 = 2 * p0; t0 < 2 * p1; t0 += kFrontThreads) {
+    for (int64_t t0 = K * p0; t0 < K * p1; t0 += kFrontThreads) {
       const int64_t t = t0 + threadIdx.x;
-      const int keep = t < 2 * p1 ? F.valid[t] : 0;
+      const int keep = t < K * p1 ? F.valid[t] : 0;
       int tot;
       const int64_t d = base + block_excl_scan(keep, red32, tot);
       if (keep) {
@@ -656,9 +690,9 @@ cudaError_t launch_expand_front(const ExpandFrontArgs& a, int max_order, int* gr
   return launch_front_rpl<4>(a, grid, s);
 }
 
-__global__ void k_child_capacity(JobArrays parent, int64_t np, int64_t* words) {
+__global__ void k_child_capacity(JobArrays parent, int64_t np, int kslots, int64_t* words) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p < np) words[p] = 2 * blk_words(parent.m[p], parent.nnz[p]);
+  if (p < np) words[p] = kslots * blk_words(parent.m[p], parent.nnz[p]);
 }
 
 // stat[0]: largest kept order, stat[1]: words of the kept blocks, stat[2]:
@@ -693,9 +727,9 @@ __global__ void k_compact(JobArrays src, const int32_t* valid, const int32_t* po
   }
 }
 
-cudaError_t launch_child_capacity(const JobArrays& parent, int64_t np, int64_t* words, cudaStream_t s) {
+cudaError_t launch_child_capacity(const JobArrays& parent, int64_t np, int kslots, int64_t* words, cudaStream_t s) {
   if (np <= 0) return cudaSuccess;
-  k_child_capacity<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(parent, np, words);
+  k_child_capacity<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(parent, np, kslots, words);
   return cudaGetLastError();
 }
 

@@ -69,17 +69,19 @@ cudaError_t launch_leaf_finalize(const uint32_t* queue, int64_t nq, const JobArr
                                  unsigned long long* mat_acc, cudaStream_t stream);
 
 // ---- K1 expansion (one level) ---------------------------------------------------
-// Parents [0, np) in arena_in.  Children go to slots 2p, 2p+1 of the child
-// arrays; child_off_base[p] is the first word of parent p's two child blocks
-// in arena_out.  valid[2p + c] is 1 for an emitted child.
+// Parents [0, np) in arena_in.  Children go to slots Kp .. Kp + K - 1 of the
+// child arrays (K = kslots: 2, or 3 with Eq. 2's third child for s >= 5);
+// child_off_base[p] is the first word of parent p's K child blocks (each of
+// the parent's size) in arena_out.  valid[Kp + c] is 1 for an emitted child.
 struct ExpandLevelArgs {
   JobArrays parent;
   const uint64_t* arena_in;
   int64_t np;
-  JobArrays child;  // 2*np slots
+  JobArrays child;  // K*np slots
   uint64_t* arena_out;
   const int64_t* child_off_base;
-  int32_t* valid;   // 2*np
+  int32_t* valid;   // K*np
+  int32_t kslots;
   int32_t leaf_size;
   int32_t split_floor;  // parents of a lower order (with depth left, above the leaf order) wait
   int32_t* err;     // device flag: first error status
@@ -89,7 +91,8 @@ cudaError_t launch_expand_level(const ExpandLevelArgs& a, int max_order, cudaStr
 // Consecutive levels in one cooperative launch.  The current jobs are
 // buf[state.cb] with their blocks in arena[state.cb] (state.used_words
 // words).  Runs a level while: level < max_levels, 0 < ncur, 2 * ncur <=
-// cap_jobs, 2 * used_words <= cap_words, and (when adaptive) max_open >
+// cap_jobs, K * used_words <= cap_words (K child slots per parent; the
+// condition on ncur is K * ncur <= cap_jobs), and (when adaptive) max_open >
 // big_order, or max_open > soft_order and ncur < soft_cap_jobs, or (ncur <
 // target_jobs and max_open > 0), where max_open is the
 // largest order of a job still to split; adaptive levels split only parents
@@ -111,8 +114,9 @@ struct ExpandFrontArgs {
   uint64_t* arena[2];
   int64_t cap_jobs;
   int64_t cap_words;
-  JobArrays slots;  // 2 * cap_jobs
-  int32_t* valid;   // 2 * cap_jobs
+  JobArrays slots;  // cap_jobs (children of at most cap_jobs / K parents)
+  int32_t* valid;   // cap_jobs
+  int32_t kslots;
   int32_t leaf_size;
   int32_t max_levels;
   int32_t adaptive;
@@ -132,8 +136,8 @@ struct ExpandFrontArgs {
 // *grid = blocks launched, 0 when the device has no cooperative launch (the
 // caller then runs every level with launch_expand_level).
 cudaError_t launch_expand_front(const ExpandFrontArgs& a, int max_order, int* grid, cudaStream_t s);
-// words[p] = 2 * blk_words(parent p) (capacity for its two children)
-cudaError_t launch_child_capacity(const JobArrays& parent, int64_t np, int64_t* words, cudaStream_t s);
+// words[p] = kslots * blk_words(parent p) (capacity for its children)
+cudaError_t launch_child_capacity(const JobArrays& parent, int64_t np, int kslots, int64_t* words, cudaStream_t s);
 // Compact valid slots into dst (natural order kept).  Accumulates into
 // stat[0] the largest kept order, stat[1] the kept blocks' words, stat[2]
 // the kept job count and stat[3] the largest order of a kept job with depth
@@ -155,6 +159,8 @@ struct DfsArgs {
   int64_t* undo;          // per-warp undo stacks
   int64_t undo_words_per_warp;
   int64_t timeout_ns;
+  int32_t three;          // s >= 5 nodes split by Eq. 2's three children (else leaves)
+  int32_t max_depth;      // undo frames per warp
 };
 // Internal job status of the narrow depth-first variant (int32 tile, leaves
 // up to 16 rows): the job needs the wide variant (int64 tile, leaves up to 32).
@@ -162,7 +168,8 @@ struct DfsArgs {
 // All queued jobs must belong to matrices of ring width W (2 or 4 words).
 cudaError_t launch_dfs(const DfsArgs& a, int tile, bool wide, int W, int num_sms, int warps_per_sm, cudaStream_t s);
 int dfs_warps_per_block(int tile, bool wide);
-int64_t dfs_undo_words(int tile);
+// undo words per warp for a stack of `frames` levels
+int64_t dfs_undo_words(int tile, int frames);
 
 // ---- K4 KKLLL estimator -------------------------------------------------------
 // scratch: kklll_scratch_bytes(njobs, max_order, trials) bytes of device memory

@@ -153,6 +153,38 @@ def test_job_list_signed_sparse(fused):
         assert (gm == wm).all() and gc == wc % (1 << 256)
 
 
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_dense_split_job_list_matches_oracle(seed, fused):
+    """Eq. 2 with the third child (s >= 5): the expansion's job list equals
+    the oracle's, and some jobs kept their order through a level."""
+    a = W.random_small(12, 500 + seed, lo=1, hi=2, density=0.75)
+    # every line holds at least five nonzeros, so the root takes three children
+    assert min((a != 0).sum(axis=0).min(), (a != 0).sum(axis=1).min()) >= 5
+    with pk.Plan([a], split_depth=4, leaf_size=3, dense_split=True, fused_levels=fused) as plan:
+        plan.expand()
+        got = plan.jobs_export()
+    want = oracle.jobs(a, 4, 3, three=True)
+    assert len(got) == len(want) > 0
+    for (_, gm, gc), (wm, wc) in zip(got, want):
+        assert gm.shape == wm.shape and (gm == wm).all() and gc == wc % (1 << 256)
+    assert any(m.shape[0] > 12 - 4 for _, m, _ in got)
+
+
+@pytest.mark.parametrize("n,d,L", [(14, 0, 6), (16, 3, 8), (18, 6, 10), (20, 2, 12)])
+def test_dense_split_permanents(n, d, L):
+    """Dense 0/1 matrices (s >= 5 everywhere): the depth-first evaluator's
+    three-child frames and the expansion give the oracle's permanent, the
+    same as the paper's rule (Ryser at s >= 5)."""
+    a = W.random_small(n, 600 + n, lo=0, hi=1, density=0.6)
+    want = oracle.permanent(a)
+    for dense in (True, False):
+        with pk.Plan([a], split_depth=d, leaf_size=L, dense_split=dense) as plan:
+            plan.expand()
+            plan.evaluate()
+            assert plan.result(0) == want, dense
+
+
 def _export(mats, fused, **kw):
     with pk.Plan(mats, fused_levels=fused, **kw) as plan:
         plan.expand()
