@@ -234,6 +234,7 @@ struct EvalState {
   int32_t* rpos = nullptr;
   uint64_t* counts = nullptr;
   uint64_t* prefix = nullptr;
+  uint32_t* owner = nullptr;  // task -> grouped leaf queue position
   void* stmp = nullptr;
   size_t stb = 0;
   unsigned long long* ctr = nullptr;  // [0] leaf tasks, [1 + g] depth-first group g
@@ -272,7 +273,8 @@ static void free_eval(Mem& M, perm_jobs* J) {
   if (E->graph) cudaGraphDestroy(E->graph);
   if (E->cap) cudaStreamDestroy(E->cap);
   for (void* p : {(void*)E->d_q, (void*)E->d_g, (void*)E->d_rq, (void*)E->rflags, (void*)E->rpos,
-                  (void*)E->counts, (void*)E->prefix, E->stmp, (void*)E->ctr, (void*)E->sum, (void*)E->undo})
+                  (void*)E->counts, (void*)E->prefix, (void*)E->owner, E->stmp, (void*)E->ctr, (void*)E->sum,
+                  (void*)E->undo})
     M.put(p);
   delete E;
   J->ev = nullptr;
@@ -971,6 +973,10 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order) {
   // the narrow variant (int32 tile, leaves <= 16 rows) unless the leaf order needs the wide one
   E.wide_first = P->L > 16;
   E.chunk = P->opts.chunk_log2 > 0 ? P->opts.chunk_log2 : 10;
+  uint64_t leaf_tasks = 0;
+  for (int64_t j = 0; j < n; ++j)
+    if (J->h_m[j] <= leaf_max) leaf_tasks += leaf_tasks_host(J->h_m[j], E.chunk);
+  E.owner = dget<uint32_t>(M, (int64_t)std::max<uint64_t>(leaf_tasks, 1));
   int dfs_warps = 0, max_tile = 32;
   for (int g = 0; g < EVAL_DFS_GROUPS; ++g) {
     if (E.db[g + 1] == E.db[g]) continue;
@@ -985,7 +991,7 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order) {
   E.frames = P->opts.dense_split ? 4 * max_tile : max_tile;
   E.undo_w = dfs_undo_words(max_tile, E.frames);
   E.undo = nd > 0 ? dget<int64_t>(M, E.undo_w * dfs_warps) : nullptr;
-  if (!E.counts || !E.prefix || !E.stmp || !E.d_rq || !E.rflags || !E.rpos || (nd > 0 && !E.undo))
+  if (!E.counts || !E.prefix || !E.owner || !E.stmp || !E.d_rq || !E.rflags || !E.rpos || (nd > 0 && !E.undo))
     return PERM_ENOMEM;
   return PERM_OK;
 }
@@ -1045,11 +1051,12 @@ static cudaError_t eval_enqueue(perm_jobs* J, cudaStream_t s) {
   if (E.nl > 0) {
     // one task scan for the grouped leaf queue, then one persistent grid per
     // kernel variant over its slice
-    EQ(launch_leaf_tasks(E.d_lq, E.nl, J->a, E.chunk, E.counts, E.prefix, E.stmp, E.stb, s));
-    launches += 3;
+    EQ(launch_leaf_tasks(E.d_lq, E.nl, J->a, E.chunk, E.counts, E.prefix, E.owner, E.stmp, E.stb, s));
+    launches += 4;
     for (size_t g = 0; g < E.groups.size(); ++g) {
       const int64_t o = E.groups[g].first;
-      EQ(launch_leaf_batch(E.d_lq + o, E.groups[g].second, E.group_cls[g], E.prefix + o, J->a, J->arena, E.chunk,
+      EQ(launch_leaf_batch(E.d_lq + o, E.groups[g].second, E.group_cls[g], E.prefix + o, E.owner, o, J->a,
+                           J->arena, E.chunk,
                            E.ctr, J->out, P->sms, s));
       ++launches;
     }

@@ -370,9 +370,12 @@ struct Dfs {
     bool ok = true;
     int myrow = lane < m ? nth_bit(R, lane) : 0;
     int mycol = lane < m ? nth_bit(C, lane) : 0;
+    // the leaf's nonzeros are the set bits of the row and column masks
+    // (a lane walks its row's few nonzeros, not every active column)
+    const uint64_t rownz = lane < m ? (rowbits[myrow] & C) : 0;
     if (lane < m) {
       int64_t ra = 0;
-      uint64_t cm = C;
+      uint64_t cm = rownz;
       while (cm) {
         const int c = __ffsll((long long)cm) - 1;
         cm &= cm - 1;
@@ -382,14 +385,13 @@ struct Dfs {
       }
       if (ra >= (1ll << 31)) ok = false;
       rmax = ra;
+      // leaf rows (ranks among the active rows) holding a nonzero in my column
       uint32_t msk = 0;
-      uint64_t rm = R;
-      int ii = 0;
+      uint64_t rm = colbits[mycol] & R;
       while (rm) {
         const int r = __ffsll((long long)rm) - 1;
         rm &= rm - 1;
-        if (T[r * S + mycol] != 0) msk |= 1u << ii;
-        ++ii;
+        msk |= 1u << __popcll(R & (bit64(r) - 1));
       }
       cmask[lane] = msk;
     }
@@ -439,11 +441,11 @@ struct Dfs {
     }
     if (lane < m) {
       int64_t rs = 0, last = 0;
-      uint64_t cm = C;
-      int jj = 0;
+      uint64_t cm = rownz;
       while (cm) {
         const int c = __ffsll((long long)cm) - 1;
         cm &= cm - 1;
+        const int jj = __popcll(C & (bit64(c) - 1));  // leaf column of c
         const int64_t a = (int64_t)T[myrow * S + c];
         rs += a;
         int gj;
@@ -452,7 +454,6 @@ struct Dfs {
         else
           gj = jj < cols ? jj : -1;
         if (gj >= 0) delta[gj * nmax + slot] = (int32_t)(2 * a); else last = a;
-        ++jj;
       }
       rho0[slot] = (int32_t)(2 * last - rs);
     }

@@ -54,15 +54,19 @@ cudaError_t launch_retry_collect(const uint32_t* dq, int64_t n, RetryBounds boun
 cudaError_t launch_eval_keys(const uint32_t* queue, int64_t n, const JobArrays& jobs, const uint64_t* arena,
                              const int32_t* mat_w, int leaf_max, uint32_t* keys, uint32_t* vals,
                              unsigned long long* hist, cudaStream_t stream);
-// Ryser tasks of every queued leaf job and their exclusive scan (nq + 1 entries).
+// Ryser tasks of every queued leaf job, their exclusive scan (nq + 1
+// entries) and the task owner map: owner[t] = queue position of task t's job
+// (prefix[nq] entries; leaf_tasks_host(m, chunk_log2) summed over the jobs).
 cudaError_t launch_leaf_tasks(const uint32_t* queue, int64_t nq, const JobArrays& jobs, int chunk_log2,
-                              uint64_t* counts_scratch, uint64_t* prefix, void* scan_tmp, size_t scan_tmp_bytes,
-                              cudaStream_t stream);
-// One variant group of leaf jobs in queue order; prefix is the group's slice
-// of the task scan (nq + 1 entries).
+                              uint64_t* counts_scratch, uint64_t* prefix, uint32_t* owner, void* scan_tmp,
+                              size_t scan_tmp_bytes, cudaStream_t stream);
+uint64_t leaf_tasks_host(int m, int chunk_log2);
+// One variant group of leaf jobs in queue order: the group starts at queue
+// position qbase of the grouped queue; queue and prefix are its slices (nq
+// and nq + 1 entries), owner the whole map.
 cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int cls, const uint64_t* prefix,
-                              const JobArrays& jobs, const uint64_t* arena, int chunk_log2,
-                              unsigned long long* task_counter, const JobOut& out, int num_sms,
+                              const uint32_t* owner, int64_t qbase, const JobArrays& jobs, const uint64_t* arena,
+                              int chunk_log2, unsigned long long* task_counter, const JobOut& out, int num_sms,
                               cudaStream_t stream);
 // Sigma -> coef * per for every leaf job, summed into the matrix accumulators.
 cudaError_t launch_leaf_finalize(const uint32_t* queue, int64_t nq, const JobArrays& jobs, const JobOut& out,

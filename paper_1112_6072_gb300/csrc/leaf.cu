@@ -56,6 +56,13 @@ __host__ __device__ __forceinline__ void leaf_split(int m, int chunk_log2, int& 
   tasks = 1ull << (e - 5 - clog);
 }
 
+// owner[t] = the grouped leaf queue position whose job holds task t
+__global__ void k_task_owner(const uint64_t* __restrict__ prefix, int64_t nq, uint32_t* __restrict__ owner) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  for (uint64_t t = prefix[q]; t < prefix[q + 1]; ++t) owner[t] = (uint32_t)q;
+}
+
 __global__ void k_leaf_task_counts(const uint32_t* __restrict__ queue, int64_t nq,
                                    const int32_t* __restrict__ jm, int chunk_log2,
                                    uint64_t* __restrict__ counts) {
@@ -223,7 +230,7 @@ __device__ void load_blocked(const uint64_t* __restrict__ arena, int64_t off, in
 template <int NMAX, int W, int PATH>
 __global__ void __launch_bounds__(LEAF_WARPS * 32)
     k_leaf_batch(const uint32_t* __restrict__ queue, int64_t nq, const uint64_t* __restrict__ prefix,
-                 JobArrays jobs, const uint64_t* __restrict__ arena, int chunk_log2,
+                 const uint32_t* __restrict__ owner, int64_t qbase, JobArrays jobs, const uint64_t* __restrict__ arena, int chunk_log2,
                  unsigned long long* __restrict__ task_counter, JobOut out) {
   __shared__ __align__(16) LeafSmem sm;
   const int lane = threadIdx.x & 31;
@@ -241,15 +248,12 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32)
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= total) break;
     t += base;
-    // queue entry holding task t: last q with prefix[q] <= t
-    int64_t lo = 0, hi = nq - 1;
-    while (lo < hi) {
-      int64_t mid = (lo + hi + 1) >> 1;
-      if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    const int64_t q = lo;
+    // queue entry holding task t, from the task owner map
+    const int64_t q = (int64_t)owner[t] - qbase;
     const uint32_t job = queue[q];
-    const uint64_t lt = t - prefix[q];
+    const uint64_t first = prefix[q];
+    const uint64_t lt = t - first;
+    const bool single = prefix[q + 1] - first == 1;  // this warp holds the whole job
     const uint64_t t0 = globaltimer_ns();
     if (q != cur_q) {
       cur_q = q;
@@ -266,9 +270,9 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32)
       if (lane == 0) {
         CsrView v = csr_view(arena, jobs.off[job], 1, jobs.nnz[job]);
         const int64_t a = jobs.nnz[job] ? v.val[0] : 0;
-        const uint64_t s = a < 0 ? ~0ull : 0ull;
+        const uint64_t sg = a < 0 ? ~0ull : 0ull;
         words[0] = (uint64_t)a;
-        words[1] = words[2] = words[3] = s;
+        words[1] = words[2] = words[3] = sg;
       }
     } else if (m >= 2) {
       int lanes, clog;
@@ -283,17 +287,24 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32)
         if constexpr (NMAX >= 16) run_lane4<NMAX, 16, W>(delta, rho0, m, gb, mycnt, words);
       } else {
         constexpr int BC = PATH == P_G15 ? 15 : (PATH == P_G31 ? 31 : 7);
-        typename WideT<W>::type s = ryser_lane<NMAX, W, BC>(delta, rho0, m, gb, mycnt);
-        s = warp_sum(s);
-        to_words(s, words);
+        typename WideT<W>::type sw = ryser_lane<NMAX, W, BC>(delta, rho0, m, gb, mycnt);
+        sw = warp_sum(sw);
+        to_words(sw, words);
       }
     }
     if (lane == 0) {
-      atomic_add_words(out.acc + 4ll * job, words, 4);
       const uint64_t t1 = globaltimer_ns();
-      unsigned long long prev = atomicMin(out.t_start + job, (unsigned long long)t0);
-      if (prev == ~0ull) out.sm[job] = (int32_t)smid();
-      atomicMax(out.t_end + job, (unsigned long long)t1);
+      if (single) {  // no other warp writes this job: plain stores
+        for (int k = 0; k < 4; ++k) out.acc[4ll * job + k] = words[k];
+        out.t_start[job] = t0;
+        out.t_end[job] = t1;
+        out.sm[job] = (int32_t)smid();
+      } else {
+        atomic_add_words(out.acc + 4ll * job, words, 4);
+        unsigned long long prev = atomicMin(out.t_start + job, (unsigned long long)t0);
+        if (prev == ~0ull) out.sm[job] = (int32_t)smid();
+        atomicMax(out.t_end + job, (unsigned long long)t1);
+      }
       if (lt == 0) out.leaves[job] = 1;
     }
   }
@@ -343,9 +354,9 @@ __global__ void k_leaf_reject(const uint32_t* __restrict__ queue, int64_t nq, Jo
 }
 
 template <int NMAX, int W, int PATH>
-cudaError_t launch_variant(const uint32_t* queue, int64_t nq, const uint64_t* prefix, const JobArrays& jobs,
-                           const uint64_t* arena, int chunk_log2, unsigned long long* task_counter,
-                           const JobOut& out, int num_sms, cudaStream_t stream) {
+cudaError_t launch_variant(const uint32_t* queue, int64_t nq, const uint64_t* prefix, const uint32_t* owner,
+                           int64_t qbase, const JobArrays& jobs, const uint64_t* arena, int chunk_log2,
+                           unsigned long long* task_counter, const JobOut& out, int num_sms, cudaStream_t stream) {
   static int per_sm = 0;
   if (per_sm == 0) {
     cudaError_t e =
@@ -353,17 +364,17 @@ cudaError_t launch_variant(const uint32_t* queue, int64_t nq, const uint64_t* pr
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
   }
-  k_leaf_batch<NMAX, W, PATH><<<num_sms * per_sm, LEAF_WARPS * 32, 0, stream>>>(queue, nq, prefix, jobs, arena,
-                                                                                chunk_log2, task_counter, out);
+  k_leaf_batch<NMAX, W, PATH><<<num_sms * per_sm, LEAF_WARPS * 32, 0, stream>>>(
+      queue, nq, prefix, owner, qbase, jobs, arena, chunk_log2, task_counter, out);
   return cudaGetLastError();
 }
 
-#define LEAF_ARGS queue, nq, prefix, jobs, arena, chunk_log2, task_counter, out, num_sms, stream
+#define LEAF_ARGS queue, nq, prefix, owner, qbase, jobs, arena, chunk_log2, task_counter, out, num_sms, stream
 
 template <int NMAX, int W>
-cudaError_t launch_path(int path, const uint32_t* queue, int64_t nq, const uint64_t* prefix, const JobArrays& jobs,
-                        const uint64_t* arena, int chunk_log2, unsigned long long* task_counter, const JobOut& out,
-                        int num_sms, cudaStream_t stream) {
+cudaError_t launch_path(int path, const uint32_t* queue, int64_t nq, const uint64_t* prefix, const uint32_t* owner,
+                        int64_t qbase, const JobArrays& jobs, const uint64_t* arena, int chunk_log2,
+                        unsigned long long* task_counter, const JobOut& out, int num_sms, cudaStream_t stream) {
   switch (path) {
     case P_G7: return launch_variant<NMAX, W, P_G7>(LEAF_ARGS);
     case P_G15: return launch_variant<NMAX, W, P_G15>(LEAF_ARGS);
@@ -388,19 +399,31 @@ cudaError_t launch_eval_keys(const uint32_t* queue, int64_t n, const JobArrays& 
 }
 
 cudaError_t launch_leaf_tasks(const uint32_t* queue, int64_t nq, const JobArrays& jobs, int chunk_log2,
-                              uint64_t* counts_scratch, uint64_t* prefix, void* scan_tmp, size_t scan_tmp_bytes,
-                              cudaStream_t stream) {
+                              uint64_t* counts_scratch, uint64_t* prefix, uint32_t* owner, void* scan_tmp,
+                              size_t scan_tmp_bytes, cudaStream_t stream) {
   if (nq <= 0) return cudaSuccess;
   const int tb = 256;
   k_leaf_task_counts<<<(unsigned)((nq + 1 + tb - 1) / tb), tb, 0, stream>>>(queue, nq, jobs.m, chunk_log2,
                                                                               counts_scratch);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return scan_exclusive_u64(counts_scratch, prefix, nq + 1, scan_tmp, scan_tmp_bytes, stream);
+  e = scan_exclusive_u64(counts_scratch, prefix, nq + 1, scan_tmp, scan_tmp_bytes, stream);
+  if (e != cudaSuccess) return e;
+  k_task_owner<<<(unsigned)((nq + tb - 1) / tb), tb, 0, stream>>>(prefix, nq, owner);
+  return cudaGetLastError();
+}
+
+uint64_t leaf_tasks_host(int m, int chunk_log2) {
+  if (m < 2) return 1;
+  int lanes, clog;
+  uint64_t tasks;
+  leaf_split(m, chunk_log2, lanes, clog, tasks);
+  return tasks;
 }
 
 cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int cls, const uint64_t* prefix,
-                              const JobArrays& jobs, const uint64_t* arena, int chunk_log2,
+                              const uint32_t* owner, int64_t qbase, const JobArrays& jobs, const uint64_t* arena,
+                              int chunk_log2,
                               unsigned long long* task_counter, const JobOut& out, int num_sms,
                               cudaStream_t stream) {
   if (nq <= 0) return cudaSuccess;
