@@ -32,6 +32,11 @@ import workloads as W  # noqa: E402
 
 METRIC = "C60 60x60 permanent wall time; leaf permanents/sec; % of integer-ALU roofline"
 LEAF_COUNT = 100_000
+# DRAM bytes (read + write) of one evaluation per leaf matrix, from ncu on the
+# 20,000-matrix case of the same seed (32.7 MB per evaluation;
+# profiles/leaf_batch_launches.md); the traffic is per leaf, so it scales
+# with the batch
+LEAF_TRAFFIC_BYTES_PER_MATRIX = 32.7e6 / 20_000
 LEAF_SEED = 20240601
 C60_SEED = 60
 
@@ -212,7 +217,9 @@ def run_ours(args, rank, world, torch):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms": min(e2e_ms)},
         "gpu_launches": launches * args.steps if launches is not None else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": LEAF_TRAFFIC_BYTES_PER_MATRIX * LEAF_COUNT,
+                     "traffic_basis": "ncu DRAM read+write of one evaluation of the 20,000-matrix case, "
+                                      "scaled by the matrix count",
                      "peak_basis": f"{sms} SMs x {imad_per_clk_sm} IMAD/clk x {sm_mhz:.0f} MHz (median under load)",
                      "ubench_imad_Tops": ub_rate / 1e12},
         "clocks": clocks,
