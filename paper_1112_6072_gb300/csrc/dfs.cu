@@ -53,21 +53,19 @@ struct Frame {
   int32_t pos[4];
 };
 
-__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    unsigned long long o = __shfl_xor_sync(0xffffffffu, v, d);
-    v = o < v ? o : v;
-  }
-  return v;
-}
-
-// a*x + b*y, false when the result leaves E
+// a*x + b*y, false when the result leaves E.  In an int32 tile all four
+// operands are tile entries (|v| < 2^31), so int64 holds the sum exactly.
 template <typename E>
 __device__ __forceinline__ bool mad2_checked(int64_t a, int64_t x, int64_t b, int64_t y, E& out) {
-  const __int128 r = (__int128)a * x + (__int128)b * y;
-  out = (E)r;
-  return r == (__int128)out;
+  if constexpr (sizeof(E) == 4) {
+    const int64_t r = a * x + b * y;
+    out = (E)r;
+    return r == (int64_t)out;
+  } else {
+    const __int128 r = (__int128)a * x + (__int128)b * y;
+    out = (E)r;
+    return r == (__int128)out;
+  }
 }
 
 // index of the (n+1)-th set bit of a 64-bit mask
@@ -341,16 +339,16 @@ struct Dfs {
   }
 
   // smallest line count over the active lines: (s << 17) | (is_col << 16) | index
+  // (s <= 64, index < 64: 24 bits), one warp-wide min reduction
   __device__ unsigned long long pivot_key() {
-    unsigned long long key = ~0ull;
+    unsigned key = 0xffffffffu;
 #pragma unroll
     for (int t = 0; t < RPL; ++t) {
       const int r = lane + 32 * t;
-      if ((R >> r) & 1) key = min(key, ((unsigned long long)__popcll(rowbits[r] & C) << 17) | (unsigned long long)r);
-      if ((C >> r) & 1)
-        key = min(key, ((unsigned long long)__popcll(colbits[r] & R) << 17) | (1ull << 16) | (unsigned long long)r);
+      if ((R >> r) & 1) key = min(key, ((unsigned)__popcll(rowbits[r] & C) << 17) | (unsigned)r);
+      if ((C >> r) & 1) key = min(key, ((unsigned)__popcll(colbits[r] & R) << 17) | (1u << 16) | (unsigned)r);
     }
-    return warp_min_u64(key);
+    return (unsigned long long)__reduce_min_sync(0xffffffffu, key);
   }
 
   // Ryser on the active sub-matrix; adds coef * per into acc (lane 0).

@@ -50,15 +50,6 @@ constexpr int kStageWords = 1024;
 constexpr size_t kLevelSmem = sizeof(uint64_t) * kStageWords * kLevelWarps;
 constexpr size_t kFrontSmem = sizeof(uint64_t) * kStageWords * kFrontWarps;
 
-__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    unsigned long long o = __shfl_xor_sync(0xffffffffu, v, d);
-    v = o < v ? o : v;
-  }
-  return v;
-}
-
 __device__ __forceinline__ int warp_excl_scan(int v, int lane, int& total) {
   int x = v;
 #pragma unroll
@@ -243,13 +234,14 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
   for (int c = lane; c < m; c += 32) ccnt[c] = 0;
   __syncwarp();
   const CsrView v = csr_view(src, 0, m, nnz);
-  unsigned long long key = ~0ull;
+  // (count << 17) | (is_col << 16) | index: count <= 128, index < 128
+  unsigned key = 0xffffffffu;
 #pragma unroll
   for (int k = 0; k < RPL; ++k) {
     const int r = lane + 32 * k;
     if (r < m) {
       const int b = v.rowptr[r], e = v.rowptr[r + 1];
-      key = min(key, ((unsigned long long)(e - b) << 17) | (unsigned long long)r);
+      key = min(key, ((unsigned)(e - b) << 17) | (unsigned)r);
       for (int t = b; t < e; ++t) atomicAdd(&ccnt[v.col[t]], 1);
     }
   }
@@ -257,10 +249,10 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
 #pragma unroll
   for (int k = 0; k < RPL; ++k) {
     const int c = lane + 32 * k;
-    if (c < m) key = min(key, ((unsigned long long)ccnt[c] << 17) | (1ull << 16) | (unsigned long long)c);
+    if (c < m) key = min(key, ((unsigned)ccnt[c] << 17) | (1u << 16) | (unsigned)c);
   }
   __syncwarp();  // counts read before the next parent clears them
-  key = warp_min_u64(key);
+  key = __reduce_min_sync(0xffffffffu, key);
   const int s = (int)(key >> 17);
   const bool is_col = (key >> 16) & 1;
   const int idx = (int)(key & 0xffff);
