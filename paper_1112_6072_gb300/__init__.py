@@ -60,6 +60,9 @@ class perm_matrix(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("a", ctypes.POINTER(ctypes.c_int64)), ("ld", ctypes.c_int64)]
 
 
+_MATRIX_DTYPE = np.dtype([("n", np.int32), ("a", np.uintp), ("ld", np.int64)], align=True)
+
+
 class perm_opts(ctypes.Structure):
     _fields_ = [("split_depth", ctypes.c_int32), ("leaf_size", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("kklll_trials", ctypes.c_int32), ("seed", ctypes.c_uint64),
@@ -213,11 +216,14 @@ class Plan:
         for m in self._mats:
             if m.ndim != 2 or m.shape[0] != m.shape[1]:
                 raise ValueError("square matrices expected")
-        arr = (perm_matrix * len(self._mats))()
-        for k, m in enumerate(self._mats):
-            arr[k].n = m.shape[0]
-            arr[k].a = m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
-            arr[k].ld = max(m.shape[0], 1)
+        # the perm_matrix descriptors, built as one numpy record array (a
+        # ctypes loop costs about 4 us per matrix)
+        desc = np.zeros(len(self._mats), dtype=_MATRIX_DTYPE)
+        desc["n"] = [m.shape[0] for m in self._mats]
+        desc["a"] = [m.__array_interface__["data"][0] for m in self._mats]
+        desc["ld"] = np.maximum(desc["n"], 1)
+        self._desc = desc
+        arr = (perm_matrix * len(self._mats)).from_buffer(desc)
         o = perm_opts()
         lib.perm_opts_default(ctypes.byref(o))
         o.split_depth = int(split_depth)
@@ -345,10 +351,15 @@ class Plan:
         w = np.zeros(4 * c, dtype=np.uint64)
         _ck(_lib().perm_result_words(self._h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), c),
             "perm_result_words")
-        out = []
-        for i in range(c):
-            v = _words_to_int(w[4 * i:4 * i + 4])
-            out.append(v - (1 << 256) if v >> 255 else v)
+        w = w.reshape(c, 4)
+        # values that fit int64 (the upper words repeat the sign) convert in bulk
+        lo = w[:, 0].view(np.int64)
+        ext = np.where(lo < 0, np.uint64(0xFFFFFFFFFFFFFFFF), np.uint64(0))
+        small = (w[:, 1] == ext) & (w[:, 2] == ext) & (w[:, 3] == ext)
+        out = lo.tolist()
+        for i in np.flatnonzero(~small).tolist():
+            v = _words_to_int(w[i])
+            out[i] = v - (1 << 256) if v >> 255 else v
         return out
 
     def job_coefs(self):

@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <numeric>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -308,8 +309,12 @@ static double log2_bound(const perm_matrix& A, bool& binary) {
   // min(prod of row abs sums, prod of column abs sums), and Bregman's bound
   // prod (r_i!)^(1/r_i) for 0/1 matrices (valid for per of a 0/1 matrix)
   const int n = A.n;
-  std::vector<double> rs(n, 0.0), cs(n, 0.0);
-  std::vector<int> rc(n, 0);
+  double rs[PERM_MAX_N], cs[PERM_MAX_N];
+  int rc[PERM_MAX_N];
+  for (int i = 0; i < n; ++i) {
+    rs[i] = cs[i] = 0.0;
+    rc[i] = 0;
+  }
   binary = true;
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
@@ -331,15 +336,16 @@ static double log2_bound(const perm_matrix& A, bool& binary) {
   return b;
 }
 
-static void put_csr(std::vector<uint64_t>& arena, const perm_matrix& A, int64_t& off, int32_t& nnz_out) {
-  const int n = A.n;
+static int count_nnz(const perm_matrix& A) {
   int nnz = 0;
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) nnz += A.a[(size_t)i * A.ld + j] != 0;
-  off = (int64_t)arena.size();
-  const int64_t words = blk_words(n, nnz);
-  arena.resize(arena.size() + (size_t)words, 0ull);
-  uint64_t* b = arena.data() + off;
+  for (int i = 0; i < A.n; ++i)
+    for (int j = 0; j < A.n; ++j) nnz += A.a[(size_t)i * A.ld + j] != 0;
+  return nnz;
+}
+
+// CSR block of A (nnz nonzeros) into b (blk_words(n, nnz) zeroed words)
+static void put_csr(uint64_t* b, const perm_matrix& A, int nnz) {
+  const int n = A.n;
   uint16_t* rp = reinterpret_cast<uint16_t*>(b);
   uint8_t* col = reinterpret_cast<uint8_t*>(b + blk_rp_words(n));
   int64_t* val = reinterpret_cast<int64_t*>(b + blk_rp_words(n) + blk_col_words(nnz));
@@ -356,7 +362,27 @@ static void put_csr(std::vector<uint64_t>& arena, const perm_matrix& A, int64_t&
     }
   }
   rp[n] = (uint16_t)k;
-  nnz_out = nnz;
+}
+
+// fn(i) for i in [0, count): on up to 16 host threads for large batches
+template <class F>
+static void parallel_for(int32_t count, F fn) {
+  unsigned th = std::thread::hardware_concurrency();
+  th = th == 0 ? 1 : (th > 16 ? 16 : th);
+  if (count < 4096 || th == 1) {
+    for (int32_t i = 0; i < count; ++i) fn(i);
+    return;
+  }
+  std::vector<std::thread> pool;
+  const int32_t chunk = (count + (int32_t)th - 1) / (int32_t)th;
+  for (unsigned t = 0; t < th; ++t) {
+    const int32_t lo = (int32_t)t * chunk, hi = std::min(count, lo + chunk);
+    if (lo >= hi) break;
+    pool.emplace_back([lo, hi, &fn]() {
+      for (int32_t i = lo; i < hi; ++i) fn(i);
+    });
+  }
+  for (auto& t : pool) t.join();
 }
 
 extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, const perm_opts* opts,
@@ -371,13 +397,19 @@ extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, 
   for (int32_t i = 0; i < count; ++i) {
     const perm_matrix& A = mats[i];
     if (A.n < 0 || A.n > PERM_MAX_N || A.ld < A.n || (A.n > 0 && !A.a)) return PERM_EINVAL;
+    maxn = std::max(maxn, A.n);
+  }
+  std::vector<uint8_t> bad(count, 0);
+  parallel_for(count, [&](int32_t i) {
+    const perm_matrix& A = mats[i];
     for (int r = 0; r < A.n; ++r)
       for (int c = 0; c < A.n; ++c) {
         const int64_t v = A.a[(size_t)r * A.ld + c];
-        if (v >= (1ll << 31) || v <= -(1ll << 31)) return PERM_EINVAL;
+        if (v >= (1ll << 31) || v <= -(1ll << 31)) bad[i] = 1;
       }
-    maxn = std::max(maxn, A.n);
-  }
+  });
+  for (uint8_t b : bad)
+    if (b) return PERM_EINVAL;
   perm_plan* P = new perm_plan();
   P->opts = o;
   P->s = (cudaStream_t)o.stream;
@@ -403,14 +435,17 @@ extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, 
   P->trivial.assign(count, 0);
   P->h_off.assign(count, -1);
   P->h_nnz.assign(count, 0);
-  for (int32_t i = 0; i < count; ++i) {
+  // per matrix, in parallel: trivial cases, ring width from the bound, nonzeros
+  std::vector<uint8_t> over(count, 0);
+  parallel_for(count, [&](int32_t i) {
     const perm_matrix& A = mats[i];
     P->n[i] = A.n;
+    P->depth[i] = P->leaf_only ? 0 : o.split_depth;  // -1: chosen during the expansion
     if (A.n == 0) {
       P->trivial[i] = 2;
       P->w[i] = 2;
       P->kbits[i] = 64;
-      continue;
+      return;
     }
     // zero line -> per = 0
     bool zero = false;
@@ -426,7 +461,7 @@ extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, 
       P->trivial[i] = 1;
       P->w[i] = 2;
       P->kbits[i] = 64;
-      continue;
+      return;
     }
     bool binary;
     const double lb = log2_bound(A, binary);
@@ -440,14 +475,27 @@ extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, 
       P->w[i] = 4;
       P->kbits[i] = 257 - lmax;
     } else {
+      over[i] = 1;
+      return;
+    }
+    P->h_nnz[i] = count_nnz(A);
+  });
+  for (uint8_t b : over)
+    if (b) {
       delete P;
       return PERM_EOVERFLOW;
     }
-    int d = o.split_depth;
-    if (P->leaf_only) d = 0;
-    P->depth[i] = d;  // -1: chosen during the expansion
-    put_csr(P->h_arena, A, P->h_off[i], P->h_nnz[i]);
+  // blocks back to back in matrix order, filled in parallel
+  int64_t words = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    if (P->trivial[i]) continue;
+    P->h_off[i] = words;
+    words += blk_words(P->n[i], P->h_nnz[i]);
   }
+  P->h_arena.assign((size_t)words, 0ull);
+  parallel_for(count, [&](int32_t i) {
+    if (!P->trivial[i]) put_csr(P->h_arena.data() + P->h_off[i], mats[i], P->h_nnz[i]);
+  });
   P->d_mat_w = dget<int32_t>(P->M, count);
   P->d_mat_acc = dget<unsigned long long>(P->M, 4ll * count);
   if (!P->d_mat_w || !P->d_mat_acc) {
