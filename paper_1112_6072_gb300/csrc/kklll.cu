@@ -369,8 +369,13 @@ __global__ void __launch_bounds__(TCfg<MT>::WARPS * 32)
     if (m >= 1 && m <= MT && t < T) {
       CsrView v = csr_view(arena, jobs.off[job], m, jobs.nnz[job]);
       const uint64_t tkey = seed ^ ((uint64_t)job * K_JOB) ^ ((uint64_t)t * K_TRIAL);
-      for (int i = 0; i < m; ++i)
-        for (int j = 0; j < m; ++j) WT(i, j) = make_float2(0.f, 0.f);
+      // the trial matrix padded to MT x MT with the identity: |det| and every
+      // pivot of the first m steps are unchanged, the padded pivots are 1, and
+      // the loops below run to the compile-time MT (fully unrolled)
+#pragma unroll
+      for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < MT; ++j) WT(i, j) = make_float2(i == j && i >= m ? 1.0f : 0.0f, 0.0f);
       for (int i = 0; i < m; ++i)
         for (int q = v.rowptr[i]; q < v.rowptr[i + 1]; ++q) {
           const int j = v.col[q];
@@ -381,61 +386,54 @@ __global__ void __launch_bounds__(TCfg<MT>::WARPS * 32)
       float pm = 1.0f;
       int pe = 0;
       bool singular = false;
-      for (int k = 0; k < m && !singular; ++k) {
-        int p = k;
-        float best = -1.0f;
-        for (int r = k; r < m; ++r) {
-          const float2 z = WT(r, k);
-          const float mg = z.x * z.x + z.y * z.y;
-          if (mg > best) {
-            best = mg;
-            p = r;
+#pragma unroll
+      for (int k = 0; k < MT; ++k) {
+        if (!singular) {
+          int p = k;
+          float best = -1.0f;
+#pragma unroll
+          for (int r = k; r < MT; ++r) {
+            const float2 z = WT(r, k);
+            const float mg = z.x * z.x + z.y * z.y;
+            if (mg > best) {
+              best = mg;
+              p = r;
+            }
           }
-        }
-        if (!(best > 0.0f)) {
-          singular = true;
-          break;
-        }
-        if (p != k)
-          for (int c = k; c < m; ++c) {
-            const float2 a = WT(k, c);
-            WT(k, c) = WT(p, c);
-            WT(p, c) = a;
-          }
-        int ex;
-        pm = frexpf(pm * best, &ex);
-        pe += ex;
-        const float2 piv = WT(k, k);
-        const float inv = 1.0f / best;
-        const float2 ip = make_float2(piv.x * inv, -piv.y * inv);
-        // two rows per pass: independent load / update / store chains
-        int r = k + 1;
-        for (; r + 1 < m; r += 2) {
-          const float2 a0 = WT(r, k), a1 = WT(r + 1, k);
-          const float2 f0 = make_float2(a0.x * ip.x - a0.y * ip.y, a0.x * ip.y + a0.y * ip.x);
-          const float2 f1 = make_float2(a1.x * ip.x - a1.y * ip.y, a1.x * ip.y + a1.y * ip.x);
-#pragma unroll 4
-          for (int c = k + 1; c < m; ++c) {
-            const float2 pc = WT(k, c);
-            float2 z0 = WT(r, c), z1 = WT(r + 1, c);
-            z0.x -= f0.x * pc.x - f0.y * pc.y;
-            z0.y -= f0.x * pc.y + f0.y * pc.x;
-            z1.x -= f1.x * pc.x - f1.y * pc.y;
-            z1.y -= f1.x * pc.y + f1.y * pc.x;
-            WT(r, c) = z0;
-            WT(r + 1, c) = z1;
-          }
-        }
-        if (r < m) {
-          const float2 a = WT(r, k);
-          const float2 f = make_float2(a.x * ip.x - a.y * ip.y, a.x * ip.y + a.y * ip.x);
-#pragma unroll 4
-          for (int c = k + 1; c < m; ++c) {
-            const float2 pc = WT(k, c);
-            float2 z = WT(r, c);
-            z.x -= f.x * pc.x - f.y * pc.y;
-            z.y -= f.x * pc.y + f.y * pc.x;
-            WT(r, c) = z;
+          if (!(best > 0.0f)) {
+            singular = true;
+          } else {
+            if (p != k) {
+#pragma unroll
+              for (int c = k; c < MT; ++c) {
+                const float2 a = WT(k, c);
+                WT(k, c) = WT(p, c);
+                WT(p, c) = a;
+              }
+            }
+            int ex;
+            pm = frexpf(pm * best, &ex);
+            pe += ex;
+            const float2 piv = WT(k, k);
+            const float inv = 1.0f / best;
+            const float2 ip = make_float2(piv.x * inv, -piv.y * inv);
+            // the pivot row's tail in registers; each trailing element is
+            // loaded and stored once per step
+            float2 pc[MT];
+#pragma unroll
+            for (int c = k + 1; c < MT; ++c) pc[c] = WT(k, c);
+#pragma unroll
+            for (int r = k + 1; r < MT; ++r) {
+              const float2 a = WT(r, k);
+              const float2 f = make_float2(a.x * ip.x - a.y * ip.y, a.x * ip.y + a.y * ip.x);
+#pragma unroll
+              for (int c = k + 1; c < MT; ++c) {
+                float2 z = WT(r, c);
+                z.x -= f.x * pc[c].x - f.y * pc[c].y;
+                z.y -= f.x * pc[c].y + f.y * pc[c].x;
+                WT(r, c) = z;
+              }
+            }
           }
         }
       }
