@@ -558,8 +558,8 @@ static const int kSplitBand = 2;
 static const int kSoftOrder = 32;
 static const int64_t kSoftCapJobs = 1ll << 25;
 // fused (single-launch) expansion buffers: initial and largest capacities
-static const int64_t kFusedJobs0 = 1ll << 15;
-static const int64_t kFusedWords0 = 1ll << 21;
+static const int64_t kFusedJobs0 = 1ll << 17;
+static const int64_t kFusedWords0 = 1ll << 23;
 static const int64_t kFusedMaxJobs = 1ll << 20;
 static const int64_t kFusedMaxWords = 1ll << 26;
 
