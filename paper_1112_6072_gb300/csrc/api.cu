@@ -723,6 +723,8 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
       const int32_t herr = (int32_t)(st0 & 0xffffffff);
       if (herr != 0) return (perm_status)herr;
       if (!levels_left(S.level, S.ncur, S.max_open)) break;
+      const bool room = K * S.ncur > cap_jobs || K * S.used_words > cap_words;
+      if (!room) continue;  // the orders now fit a narrower variant: launch it
       // stopped for room: grow, or hand over to the per-level loop
       if (cap_jobs >= kFusedMaxJobs || cap_words >= kFusedMaxWords) break;
       if (K * S.ncur > cap_jobs) cap_jobs = std::min<int64_t>(kFusedMaxJobs, 4 * cap_jobs);

@@ -143,6 +143,13 @@ __device__ __forceinline__ bool child_row(const CsrView& v, const ChildSpec& cs,
   return ok;
 }
 
+// Largest order and largest order still to split among a warp's kept
+// children (lane 0), flushed to the level's maxima once per warp.
+struct WarpMax {
+  int order = 0;
+  int open = 0;
+};
+
 // Where children's blocks go: reserved (cbase + c * parent words) or
 // bump-allocated from a per-level counter.
 struct ExpandCtx {
@@ -153,8 +160,6 @@ struct ExpandCtx {
   const int64_t* child_off_base;  // reserved mode, else null
   unsigned long long* bump;       // bump mode: words used in arena_out
   int64_t cap_words;              // bump mode: arena_out capacity
-  int32_t* max_order;             // bump mode: largest kept order
-  int32_t* max_open;              // bump mode: largest order of a kept job still to split
   int32_t* valid;
   int32_t leaf_size;
   int32_t split_floor;            // parents of a lower order wait for a later level
@@ -186,7 +191,7 @@ __device__ __forceinline__ int64_t child_block(const ExpandCtx& X, int64_t p, in
 
 // Parent p unchanged into slot Kp with depth_left dl_out.
 __device__ void carry_parent(const ExpandCtx& X, int64_t p, const uint64_t* src, int64_t pw, int m, int nnz,
-                             int dl_out, int lane) {
+                             int dl_out, int lane, WarpMax& wm) {
   const int64_t o = child_block(X, p, 0, pw, pw, lane);
   if (o >= 0) copy_words(X.arena_out + o, src, pw, lane);
   if (lane == 0) {
@@ -200,8 +205,8 @@ __device__ void carry_parent(const ExpandCtx& X, int64_t p, const uint64_t* src,
       X.child.mat[c0] = X.parent.mat[p];
       X.child.depth_left[c0] = dl_out;
       for (int w = 0; w < 4; ++w) X.child.coef[4 * c0 + w] = X.parent.coef[4 * p + w];
-      if (X.max_order) atomicMax(X.max_order, m);
-      if (X.max_open && dl_out > 0) atomicMax(X.max_open, m);
+      wm.order = max(wm.order, m);
+      if (dl_out > 0) wm.open = max(wm.open, m);
     }
   }
 }
@@ -213,7 +218,7 @@ __device__ void carry_parent(const ExpandCtx& X, int64_t p, const uint64_t* src,
 // cases); -1: all.
 template <int RPL>
 __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* ccnt, uint64_t* stage,
-                              int only_child = -1) {
+                              WarpMax& wm, int only_child = -1) {
   const int m = X.parent.m[p];
   const int nnz = X.parent.nnz[p];
   const int64_t off = X.parent.off[p];
@@ -222,7 +227,7 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
   const int cut = X.leaf_size > 2 ? X.leaf_size : 2;
   __syncwarp();  // the previous parent's reads of stage and ccnt are done
   if (dl > 0 && m > cut && m < X.split_floor) {
-    if (only_child <= 0) carry_parent(X, p, X.arena_in + off, pw, m, nnz, dl, lane);
+    if (only_child <= 0) carry_parent(X, p, X.arena_in + off, pw, m, nnz, dl, lane, wm);
     return;
   }
   const uint64_t* src = X.arena_in + off;
@@ -263,7 +268,7 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
     return;
   }
   if (dl <= 0 || m <= cut || (s >= 5 && !three)) {
-    if (only_child <= 0) carry_parent(X, p, src, pw, m, nnz, 0, lane);
+    if (only_child <= 0) carry_parent(X, p, src, pw, m, nnz, 0, lane, wm);
     return;
   }
   // pivot line's nonzero positions (ascending) and values
@@ -440,8 +445,8 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
         X.child.depth_left[slot] = dl - 1;
         u256 cc = cs.fac == 1 ? pcoef : u256_mul_s64(pcoef, cs.fac);
         for (int w = 0; w < 4; ++w) X.child.coef[4 * slot + w] = cc.w[w];
-        if (X.max_order) atomicMax(X.max_order, mc);
-        if (X.max_open && dl - 1 > 0 && mc > cut) atomicMax(X.max_open, mc);
+        wm.order = max(wm.order, mc);
+        if (dl - 1 > 0 && mc > cut) wm.open = max(wm.open, mc);
       }
     }
   }
@@ -461,16 +466,15 @@ __global__ void __launch_bounds__(kLevelWarps * 32) k_expand_level(ExpandLevelAr
   X.child_off_base = A.child_off_base;
   X.bump = nullptr;
   X.cap_words = 0;
-  X.max_order = nullptr;
-  X.max_open = nullptr;
   X.valid = A.valid;
   X.leaf_size = A.leaf_size;
   X.split_floor = A.split_floor;
   X.kslots = A.kslots;
   X.err = A.err;
   const int64_t nwarps = (int64_t)gridDim.x * kLevelWarps;
+  WarpMax wm;  // unused: the compaction takes the level's maxima
   for (int64_t p = (int64_t)blockIdx.x * kLevelWarps + wib; p < A.np; p += nwarps)
-    expand_parent<RPL>(X, p, lane, ccnt[wib], stage + wib * kStageWords);
+    expand_parent<RPL>(X, p, lane, ccnt[wib], stage + wib * kStageWords, wm);
 }
 
 // ---- multi-level driver ---------------------------------------------------------
@@ -552,8 +556,11 @@ __global__ void __launch_bounds__(kFrontThreads) k_expand_front(ExpandFrontArgs 
     // between the same two barriers (the flag is only raised while
     // children are built, before the first barrier of a level)
     const int K = F.kslots;
+    // also stop when every order fits the next narrower variant (fewer rows
+    // per lane): the host launches that one for the remaining levels
     bool stop = failed || S.level >= F.max_levels || S.ncur <= 0 || S.max_order > RPL * 32 ||
-                K * S.ncur > F.cap_jobs || K * S.used_words > F.cap_words;
+                (RPL > 1 && S.max_order <= RPL * 16) || K * S.ncur > F.cap_jobs ||
+                K * S.used_words > F.cap_words;
     if (!stop && F.adaptive) {
       const bool big = S.max_open > F.big_order;
       const bool soft = S.max_open > F.soft_order && S.ncur < F.soft_cap_jobs;
@@ -570,21 +577,24 @@ __global__ void __launch_bounds__(kFrontThreads) k_expand_front(ExpandFrontArgs 
     X.child_off_base = nullptr;
     X.bump = F.lvl_words + S.level;
     X.cap_words = F.cap_words;
-    X.max_order = F.lvl_maxo + S.level;
-    X.max_open = F.lvl_maxopen + S.level;
     X.valid = F.valid;
     X.leaf_size = F.leaf_size;
     X.split_floor = F.adaptive ? S.max_open - F.band : 0;
     X.kslots = F.kslots;
     X.err = F.err;
     const int64_t p0 = S.ncur * b / G, p1 = S.ncur * (b + 1) / G;
+    WarpMax wm;
     if (K * S.ncur <= G * kFrontWarps) {
       // small frontier: a warp per child, cutting the level's latency
       for (int64_t t = K * p0 + wib; t < K * p1; t += kFrontWarps)
-        expand_parent<RPL>(X, t / K, lane, ccnt[wib], stage + wib * kStageWords, (int)(t % K));
+        expand_parent<RPL>(X, t / K, lane, ccnt[wib], stage + wib * kStageWords, wm, (int)(t % K));
     } else {
       for (int64_t p = p0 + wib; p < p1; p += kFrontWarps)
-        expand_parent<RPL>(X, p, lane, ccnt[wib], stage + wib * kStageWords);
+        expand_parent<RPL>(X, p, lane, ccnt[wib], stage + wib * kStageWords, wm);
+    }
+    if (lane == 0) {  // one update of the level's maxima per warp
+      if (wm.order > 0) atomicMax(F.lvl_maxo + S.level, wm.order);
+      if (wm.open > 0) atomicMax(F.lvl_maxopen + S.level, wm.open);
     }
     __syncthreads();
     long long kept = 0;
