@@ -68,6 +68,41 @@ __device__ __forceinline__ bool mad2_checked(int64_t a, int64_t x, int64_t b, in
   return r == (__int128)out;
 }
 
+// A group of LW lanes (the whole warp, or a half warp for parents of order
+// <= 16) that works on one parent: every collective takes only its lanes.
+template <int LW>
+struct Grp {
+  unsigned mask;  // lanes of the group
+  int base;       // its first lane
+  int sub;        // this lane's index in the group
+  __device__ explicit Grp(int lane) {
+    base = LW == 32 ? 0 : (lane & ~(LW - 1));
+    sub = lane - base;
+    mask = LW == 32 ? 0xffffffffu : (((1u << (LW & 31)) - 1u) << base);
+  }
+  __device__ void sync() const { __syncwarp(mask); }
+  __device__ unsigned min(unsigned v) const { return __reduce_min_sync(mask, v); }
+  __device__ unsigned ballot(bool q) const { return __ballot_sync(mask, q) >> base; }
+  __device__ bool any(bool q) const { return __any_sync(mask, q); }
+  template <typename T>
+  __device__ T shfl(T v, int from) const { return __shfl_sync(mask, v, base + from); }
+  __device__ uint64_t or_all(uint64_t v) const {
+#pragma unroll
+    for (int d = LW / 2; d > 0; d >>= 1) v |= __shfl_xor_sync(mask, v, d);
+    return v;
+  }
+  __device__ int excl_scan(int v, int& total) const {
+    int x = v;
+#pragma unroll
+    for (int d = 1; d < LW; d <<= 1) {
+      const int y = __shfl_up_sync(mask, x, d, LW);
+      if (sub >= d) x += y;
+    }
+    total = __shfl_sync(mask, x, base + LW - 1);
+    return x - v;
+  }
+};
+
 struct ChildSpec {
   int del_row, del_col;  // kNone for the cleared child
   int merge;      // 0 none, 1 column p merged (row pivot), 2 row p merged (column pivot),
@@ -167,34 +202,37 @@ struct ExpandCtx {
   int32_t* err;
 };
 
-__device__ __forceinline__ void copy_words(uint64_t* dst, const uint64_t* src, int64_t words, int lane) {
+__device__ __forceinline__ void copy_words(uint64_t* dst, const uint64_t* src, int64_t words, int sub, int step) {
   // blocks start on 16 bytes and hold an even number of words
   const uint4* s4 = reinterpret_cast<const uint4*>(src);
   uint4* d4 = reinterpret_cast<uint4*>(dst);
-  for (int64_t k = lane; k < words / 2; k += 32) d4[k] = s4[k];
+  for (int64_t k = sub; k < words / 2; k += step) d4[k] = s4[k];
 }
 
-// Offset of a child's block: lane 0 allocates, the warp gets it back.  -1 if
-// the arena is full (bump mode; the caller's capacity rule excludes it).
+// Offset of a child's block: the group's first lane allocates, the group
+// gets it back.  -1 if the arena is full (bump mode; the caller's capacity
+// rule excludes it).
+template <int LW>
 __device__ __forceinline__ int64_t child_block(const ExpandCtx& X, int64_t p, int c, int64_t pw, int64_t words,
-                                               int lane) {
+                                               const Grp<LW>& G) {
   if (X.child_off_base) return X.child_off_base[p] + c * pw;
   unsigned long long o = 0;
-  if (lane == 0) o = atomicAdd(X.bump, (unsigned long long)words);
-  o = __shfl_sync(0xffffffffu, o, 0);
+  if (G.sub == 0) o = atomicAdd(X.bump, (unsigned long long)words);
+  o = G.shfl(o, 0);
   if ((int64_t)o + words > X.cap_words) {
-    if (lane == 0) atomicCAS(X.err, 0, PERM_ENOMEM);
+    if (G.sub == 0) atomicCAS(X.err, 0, PERM_ENOMEM);
     return -1;
   }
   return (int64_t)o;
 }
 
 // Parent p unchanged into slot Kp with depth_left dl_out.
+template <int LW>
 __device__ void carry_parent(const ExpandCtx& X, int64_t p, const uint64_t* src, int64_t pw, int m, int nnz,
-                             int dl_out, int lane, WarpMax& wm) {
-  const int64_t o = child_block(X, p, 0, pw, pw, lane);
-  if (o >= 0) copy_words(X.arena_out + o, src, pw, lane);
-  if (lane == 0) {
+                             int dl_out, const Grp<LW>& G, WarpMax& wm) {
+  const int64_t o = child_block(X, p, 0, pw, pw, G);
+  if (o >= 0) copy_words(X.arena_out + o, src, pw, G.sub, LW);
+  if (G.sub == 0) {
     const int64_t c0 = (int64_t)X.kslots * p;
     X.valid[c0] = o >= 0 ? 1 : 0;
     for (int c = 1; c < X.kslots; ++c) X.valid[c0 + c] = 0;
@@ -211,53 +249,55 @@ __device__ void carry_parent(const ExpandCtx& X, int64_t p, const uint64_t* src,
   }
 }
 
-// Divide parent p (one warp).  ccnt: the warp's shared-memory column counts
-// (RPL * 32 entries); stage: its kStageWords-word copy of the parent block.
+// Divide parent p (one group of LW lanes; lane l of the group owns rows l,
+// l + LW, ...).  ccnt: the group's shared-memory column counts (RPL * LW
+// entries); stage: its stage_words-word copy of the parent block.
 // only_child >= 0: build that child alone (one warp per child when the
 // frontier is small; the child-0 warp also writes the carried and dropped
 // cases); -1: all.
-template <int RPL>
-__device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* ccnt, uint64_t* stage,
-                              WarpMax& wm, int only_child = -1) {
+template <int RPL, int LW>
+__device__ void expand_parent(const ExpandCtx& X, int64_t p, const Grp<LW>& G, int32_t* ccnt, uint64_t* stage,
+                              int stage_words, WarpMax& wm, int only_child = -1) {
+  const int lane = G.sub;
   const int m = X.parent.m[p];
   const int nnz = X.parent.nnz[p];
   const int64_t off = X.parent.off[p];
   const int dl = X.parent.depth_left[p];
   const int64_t pw = blk_words(m, nnz);
   const int cut = X.leaf_size > 2 ? X.leaf_size : 2;
-  __syncwarp();  // the previous parent's reads of stage and ccnt are done
+  G.sync();  // the previous parent's reads of stage and ccnt are done
   if (dl > 0 && m > cut && m < X.split_floor) {
-    if (only_child <= 0) carry_parent(X, p, X.arena_in + off, pw, m, nnz, dl, lane, wm);
+    if (only_child <= 0) carry_parent(X, p, X.arena_in + off, pw, m, nnz, dl, G, wm);
     return;
   }
   const uint64_t* src = X.arena_in + off;
-  if (pw <= kStageWords) {
-    copy_words(stage, src, pw, lane);
+  if (pw <= stage_words) {
+    copy_words(stage, src, pw, lane, LW);
     src = stage;
   }
   // line counts: rows from rowptr, columns by shared-memory atomics
-  for (int c = lane; c < m; c += 32) ccnt[c] = 0;
-  __syncwarp();
+  for (int c = lane; c < m; c += LW) ccnt[c] = 0;
+  G.sync();
   const CsrView v = csr_view(src, 0, m, nnz);
   // (count << 17) | (is_col << 16) | index: count <= 128, index < 128
   unsigned key = 0xffffffffu;
 #pragma unroll
   for (int k = 0; k < RPL; ++k) {
-    const int r = lane + 32 * k;
+    const int r = lane + LW * k;
     if (r < m) {
       const int b = v.rowptr[r], e = v.rowptr[r + 1];
       key = min(key, ((unsigned)(e - b) << 17) | (unsigned)r);
       for (int t = b; t < e; ++t) atomicAdd(&ccnt[v.col[t]], 1);
     }
   }
-  __syncwarp();
+  G.sync();
 #pragma unroll
   for (int k = 0; k < RPL; ++k) {
-    const int c = lane + 32 * k;
+    const int c = lane + LW * k;
     if (c < m) key = min(key, ((unsigned)ccnt[c] << 17) | (1u << 16) | (unsigned)c);
   }
-  __syncwarp();  // counts read before the next parent clears them
-  key = __reduce_min_sync(0xffffffffu, key);
+  G.sync();  // counts read before the next parent clears them
+  key = G.min(key);
   const int s = (int)(key >> 17);
   const bool is_col = (key >> 16) & 1;
   const int idx = (int)(key & 0xffff);
@@ -268,7 +308,7 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
     return;
   }
   if (dl <= 0 || m <= cut || (s >= 5 && !three)) {
-    if (only_child <= 0) carry_parent(X, p, src, pw, m, nnz, 0, lane, wm);
+    if (only_child <= 0) carry_parent(X, p, src, pw, m, nnz, 0, G, wm);
     return;
   }
   // pivot line's nonzero positions (ascending) and values
@@ -290,22 +330,22 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
     }
 #pragma unroll
     for (int k = 0; k < RPL; ++k) {
-      const int r = lane + 32 * k;
+      const int r = lane + LW * k;
       int64_t x = 0;
       if (r < m) {
         const int b = v.rowptr[r], e = v.rowptr[r + 1];
         for (int t = b; t < e; ++t)
           if (v.col[t] == idx) x = v.val[t];
       }
-      unsigned bal = __ballot_sync(0xffffffffu, x != 0);
+      unsigned bal = G.ballot(x != 0);
       while (bal) {
         const int l = __ffs(bal) - 1;
         bal &= bal - 1;
-        const long long xv = __shfl_sync(0xffffffffu, (long long)x, l);
+        const long long xv = G.shfl((long long)x, l);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
           if (u == n) {
-            pos[u] = l + 32 * k;
+            pos[u] = l + LW * k;
             pv[u] = xv;
           }
         ++n;
@@ -371,7 +411,7 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
     bool ovf = false;
 #pragma unroll
     for (int k = 0; k < RPL; ++k) {
-      const int rc = lane + 32 * k;
+      const int rc = lane + LW * k;
       int n = 0;
       if (rc < mc) {
         const int r = rc + (rc >= cs.del_row);
@@ -386,17 +426,14 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
       }
       cnt[k] = n;
     }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      cm0 |= __shfl_xor_sync(0xffffffffu, cm0, d);
-      cm1 |= __shfl_xor_sync(0xffffffffu, cm1, d);
-    }
+    cm0 = G.or_all(cm0);
+    cm1 = G.or_all(cm1);
     bool zero_row = false;
 #pragma unroll
     for (int k = 0; k < RPL; ++k)
-      if (lane + 32 * k < mc && cnt[k] == 0) zero_row = true;
-    zero_row = __any_sync(0xffffffffu, zero_row);
-    ovf = __any_sync(0xffffffffu, ovf);
+      if (lane + LW * k < mc && cnt[k] == 0) zero_row = true;
+    zero_row = G.any(zero_row);
+    ovf = G.any(ovf);
     if (ovf && lane == 0) atomicCAS(X.err, 0, PERM_EOVERFLOW);
     const int ncols = __popcll(cm0) + __popcll(cm1);
     bool keep = !ovf && !zero_row && ncols == mc;
@@ -407,10 +444,10 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
 #pragma unroll
       for (int k = 0; k < RPL; ++k) {
         int tot;
-        offs[k] = cnnz + warp_excl_scan(cnt[k], lane, tot);
+        offs[k] = cnnz + G.excl_scan(cnt[k], tot);
         cnnz += tot;
       }
-      o = child_block(X, p, c, pw, blk_words(mc, cnnz), lane);
+      o = child_block(X, p, c, pw, blk_words(mc, cnnz), G);
       keep = o >= 0;
     }
     if (keep) {
@@ -422,7 +459,7 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, int lane, int32_t* 
       if (lane == 0) rowptr[mc] = (uint16_t)cnnz;
 #pragma unroll
       for (int k = 0; k < RPL; ++k) {
-        const int rc = lane + 32 * k;
+        const int rc = lane + LW * k;
         if (rc < mc) {
           const int r = rc + (rc >= cs.del_row);
           rowptr[rc] = (uint16_t)offs[k];
@@ -473,8 +510,9 @@ __global__ void __launch_bounds__(kLevelWarps * 32) k_expand_level(ExpandLevelAr
   X.err = A.err;
   const int64_t nwarps = (int64_t)gridDim.x * kLevelWarps;
   WarpMax wm;  // unused: the compaction takes the level's maxima
+  const Grp<32> G(lane);
   for (int64_t p = (int64_t)blockIdx.x * kLevelWarps + wib; p < A.np; p += nwarps)
-    expand_parent<RPL>(X, p, lane, ccnt[wib], stage + wib * kStageWords, wm);
+    expand_parent<RPL, 32>(X, p, G, ccnt[wib], stage + wib * kStageWords, kStageWords, wm);
 }
 
 // ---- multi-level driver ---------------------------------------------------------
@@ -539,15 +577,21 @@ __device__ bool grid_barrier(unsigned long long* bar, unsigned long long& target
   return __syncthreads_or(failed) == 0;
 }
 
-template <int RPL>
+template <int RPL, int LW>
 __global__ void __launch_bounds__(kFrontThreads) k_expand_front(ExpandFrontArgs F) {
-  __shared__ int32_t ccnt[kFrontWarps][RPL * 32];
+  // groups of LW lanes, one parent (or child) each
+  constexpr int GPW = 32 / LW;
+  constexpr int NG = kFrontWarps * GPW;
+  constexpr int SW = kStageWords / GPW;  // stage words per group
+  __shared__ int32_t ccnt[NG][RPL * LW];
   extern __shared__ __align__(16) uint64_t stage[];
   __shared__ long long red64[kFrontWarps];
   __shared__ int red32[kFrontWarps];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int64_t G = gridDim.x, b = blockIdx.x;
+  const Grp<LW> grp(lane);
+  const int gid = wib * GPW + lane / LW;
   unsigned long long target = 0;
   ExpandFrontState S = *F.state;
   bool failed = false;  // an error flag raised during the last level
@@ -558,9 +602,9 @@ __global__ void __launch_bounds__(kFrontThreads) k_expand_front(ExpandFrontArgs 
     const int K = F.kslots;
     // also stop when every order fits the next narrower variant (fewer rows
     // per lane): the host launches that one for the remaining levels
-    bool stop = failed || S.level >= F.max_levels || S.ncur <= 0 || S.max_order > RPL * 32 ||
-                (RPL > 1 && S.max_order <= RPL * 16) || K * S.ncur > F.cap_jobs ||
-                K * S.used_words > F.cap_words;
+    constexpr int narrower = LW == 16 ? 0 : (RPL > 1 ? RPL * 16 : 16);
+    bool stop = failed || S.level >= F.max_levels || S.ncur <= 0 || S.max_order > RPL * LW ||
+                S.max_order <= narrower || K * S.ncur > F.cap_jobs || K * S.used_words > F.cap_words;
     if (!stop && F.adaptive) {
       const bool big = S.max_open > F.big_order;
       const bool soft = S.max_open > F.soft_order && S.ncur < F.soft_cap_jobs;
@@ -584,15 +628,15 @@ __global__ void __launch_bounds__(kFrontThreads) k_expand_front(ExpandFrontArgs 
     X.err = F.err;
     const int64_t p0 = S.ncur * b / G, p1 = S.ncur * (b + 1) / G;
     WarpMax wm;
-    if (K * S.ncur <= G * kFrontWarps) {
-      // small frontier: a warp per child, cutting the level's latency
-      for (int64_t t = K * p0 + wib; t < K * p1; t += kFrontWarps)
-        expand_parent<RPL>(X, t / K, lane, ccnt[wib], stage + wib * kStageWords, wm, (int)(t % K));
+    if (K * S.ncur <= G * NG) {
+      // small frontier: a group per child, cutting the level's latency
+      for (int64_t t = K * p0 + gid; t < K * p1; t += NG)
+        expand_parent<RPL, LW>(X, t / K, grp, ccnt[gid], stage + gid * SW, SW, wm, (int)(t % K));
     } else {
-      for (int64_t p = p0 + wib; p < p1; p += kFrontWarps)
-        expand_parent<RPL>(X, p, lane, ccnt[wib], stage + wib * kStageWords, wm);
+      for (int64_t p = p0 + gid; p < p1; p += NG)
+        expand_parent<RPL, LW>(X, p, grp, ccnt[gid], stage + gid * SW, SW, wm);
     }
-    if (lane == 0) {  // one update of the level's maxima per warp
+    if (grp.sub == 0) {  // one update of the level's maxima per group
       if (wm.order > 0) atomicMax(F.lvl_maxo + S.level, wm.order);
       if (wm.open > 0) atomicMax(F.lvl_maxopen + S.level, wm.open);
     }
@@ -655,24 +699,26 @@ cudaError_t launch_level_rpl(const ExpandLevelArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int RPL>
+template <int RPL, int LW>
 cudaError_t launch_front_rpl(ExpandFrontArgs a, int* grid, cudaStream_t s) {
   int dev = 0, sms = 0, coop = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_expand_front<RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFrontSmem);
+    e = cudaFuncSetAttribute(k_expand_front<RPL, LW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kFrontSmem);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand_front<RPL>, kFrontThreads, kFrontSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand_front<RPL, LW>, kFrontThreads,
+                                                      kFrontSmem);
   if (e != cudaSuccess) return e;
   *grid = 0;
   if (!coop || per_sm <= 0) return cudaSuccess;  // not available: per-level launches only
   int g = sms * (per_sm < 2 ? per_sm : 2);
   if (g > PERM_FRONT_MAX_BLOCKS) g = PERM_FRONT_MAX_BLOCKS;
   void* args[] = {&a};
-  e = cudaLaunchCooperativeKernel((const void*)k_expand_front<RPL>, dim3((unsigned)g), dim3(kFrontThreads), args,
-                                  kFrontSmem, s);
+  e = cudaLaunchCooperativeKernel((const void*)k_expand_front<RPL, LW>, dim3((unsigned)g), dim3(kFrontThreads),
+                                  args, kFrontSmem, s);
   if (e == cudaSuccess) *grid = g;
   return e;
 }
@@ -687,9 +733,10 @@ cudaError_t launch_expand_level(const ExpandLevelArgs& a, int max_order, cudaStr
 }
 
 cudaError_t launch_expand_front(const ExpandFrontArgs& a, int max_order, int* grid, cudaStream_t s) {
-  if (max_order <= 32) return launch_front_rpl<1>(a, grid, s);
-  if (max_order <= 64) return launch_front_rpl<2>(a, grid, s);
-  return launch_front_rpl<4>(a, grid, s);
+  if (max_order <= 16) return launch_front_rpl<1, 16>(a, grid, s);
+  if (max_order <= 32) return launch_front_rpl<1, 32>(a, grid, s);
+  if (max_order <= 64) return launch_front_rpl<2, 32>(a, grid, s);
+  return launch_front_rpl<4, 32>(a, grid, s);
 }
 
 __global__ void k_child_capacity(JobArrays parent, int64_t np, int kslots, int64_t* words) {
