@@ -78,11 +78,11 @@ __device__ __forceinline__ int nth_bit(uint64_t mask, int n) {
 
 __device__ __forceinline__ uint64_t bit64(int i) { return 1ull << i; }
 
-// One leaf walk per (NMAX, W, path), kept out of line: the node loop of the
-// evaluator stays small in the instruction cache, and each walk exists once.
+// One leaf walk per (NMAX, W, path), inlined (measured 2-3 % faster than
+// out of line: the walk keeps the registers it needs).
 // path: 0/1/2 plain walk with bit class 7/15/31, 3 blocked NN=8, 4 blocked NN=16
 template <int NM, int W, int PATH>
-__device__ __noinline__ void leaf_walk(const int32_t* delta, const int32_t* rho0, int m, uint64_t gb, uint64_t cnt,
+__device__ __forceinline__ void leaf_walk(const int32_t* delta, const int32_t* rho0, int m, uint64_t gb, uint64_t cnt,
                                        uint64_t* words) {
   if constexpr (PATH == 3) {
     run_lane4<NM, 8, W>(delta, rho0, m, gb, cnt, words);
