@@ -20,6 +20,54 @@ constexpr uint64_t K_JOB = 0xD1B54A32D192ED03ull;
 constexpr uint64_t K_TRIAL = 0xABC98388FB8FAC03ull;
 constexpr uint64_t K_ENTRY = 0x8CB92BA72F3D8DD7ull;
 
+constexpr double LN2 = 0.69314718055994530942;
+
+// Running sum of the trials' |det W|^2 = pm * 2^pe (pm in [1/2, 1)), held as
+// S * 2^E with S a double: adding a trial scales by a power of two and takes
+// no logarithm or exponential.
+struct Pow2Sum {
+  double S = 0.0;
+  int E = -(1 << 30);
+  // 2^e for e <= 0; 0 below the normal range (such a term is below 2^-1022
+  // of the running sum)
+  __device__ __forceinline__ static double pow2(int e) {
+    return e < -1022 ? 0.0 : __hiloint2double((e + 1023) << 20, 0);
+  }
+  __device__ __forceinline__ void add(float pm, int pe) {
+    if (pe > E) {
+      S = S * pow2(E - pe) + (double)pm;
+      E = pe;
+    } else {
+      S += (double)pm * pow2(pe - E);
+    }
+  }
+  __device__ __forceinline__ void merge(double oS, int oE) {
+    const int e = oE > E ? oE : E;
+    S = S * pow2(E - e) + oS * pow2(oE - e);
+    E = e;
+  }
+  // butterfly merge with the lanes at xor distances d0, 2 d0, ..., 16
+  __device__ __forceinline__ void warp_merge(int d0) {
+    for (int d = d0; d < 32; d <<= 1) merge(__shfl_xor_sync(0xffffffffu, S, d), __shfl_xor_sync(0xffffffffu, E, d));
+  }
+  // as a log-sum-exp pair: the sum is lsum * e^lmax
+  __device__ __forceinline__ void lse(double& lmax, double& lsum) const {
+    if (S > 0.0) {
+      lmax = (double)E * LN2;
+      lsum = S;
+    } else {
+      lmax = -INFINITY;
+      lsum = 0.0;
+    }
+  }
+};
+
+// e^(2 pi i w / 3), w in {0, 1, 2}
+__device__ __forceinline__ float2 cube_root(uint32_t w) {
+  const float h = 0.86602540378443864676f;  // sqrt(3) / 2
+  return make_float2(w == 0 ? 1.0f : -0.5f, w == 0 ? 0.0f : (w == 1 ? h : -h));
+}
+
 // SplitMix64's output function (Steele, Lea, Flood, OOPSLA 2014).
 __device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
   z += 0x9E3779B97F4A7C15ull;
@@ -50,8 +98,6 @@ __global__ void __launch_bounds__(KCfg<TILE>::WARPS * 32)
   unsigned char* base = smem_raw + (size_t)wib * KCfg<TILE>::WARP_BYTES;
   float2* Wm = reinterpret_cast<float2*>(base);
   uint64_t* pat = reinterpret_cast<uint64_t*>(base + sizeof(float2) * TILE * S);
-  const float RE[3] = {1.0f, -0.5f, -0.5f};
-  const float IM[3] = {0.0f, 0.86602540378443864676f, -0.86602540378443864676f};
   const int64_t nwarps = (int64_t)gridDim.x * KCfg<TILE>::WARPS;
   for (int64_t job = (int64_t)blockIdx.x * KCfg<TILE>::WARPS + wib; job < njobs; job += nwarps) {
     __syncwarp();
@@ -77,7 +123,7 @@ __global__ void __launch_bounds__(KCfg<TILE>::WARPS * 32)
     __syncwarp();
     const int T = trials > 0 ? trials : m * m;
     const uint64_t jkey = seed ^ ((uint64_t)job * K_JOB);
-    double lmax = -INFINITY, lsum = 0.0;  // running log-sum-exp (lane 0)
+    Pow2Sum acc;  // lane 0
     for (int t = 0; t < T; ++t) {
       const uint64_t tkey = jkey ^ ((uint64_t)t * K_TRIAL);
       // trial matrix
@@ -90,7 +136,7 @@ __global__ void __launch_bounds__(KCfg<TILE>::WARPS * 32)
           if (c < m && ((b >> (c & 63)) & 1)) {
             const uint64_t h = splitmix64_mix(tkey ^ ((uint64_t)(r * m + c) * K_ENTRY));
             const int w = (int)(((h >> 32) * 3ull) >> 32);
-            z = make_float2(RE[w], IM[w]);
+            z = cube_root((uint32_t)w);
           }
           if (c < m) Wm[r * S + c] = z;
         }
@@ -164,18 +210,12 @@ __global__ void __launch_bounds__(KCfg<TILE>::WARPS * 32)
         }
         __syncwarp();
       }
-      if (lane == 0 && !singular) {
-        const double l = log((double)pm) + (double)pe * 0.69314718055994530942;
-        if (l > lmax) {
-          lsum = lsum * exp(lmax - l) + 1.0;
-          lmax = l;
-        } else {
-          lsum += exp(l - lmax);
-        }
-      }
+      if (lane == 0 && !singular) acc.add(pm, pe);
       __syncwarp();
     }
     if (lane == 0) {
+      double lmax, lsum;
+      acc.lse(lmax, lsum);
       log_ap[job] = lmax == -INFINITY ? -INFINITY : (float)(lmax + log(lsum / (double)T));
     }
   }
@@ -218,8 +258,6 @@ __global__ void __launch_bounds__(128)
   const unsigned gmask = (RL == 32) ? 0xffffffffu : (((1u << RL) - 1u) << (grp * RL));
   float2* prow = prow_s[wib][grp];
   uint32_t* pat = pat_s[wib];
-  const float RE[3] = {1.0f, -0.5f, -0.5f};
-  const float IM[3] = {0.0f, 0.86602540378443864676f, -0.86602540378443864676f};
   const int64_t nwarps = (int64_t)gridDim.x * 4;
   for (int64_t job = (int64_t)blockIdx.x * 4 + wib; job < njobs; job += nwarps) {
     __syncwarp();
@@ -238,7 +276,7 @@ __global__ void __launch_bounds__(128)
     const int T = trials > 0 ? trials : m * m;
     const uint64_t jkey = seed ^ ((uint64_t)job * K_JOB);
     const uint32_t myrow = r < m ? pat[r] : 0u;
-    double lmax = -INFINITY, lsum = 0.0;  // running log-sum-exp of this group's trials
+    Pow2Sum acc;  // this group's trials (lane r == 0)
     const int rounds = (T + TPW - 1) / TPW;
     for (int it = 0; it < rounds; ++it) {
       const int t = it * TPW + grp;
@@ -251,7 +289,7 @@ __global__ void __launch_bounds__(128)
         if (live && c < m && ((myrow >> c) & 1)) {
           const uint64_t h = splitmix64_mix(tkey ^ ((uint64_t)(r * m + c) * K_ENTRY));
           const int w = (int)(((h >> 32) * 3ull) >> 32);
-          z = make_float2(RE[w], IM[w]);
+          z = cube_root((uint32_t)w);
         }
         row[c] = z;
       }
@@ -308,28 +346,12 @@ __global__ void __launch_bounds__(128)
           }
         }
       }
-      if (r == 0 && !singular) {
-        const double l = log((double)pm) + (double)pe * 0.69314718055994530942;
-        if (l > lmax) {
-          lsum = lsum * exp(lmax - l) + 1.0;
-          lmax = l;
-        } else {
-          lsum += exp(l - lmax);
-        }
-      }
+      if (r == 0 && !singular) acc.add(pm, pe);
     }
-    // merge the groups' log-sum-exp accumulators into lane 0
-#pragma unroll
-    for (int d = RL; d < 32; d <<= 1) {
-      const double om = __shfl_down_sync(0xffffffffu, lmax, d);
-      const double os = __shfl_down_sync(0xffffffffu, lsum, d);
-      if (om > lmax) {
-        lsum = lsum * exp(lmax - om) + os;
-        lmax = om;
-      } else if (om > -INFINITY) {
-        lsum += os * exp(om - lmax);
-      }
-    }
+    // merge the groups' sums (held by their lanes r == 0)
+    acc.warp_merge(RL);
+    double lmax, lsum;
+    acc.lse(lmax, lsum);
     if (lane == 0) log_ap[job] = lmax == -INFINITY ? -INFINITY : (float)(lmax + log(lsum / (double)T));
   }
 }
@@ -341,9 +363,11 @@ __global__ void __launch_bounds__(128)
 // second kernel combines a job's parts.
 template <int MT>
 struct TCfg {
-  static constexpr int WARPS = MT <= 8 ? 12 : (MT <= 12 ? 5 : 3);
+  // as many warps as 227 KB of shared memory holds (14, 6, 3)
+  static constexpr int WARPS = MT <= 8 ? 14 : (MT <= 12 ? 6 : 3);
   static constexpr size_t WARP_BYTES = sizeof(float2) * MT * MT * 32;
   static constexpr size_t SMEM = WARPS * WARP_BYTES;
+  static_assert(SMEM <= 232448, "at most 227 KB of dynamic shared memory per block");
 };
 
 template <int MT>
@@ -355,8 +379,6 @@ __global__ void __launch_bounds__(TCfg<MT>::WARPS * 32)
   const int wib = threadIdx.x >> 5;
   float2* Wt = reinterpret_cast<float2*>(smem_raw + (size_t)wib * TCfg<MT>::WARP_BYTES);
 #define WT(i, j) Wt[((i) * MT + (j)) * 32 + lane]
-  const float RE[3] = {1.0f, -0.5f, -0.5f};
-  const float IM[3] = {0.0f, 0.86602540378443864676f, -0.86602540378443864676f};
   const int64_t items = njobs * (int64_t)chunks_per_job;
   const int64_t nwarps = (int64_t)gridDim.x * TCfg<MT>::WARPS;
   for (int64_t item = (int64_t)blockIdx.x * TCfg<MT>::WARPS + wib; item < items; item += nwarps) {
@@ -365,7 +387,7 @@ __global__ void __launch_bounds__(TCfg<MT>::WARPS * 32)
     const int m = jobs.m[job];
     const int T = trials > 0 ? trials : m * m;
     const int t = chunk * 32 + lane;
-    double lmax = -INFINITY, lsum = 0.0;
+    Pow2Sum acc;
     if (m >= 1 && m <= MT && t < T) {
       CsrView v = csr_view(arena, jobs.off[job], m, jobs.nnz[job]);
       const uint64_t tkey = seed ^ ((uint64_t)job * K_JOB) ^ ((uint64_t)t * K_TRIAL);
@@ -381,7 +403,7 @@ __global__ void __launch_bounds__(TCfg<MT>::WARPS * 32)
           const int j = v.col[q];
           const uint64_t h = splitmix64_mix(tkey ^ ((uint64_t)(i * m + j) * K_ENTRY));
           const int w = (int)(((h >> 32) * 3ull) >> 32);
-          WT(i, j) = make_float2(RE[w], IM[w]);
+          WT(i, j) = cube_root((uint32_t)w);
         }
       float pm = 1.0f;
       int pe = 0;
@@ -437,23 +459,177 @@ __global__ void __launch_bounds__(TCfg<MT>::WARPS * 32)
           }
         }
       }
-      if (!singular) {
-        lmax = log((double)pm) + (double)pe * 0.69314718055994530942;
-        lsum = 1.0;
-      }
+      if (!singular) acc.add(pm, pe);
     }
 #undef WT
-    // warp log-sum-exp of the 32 trials
+    // sum of the warp's 32 trials
+    acc.warp_merge(1);
+    double lmax, lsum;
+    acc.lse(lmax, lsum);
+    if (lane == 0) part[item] = make_double2(lmax, lsum);
+  }
+}
+
+// Register form for jobs of order m <= MT, several rows per lane: a group
+// of LPG = MT / RPL lanes runs one trial, lane i holding rows i*RPL ..
+// i*RPL+RPL-1 of the trial matrix in registers, so a warp runs 32 / LPG
+// trials side by side with no shared memory.  Rows never move: the pivot of
+// step k is the row not yet pivoted with the largest |z|^2, ties to the row
+// at the lowest position (positions follow the row swaps of partial
+// pivoting, so the pivot sequence is that of the swapping elimination), and
+// the pivot row is broadcast column by column with a shuffle from the lane
+// holding it.  |det W|^2 is the product of the pivots' |z|^2.  A warp takes
+// 32 trials of one job (32 / LPG rounds) and writes their log-sum-exp to
+// part[], which k_kklll_combine merges per job.
+template <int MT, int RPL>
+__global__ void __launch_bounds__(256, 2)
+    k_kklll_lanes(JobArrays jobs, int64_t njobs, const uint64_t* __restrict__ arena, int trials, uint64_t seed,
+                  int chunks_per_job, double2* __restrict__ part) {
+  constexpr int LPG = MT / RPL;   // lanes per trial
+  constexpr int TPR = 32 / LPG;   // trials per warp and round
+  static_assert(MT % RPL == 0 && 32 % LPG == 0, "rows must tile the lanes");
+  const int lane = threadIdx.x & 31;
+  const int li = lane % LPG;
+  const int grp = lane / LPG;
+  const int64_t items = njobs * (int64_t)chunks_per_job;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < items; item += nwarps) {
+    const int64_t job = item / chunks_per_job;
+    const int chunk = (int)(item % chunks_per_job);
+    const int m = jobs.m[job];
+    const int T = trials > 0 ? trials : m * m;
+    Pow2Sum acc;
+    if (m >= 1 && m <= MT) {
+      const CsrView v = csr_view(arena, jobs.off[job], m, jobs.nnz[job]);
+      uint32_t pat[RPL];
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      const double om = __shfl_xor_sync(0xffffffffu, lmax, d);
-      const double os = __shfl_xor_sync(0xffffffffu, lsum, d);
-      const double mx = om > lmax ? om : lmax;
-      if (mx > -INFINITY) {
-        lsum = (lmax > -INFINITY ? lsum * exp(lmax - mx) : 0.0) + (om > -INFINITY ? os * exp(om - mx) : 0.0);
-        lmax = mx;
+      for (int s = 0; s < RPL; ++s) {
+        const int r = li * RPL + s;
+        uint32_t b = 0;
+        if (r < m)
+          for (int q = v.rowptr[r]; q < v.rowptr[r + 1]; ++q) b |= 1u << v.col[q];
+        pat[s] = b;
+      }
+      const uint64_t jkey = seed ^ ((uint64_t)job * K_JOB);
+      for (int round = 0; round < 32 / TPR; ++round) {
+        const int t0 = chunk * 32 + round * TPR;
+        if (t0 >= T) break;
+        const int t = t0 + grp;
+        const bool live = t < T;
+        const uint64_t tkey = jkey ^ ((uint64_t)t * K_TRIAL);
+        // cube-root indices of the row's nonzeros, two bits per column
+        uint32_t code[RPL];
+#pragma unroll
+        for (int s = 0; s < RPL; ++s) {
+          const int r = li * RPL + s;
+          uint32_t cd = 0, b = live ? pat[s] : 0u;
+          while (b) {
+            const int c = __ffs(b) - 1;
+            b &= b - 1;
+            const uint64_t h = splitmix64_mix(tkey ^ ((uint64_t)(r * m + c) * K_ENTRY));
+            cd |= (uint32_t)(((h >> 32) * 3ull) >> 32) << (2 * c);
+          }
+          code[s] = cd;
+        }
+        float2 W[RPL][MT];
+#pragma unroll
+        for (int s = 0; s < RPL; ++s) {
+          const uint32_t on = live ? pat[s] : 0u;
+#pragma unroll
+          for (int c = 0; c < MT; ++c) {
+            W[s][c] = ((on >> c) & 1u) ? cube_root((code[s] >> (2 * c)) & 3u) : make_float2(0.0f, 0.0f);
+          }
+        }
+        int pos[RPL];
+        bool done[RPL];
+#pragma unroll
+        for (int s = 0; s < RPL; ++s) {
+          pos[s] = li * RPL + s;
+          done[s] = pos[s] >= m;
+        }
+        float pm = 1.0f;
+        int pe = 0;
+        bool singular = !live;
+#pragma unroll
+        for (int k = 0; k < MT; ++k) {
+          if (k < m) {
+            // key: |z|^2 with its low 8 bits replaced by (15 - position,
+            // row), so magnitudes within 2^-15 of each other tie and go to
+            // the lower position; a non-negative float orders like its bits
+            uint32_t key = 0u;
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) {
+              const float mg = W[s][k].x * W[s][k].x + W[s][k].y * W[s][k].y;
+              const uint32_t ks = done[s] ? 0u
+                                          : (__float_as_uint(mg) & 0xffffff00u) |
+                                                ((uint32_t)(15 - pos[s]) << 4) | (uint32_t)(li * RPL + s);
+              key = ks > key ? ks : key;
+            }
+#pragma unroll
+            for (int d = LPG / 2; d > 0; d >>= 1) {
+              const uint32_t o = __shfl_xor_sync(0xffffffffu, key, d, LPG);
+              key = o > key ? o : key;
+            }
+            const int pr = (int)(key & 0xf);
+            const int ppos = 15 - (int)((key >> 4) & 0xf);
+            const int plane = pr / RPL, pslot = pr % RPL;
+            // the row now at position k moves to the pivot's old position
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) {
+              if (pos[s] == k) pos[s] = ppos;
+              if (li * RPL + s == pr) {
+                pos[s] = k;
+                done[s] = true;
+              }
+            }
+            float2 sel = W[0][k];
+#pragma unroll
+            for (int s = 1; s < RPL; ++s)
+              if (pslot == s) sel = W[s][k];
+            const float2 piv = make_float2(__shfl_sync(0xffffffffu, sel.x, plane, LPG),
+                                           __shfl_sync(0xffffffffu, sel.y, plane, LPG));
+            const float pmag = piv.x * piv.x + piv.y * piv.y;
+            if (!(pmag > 0.0f)) singular = true;
+            if (!singular) {
+              int ex;
+              pm = frexpf(pm * pmag, &ex);
+              pe += ex;
+            }
+            const float inv = singular ? 0.0f : 1.0f / pmag;
+            float2 f[RPL];
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) {
+              const float2 a = W[s][k];
+              f[s] = done[s] ? make_float2(0.0f, 0.0f)
+                             : make_float2((a.x * piv.x + a.y * piv.y) * inv, (a.y * piv.x - a.x * piv.y) * inv);
+            }
+#pragma unroll
+            // (constant bounds, so the loop unrolls with the step loop and
+            // every register index stays a constant)
+            for (int c = 1; c < MT; ++c) {
+              if (c > k) {  // columns >= m are zero in every row
+                float2 ps = W[0][c];
+#pragma unroll
+                for (int s = 1; s < RPL; ++s)
+                  if (pslot == s) ps = W[s][c];
+                const float2 pc = make_float2(__shfl_sync(0xffffffffu, ps.x, plane, LPG),
+                                              __shfl_sync(0xffffffffu, ps.y, plane, LPG));
+#pragma unroll
+                for (int s = 0; s < RPL; ++s) {
+                  W[s][c].x -= f[s].x * pc.x - f[s].y * pc.y;
+                  W[s][c].y -= f[s].x * pc.y + f[s].y * pc.x;
+                }
+              }
+            }
+          }
+        }
+        if (!singular) acc.add(pm, pe);
       }
     }
+    // the groups' sums (every lane of a group holds its group's), merged
+    acc.warp_merge(LPG);
+    double lmax, lsum;
+    acc.lse(lmax, lsum);
     if (lane == 0) part[item] = make_double2(lmax, lsum);
   }
 }
@@ -498,6 +674,17 @@ cudaError_t launch_thread(const JobArrays& jobs, int64_t njobs, const uint64_t* 
   return cudaGetLastError();
 }
 
+template <int MT, int RPL>
+cudaError_t launch_lanes(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, int trials, uint64_t seed,
+                         float* log_ap, double2* part, int chunks, cudaStream_t s) {
+  const int64_t items = njobs * chunks;
+  int64_t blocks = (items + 7) / 8;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_kklll_lanes<MT, RPL><<<(unsigned)blocks, 256, 0, s>>>(jobs, njobs, arena, trials, seed, chunks, part);
+  k_kklll_combine<<<(unsigned)((njobs + 255) / 256), 256, 0, s>>>(jobs, njobs, trials, chunks, part, log_ap);
+  return cudaGetLastError();
+}
+
 template <int RL>
 cudaError_t launch_rows(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, int trials, uint64_t seed,
                         float* log_ap, cudaStream_t s) {
@@ -526,7 +713,7 @@ cudaError_t launch_kklll(const JobArrays& jobs, int64_t njobs, const uint64_t* a
   const int chunks = kklll_chunks(max_order, trials);
   if (max_order <= 8) return launch_thread<8>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
   if (max_order <= 12) return launch_thread<12>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
-  if (max_order <= 16) return launch_thread<16>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
+  if (max_order <= 16) return launch_lanes<16, 2>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
   if (max_order <= 32) return launch_rows<32>(jobs, njobs, arena, trials, seed, log_ap, s);
   if (max_order <= 64) return launch_k<64>(jobs, njobs, arena, trials, seed, log_ap, s);
   return launch_k<128>(jobs, njobs, arena, trials, seed, log_ap, s);

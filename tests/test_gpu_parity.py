@@ -313,12 +313,13 @@ def test_batch_of_matrices_one_launch():
 
 
 # ---------------------------------------------------------------- estimator (K4) and order
-@pytest.mark.parametrize("n,d,trials", [(30, 14, 0), (20, 12, 0), (40, 16, 0), (50, 8, 300), (80, 0, 12),
-                                         (96, 10, 6)])
+@pytest.mark.parametrize("n,d,trials", [(30, 14, 0), (20, 12, 0), (26, 14, 0), (28, 17, 40), (40, 16, 0),
+                                         (50, 8, 300), (80, 0, 12), (96, 10, 6)])
 def test_kklll_matches_oracle(n, d, trials):
-    """Register kernels for job orders <= 8, 16, 32 and the shared-memory
-    kernels above 32 (two pattern words per row above 64); relative 1e-5 on
-    the mean (FP32 against fp64)."""
+    """Several-rows-per-lane register kernels for job orders <= 8, 12, 16
+    (order 11 with 40 trials: a partial last chunk of 32), one row per lane
+    up to 32, the shared-memory kernels above 32 (two pattern words per row
+    above 64); relative 1e-5 on the mean (FP32 against fp64)."""
     a = W.regular3(n, 4)
     with pk.Plan([a], split_depth=d, leaf_size=4, kklll_trials=trials, seed=1234) as plan:
         plan.expand()
