@@ -221,6 +221,151 @@ __global__ void __launch_bounds__(KCfg<TILE>::WARPS * 32)
   }
 }
 
+// Tile form for jobs of order 33 <= m <= MT (MT <= 64): a warp runs one
+// trial at a time, the m x m trial matrix in shared memory with row stride
+// S (S = 8 mod 16, so four consecutive rows by eight consecutive columns hit
+// 32 distinct bank pairs).  Step k swaps the pivot row into row k (partial
+// pivoting: largest |z|^2 in column k among rows >= k, the lowest row on
+// ties, ties meaning within 2^-17 relative since the key keeps 63 - row in
+// the magnitude's low 6 bits) and updates the trailing block, spread over
+// the lanes as a 4 x 8 grid: lane (ly, lx) takes the rows r = ly (mod 4)
+// and columns c = lx (mod 8) above k.  The lanes whose first column is k+1
+// form the next step's pivot keys while they update it, so a step needs
+// one warp reduction.  A warp takes chunk_trials trials of one job and
+// writes their sum to part[]; k_kklll_combine merges a job's parts.
+template <int MT>
+struct TileCfg {
+  static constexpr int JMAX = MT / 8;  // columns of a row per lane
+  static constexpr int LIST = 512;     // nonzeros held as (row, column) pairs
+  // one warp per block: the blocks per SM follow the launch's shared memory
+  static constexpr int WARPS = 1;
+};
+
+__host__ __device__ __forceinline__ int tile_stride(int mmax) { return (mmax - 8 + 15) / 16 * 16 + 8; }
+
+__device__ __forceinline__ uint32_t tile_key(float2 z, int r) {
+  return (__float_as_uint(z.x * z.x + z.y * z.y) & ~63u) | (uint32_t)(63 - r);
+}
+
+template <int MT>
+__global__ void __launch_bounds__(TileCfg<MT>::WARPS * 32, 16)
+    k_kklll_tile(JobArrays jobs, int64_t njobs, const uint64_t* __restrict__ arena, int trials, uint64_t seed,
+                 int chunks_per_job, int chunk_trials, int S, int wrows, int warp_bytes, double2* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int JMAX = TileCfg<MT>::JMAX;
+  constexpr int LIST = TileCfg<MT>::LIST;
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int ly = lane >> 3, lx = lane & 7;
+  unsigned char* base = smem_raw + (size_t)wib * warp_bytes;
+  float2* Wm = reinterpret_cast<float2*>(base);
+  uint16_t* nzl = reinterpret_cast<uint16_t*>(base + (size_t)wrows * S * sizeof(float2));
+  const int64_t items = njobs * (int64_t)chunks_per_job;
+  const int64_t nwarps = (int64_t)gridDim.x * TileCfg<MT>::WARPS;
+  for (int64_t item = (int64_t)blockIdx.x * TileCfg<MT>::WARPS + wib; item < items; item += nwarps) {
+    const int64_t job = item / chunks_per_job;
+    const int chunk = (int)(item % chunks_per_job);
+    const int m = jobs.m[job];
+    const int T = trials > 0 ? trials : m * m;
+    const int t_begin = chunk * chunk_trials;
+    const int t_end = min(T, t_begin + chunk_trials);
+    Pow2Sum acc;
+    if (m >= 1 && m <= wrows && t_begin < t_end) {
+      const CsrView v = csr_view(arena, jobs.off[job], m, jobs.nnz[job]);
+      const int nnz = jobs.nnz[job];
+      const bool listed = nnz <= LIST;
+      __syncwarp();
+      if (listed)
+        for (int r = lane; r < m; r += 32)
+          for (int q = v.rowptr[r]; q < v.rowptr[r + 1]; ++q) nzl[q] = (uint16_t)((r << 8) | v.col[q]);
+      __syncwarp();
+      const uint64_t jkey = seed ^ ((uint64_t)job * K_JOB);
+      for (int t = t_begin; t < t_end; ++t) {
+        const uint64_t tkey = jkey ^ ((uint64_t)t * K_TRIAL);
+        float4* W4 = reinterpret_cast<float4*>(Wm);
+        for (int e = lane; e < m * S / 2; e += 32) W4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncwarp();
+        if (listed) {
+          for (int q = lane; q < nnz; q += 32) {
+            const int rc = nzl[q], r = rc >> 8, c = rc & 255;
+            const uint64_t h = splitmix64_mix(tkey ^ ((uint64_t)(r * m + c) * K_ENTRY));
+            Wm[r * S + c] = cube_root((uint32_t)(((h >> 32) * 3ull) >> 32));
+          }
+        } else {
+          for (int r = 0; r < m; ++r)
+            for (int q = v.rowptr[r] + lane; q < v.rowptr[r + 1]; q += 32) {
+              const int c = v.col[q];
+              const uint64_t h = splitmix64_mix(tkey ^ ((uint64_t)(r * m + c) * K_ENTRY));
+              Wm[r * S + c] = cube_root((uint32_t)(((h >> 32) * 3ull) >> 32));
+            }
+        }
+        __syncwarp();
+        uint32_t key = 0;
+        for (int r = lane; r < m; r += 32) key = max(key, tile_key(Wm[r * S], r));
+        float pm = 1.0f;  // |det|^2 = pm * 2^pe
+        int pe = 0;
+        bool singular = false;
+        for (int k = 0; k < m; ++k) {
+          key = __reduce_max_sync(0xffffffffu, key);
+          const int p = 63 - (int)(key & 63u);
+          if (p != k) {
+            for (int c = k + lane; c < m; c += 32) {
+              const float2 a = Wm[k * S + c];
+              Wm[k * S + c] = Wm[p * S + c];
+              Wm[p * S + c] = a;
+            }
+            __syncwarp();
+          }
+          const float2 piv = Wm[k * S + k];
+          const float mag = piv.x * piv.x + piv.y * piv.y;
+          if (!(mag > 0.0f)) {
+            singular = true;
+            break;
+          }
+          int ex;
+          pm = frexpf(pm * mag, &ex);
+          pe += ex;
+          const float inv = 1.0f / mag;
+          const float2 ipiv = make_float2(piv.x * inv, -piv.y * inv);  // 1 / piv
+          const int r0 = k + 1 + ((ly - (k + 1)) & 3);
+          const int c0 = k + 1 + ((lx - (k + 1)) & 7);
+          float2 pk[JMAX];
+#pragma unroll
+          for (int j = 0; j < JMAX; ++j) {
+            const int c = c0 + 8 * j;
+            pk[j] = c < m ? Wm[k * S + c] : make_float2(0.f, 0.f);
+          }
+          const bool keycol = c0 == k + 1;
+          key = 0;
+          for (int r = r0; r < m; r += 4) {
+            const float2 a = Wm[r * S + k];
+            const float2 f = make_float2(a.x * ipiv.x - a.y * ipiv.y, a.x * ipiv.y + a.y * ipiv.x);
+#pragma unroll
+            for (int j = 0; j < JMAX; ++j) {
+              const int c = c0 + 8 * j;
+              if (c < m) {
+                float2 z = Wm[r * S + c];
+                z.x -= f.x * pk[j].x - f.y * pk[j].y;
+                z.y -= f.x * pk[j].y + f.y * pk[j].x;
+                Wm[r * S + c] = z;
+                if (j == 0 && keycol) key = max(key, tile_key(z, r));
+              }
+            }
+          }
+          __syncwarp();
+        }
+        __syncwarp();
+        if (!singular) acc.add(pm, pe);
+      }
+    }
+    if (lane == 0) {
+      double lmax, lsum;
+      acc.lse(lmax, lsum);
+      part[item] = make_double2(lmax, lsum);
+    }
+  }
+}
+
 template <int TILE>
 cudaError_t launch_k(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, int trials, uint64_t seed,
                      float* log_ap, cudaStream_t s) {
@@ -685,6 +830,33 @@ cudaError_t launch_lanes(const JobArrays& jobs, int64_t njobs, const uint64_t* a
   return cudaGetLastError();
 }
 
+static size_t tile_warp_bytes(int mmax) {
+  return ((size_t)mmax * tile_stride(mmax) * sizeof(float2) + 2 * TileCfg<64>::LIST + 15) / 16 * 16;
+}
+
+template <int MT>
+cudaError_t launch_tile(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, int trials, uint64_t seed,
+                        float* log_ap, double2* part, int chunks, int chunk_trials, int max_order, cudaStream_t s) {
+  typedef TileCfg<MT> C;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_kklll_tile<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(C::WARPS * tile_warp_bytes(MT)));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int wb = (int)tile_warp_bytes(max_order);
+  const int smem = C::WARPS * wb;
+  const int64_t items = njobs * chunks;
+  int64_t blocks = (items + C::WARPS - 1) / C::WARPS;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_kklll_tile<MT><<<(unsigned)blocks, C::WARPS * 32, smem, s>>>(jobs, njobs, arena, trials, seed, chunks,
+                                                                  chunk_trials, tile_stride(max_order), max_order,
+                                                                  wb, part);
+  k_kklll_combine<<<(unsigned)((njobs + 255) / 256), 256, 0, s>>>(jobs, njobs, trials, chunks, part, log_ap);
+  return cudaGetLastError();
+}
+
 template <int RL>
 cudaError_t launch_rows(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, int trials, uint64_t seed,
                         float* log_ap, cudaStream_t s) {
@@ -696,25 +868,43 @@ cudaError_t launch_rows(const JobArrays& jobs, int64_t njobs, const uint64_t* ar
 
 }  // namespace
 
-static int kklll_chunks(int max_order, int trials) {
-  const int T = trials > 0 ? trials : max_order * max_order;
-  return (T + 31) / 32;
+// Trials per part: 32 (one per lane, or per lane group, of a warp) up to
+// order 16; for the tile form 32 doubled until the parts number at most
+// 2^23 (128 MB).
+static int kklll_chunk_trials(int64_t njobs, int max_order, int trials) {
+  if (max_order <= 16 || max_order > 64) return 32;
+  const int64_t T = trials > 0 ? trials : (int64_t)max_order * max_order;
+  int ct = 32;
+  while ((T + ct - 1) / ct * (njobs > 0 ? njobs : 1) > (1ll << 23) && ct < (1 << 20)) ct *= 2;
+  return ct;
 }
 
+static int kklll_chunks(int64_t njobs, int max_order, int trials) {
+  const int64_t T = trials > 0 ? trials : (int64_t)max_order * max_order;
+  const int ct = kklll_chunk_trials(njobs, max_order, trials);
+  return (int)((T + ct - 1) / ct);
+}
+
+static bool kklll_uses_parts(int max_order) { return max_order <= 16 || (max_order > 32 && max_order <= 64); }
+
 size_t kklll_scratch_bytes(int64_t njobs, int max_order, int trials) {
-  if (max_order > 16) return 16;
-  return sizeof(double2) * (size_t)(njobs > 0 ? njobs : 1) * (size_t)kklll_chunks(max_order, trials);
+  if (!kklll_uses_parts(max_order)) return 16;
+  return sizeof(double2) * (size_t)(njobs > 0 ? njobs : 1) * (size_t)kklll_chunks(njobs, max_order, trials);
 }
 
 cudaError_t launch_kklll(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, int trials, uint64_t seed,
                          float* log_ap, int max_order, void* scratch, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
   double2* part = reinterpret_cast<double2*>(scratch);
-  const int chunks = kklll_chunks(max_order, trials);
+  const int chunks = kklll_chunks(njobs, max_order, trials);
   if (max_order <= 8) return launch_thread<8>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
   if (max_order <= 12) return launch_thread<12>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
   if (max_order <= 16) return launch_lanes<16, 2>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
   if (max_order <= 32) return launch_rows<32>(jobs, njobs, arena, trials, seed, log_ap, s);
-  if (max_order <= 64) return launch_k<64>(jobs, njobs, arena, trials, seed, log_ap, s);
+  const int ct = kklll_chunk_trials(njobs, max_order, trials);
+  if (max_order <= 40) return launch_tile<40>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, ct, max_order, s);
+  if (max_order <= 48) return launch_tile<48>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, ct, max_order, s);
+  if (max_order <= 56) return launch_tile<56>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, ct, max_order, s);
+  if (max_order <= 64) return launch_tile<64>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, ct, max_order, s);
   return launch_k<128>(jobs, njobs, arena, trials, seed, log_ap, s);
 }

@@ -314,12 +314,14 @@ def test_batch_of_matrices_one_launch():
 
 # ---------------------------------------------------------------- estimator (K4) and order
 @pytest.mark.parametrize("n,d,trials", [(30, 14, 0), (20, 12, 0), (26, 14, 0), (28, 17, 40), (40, 16, 0),
-                                         (50, 8, 300), (80, 0, 12), (96, 10, 6)])
+                                         (80, 40, 60), (50, 8, 300), (70, 6, 40), (80, 0, 12), (96, 10, 6)])
 def test_kklll_matches_oracle(n, d, trials):
-    """Several-rows-per-lane register kernels for job orders <= 8, 12, 16
-    (order 11 with 40 trials: a partial last chunk of 32), one row per lane
-    up to 32, the shared-memory kernels above 32 (two pattern words per row
-    above 64); relative 1e-5 on the mean (FP32 against fp64)."""
+    """Thread kernels for job orders <= 8 and 12 (order 11 with 40 trials: a
+    partial last chunk of 32), the several-rows-per-lane register kernel up
+    to 16, one row per lane up to 32, the tiled kernels for 40, 48 and 64
+    (parts of 32 trials, the last one partial), the shared-memory kernel
+    above 64 (two pattern words per row); relative 1e-5 on the mean (FP32
+    against fp64)."""
     a = W.regular3(n, 4)
     with pk.Plan([a], split_depth=d, leaf_size=4, kklll_trials=trials, seed=1234) as plan:
         plan.expand()
@@ -329,6 +331,19 @@ def test_kklll_matches_oracle(n, d, trials):
     for j in rng.choice(len(jobs), size=min(8, len(jobs)), replace=False):
         want = oracle.kklll_log_ap(jobs[j][1], seed=1234, job=int(j), trials=trials or None)
         assert abs(float(la[j]) - want) < 1e-5, (j, la[j], want)
+
+
+def test_kklll_dense_job_matches_oracle():
+    """A job with more nonzeros than the tiled kernel's nonzero list (700 >
+    512) fills its trial matrices row by row from the CSR block."""
+    a = W.random01(36, 700, 11)
+    with pk.Plan([a], split_depth=0, leaf_size=4, kklll_trials=40, seed=77) as plan:
+        plan.expand()
+        la = plan.estimate()
+        jobs = plan.jobs_export()
+    assert len(jobs) == 1 and int(np.count_nonzero(jobs[0][1])) == 700
+    want = oracle.kklll_log_ap(jobs[0][1], seed=77, job=0, trials=40)
+    assert abs(float(la[0]) - want) < 1e-5, (la[0], want)
 
 
 def test_lpt_order_is_stable_sort_of_estimate():
