@@ -2,11 +2,14 @@
 // (Section 3's B).  Each nonzero becomes a cube root of unity drawn from a
 // counter-based SplitMix64 stream; |det W|^2 is an unbiased estimate of
 // per(B) (the paper's Theorem), and the job's approximate permanent is the
-// mean over T trials.  One warp per job; the trial matrix sits in shared
-// memory as complex FP32 and is reduced by Gaussian elimination with partial
-// pivoting on |z| (lowest row on ties).  |det|^2 is the product of the
-// pivots' squared moduli, kept as an FP32 mantissa with an integer exponent;
-// the mean over trials is accumulated in FP64 as a log-sum-exp.
+// mean over T trials.  Each trial matrix is complex FP32, reduced by
+// Gaussian elimination with partial pivoting on |z| (lowest row on ties);
+// |det|^2 is the product of the pivots' squared moduli, kept as an FP32
+// mantissa with an integer exponent, and trials are summed in FP64 scaled
+// by powers of two.  The form follows the launch's largest job order:
+// one trial per thread in shared memory (<= 12), per group of lanes in
+// registers (<= 16), per warp in shared memory (<= 64, the trials of a job
+// split into parts merged by k_kklll_combine), one job per warp above 64.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -61,6 +64,14 @@ struct Pow2Sum {
     }
   }
 };
+
+// z -= f * p in complex arithmetic, as four fused multiply-adds
+__device__ __forceinline__ void cfms(float2& z, float2 f, float2 p) {
+  z.x = fmaf(-f.x, p.x, z.x);
+  z.x = fmaf(f.y, p.y, z.x);
+  z.y = fmaf(-f.x, p.y, z.y);
+  z.y = fmaf(-f.y, p.x, z.y);
+}
 
 // e^(2 pi i w / 3), w in {0, 1, 2}
 __device__ __forceinline__ float2 cube_root(uint32_t w) {
@@ -202,8 +213,7 @@ __global__ void __launch_bounds__(KCfg<TILE>::WARPS * 32)
             const int c = lane + 32 * u;
             if (c > k && c < m) {
               float2 z = Wm[r * S + c];
-              z.x -= f.x * rowk[u].x - f.y * rowk[u].y;
-              z.y -= f.x * rowk[u].y + f.y * rowk[u].x;
+              cfms(z, f, rowk[u]);
               Wm[r * S + c] = z;
             }
           }
@@ -221,7 +231,7 @@ __global__ void __launch_bounds__(KCfg<TILE>::WARPS * 32)
   }
 }
 
-// Tile form for jobs of order 33 <= m <= MT (MT <= 64): a warp runs one
+// Tile form for jobs of order 17 <= m <= MT (MT <= 64): a warp runs one
 // trial at a time, the m x m trial matrix in shared memory with row stride
 // S (S = 8 mod 16, so four consecutive rows by eight consecutive columns hit
 // 32 distinct bank pairs).  Step k swaps the pivot row into row k (partial
@@ -336,6 +346,7 @@ __global__ void __launch_bounds__(TileCfg<MT>::WARPS * 32, 16)
             pk[j] = c < m ? Wm[k * S + c] : make_float2(0.f, 0.f);
           }
           const bool keycol = c0 == k + 1;
+          const int jw = (m - k - 1 + 7) >> 3;  // columns per lane and row, at most (warp-uniform)
           key = 0;
           for (int r = r0; r < m; r += 4) {
             const float2 a = Wm[r * S + k];
@@ -343,10 +354,9 @@ __global__ void __launch_bounds__(TileCfg<MT>::WARPS * 32, 16)
 #pragma unroll
             for (int j = 0; j < JMAX; ++j) {
               const int c = c0 + 8 * j;
-              if (c < m) {
+              if (j < jw && c < m) {
                 float2 z = Wm[r * S + c];
-                z.x -= f.x * pk[j].x - f.y * pk[j].y;
-                z.y -= f.x * pk[j].y + f.y * pk[j].x;
+                cfms(z, f, pk[j]);
                 Wm[r * S + c] = z;
                 if (j == 0 && keycol) key = max(key, tile_key(z, r));
               }
@@ -380,125 +390,6 @@ cudaError_t launch_k(const JobArrays& jobs, int64_t njobs, const uint64_t* arena
   if (blocks > 152 * 32) blocks = 152 * 32;
   k_kklll<TILE><<<(unsigned)blocks, C::WARPS * 32, C::SMEM, s>>>(jobs, njobs, arena, trials, seed, log_ap);
   return cudaGetLastError();
-}
-
-// Register form for jobs of order m <= RL: a group of RL lanes runs one
-// trial at a time, lane r holding row r of the trial matrix in registers;
-// a warp runs 32 / RL trials side by side.  Rows never move: the pivot of
-// step k is chosen among the lanes not yet pivoted by largest |z|^2, ties to
-// the row currently at the lowest position (positions follow the row swaps
-// of partial pivoting), and its row is broadcast through shared memory.  The
-// step loop is unrolled to RL so every register index is a constant.
-template <int RL>
-__global__ void __launch_bounds__(128)
-    k_kklll_rows(JobArrays jobs, int64_t njobs, const uint64_t* __restrict__ arena, int trials, uint64_t seed,
-                 float* __restrict__ log_ap) {
-  constexpr int TPW = 32 / RL;  // trials per warp
-  __shared__ float2 prow_s[4][TPW][RL];
-  __shared__ uint32_t pat_s[4][32];
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int grp = lane / RL;
-  const int r = lane % RL;
-  const unsigned gmask = (RL == 32) ? 0xffffffffu : (((1u << RL) - 1u) << (grp * RL));
-  float2* prow = prow_s[wib][grp];
-  uint32_t* pat = pat_s[wib];
-  const int64_t nwarps = (int64_t)gridDim.x * 4;
-  for (int64_t job = (int64_t)blockIdx.x * 4 + wib; job < njobs; job += nwarps) {
-    __syncwarp();
-    const int m = jobs.m[job];
-    if (m <= 0) {
-      if (lane == 0) log_ap[job] = 0.0f;
-      continue;
-    }
-    CsrView v = csr_view(arena, jobs.off[job], m, jobs.nnz[job]);
-    if (lane < m) {
-      uint32_t b = 0;
-      for (int q = v.rowptr[lane]; q < v.rowptr[lane + 1]; ++q) b |= 1u << v.col[q];
-      pat[lane] = b;
-    }
-    __syncwarp();
-    const int T = trials > 0 ? trials : m * m;
-    const uint64_t jkey = seed ^ ((uint64_t)job * K_JOB);
-    const uint32_t myrow = r < m ? pat[r] : 0u;
-    Pow2Sum acc;  // this group's trials (lane r == 0)
-    const int rounds = (T + TPW - 1) / TPW;
-    for (int it = 0; it < rounds; ++it) {
-      const int t = it * TPW + grp;
-      const bool live = t < T;
-      const uint64_t tkey = jkey ^ ((uint64_t)t * K_TRIAL);
-      float2 row[RL];
-#pragma unroll
-      for (int c = 0; c < RL; ++c) {
-        float2 z = make_float2(0.f, 0.f);
-        if (live && c < m && ((myrow >> c) & 1)) {
-          const uint64_t h = splitmix64_mix(tkey ^ ((uint64_t)(r * m + c) * K_ENTRY));
-          const int w = (int)(((h >> 32) * 3ull) >> 32);
-          z = cube_root((uint32_t)w);
-        }
-        row[c] = z;
-      }
-      bool done = r >= m;
-      int pos = r;
-      float pm = 1.0f;
-      int pe = 0;
-      bool singular = !live;
-#pragma unroll
-      for (int k = 0; k < RL; ++k) {
-        if (k < m && !singular) {
-          const float mag = done ? -1.0f : row[k].x * row[k].x + row[k].y * row[k].y;
-          unsigned long long key = done ? 0ull
-                                        : ((unsigned long long)__float_as_uint(mag) << 32) |
-                                              (unsigned long long)(0xffffu - (unsigned)pos) << 8 | (unsigned)r;
-#pragma unroll
-          for (int d = RL / 2; d > 0; d >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(gmask, key, d, RL);
-            key = o > key ? o : key;
-          }
-          const float pmag = __uint_as_float((uint32_t)(key >> 32));
-          const int plane = (int)(key & 0xff);
-          if (!(pmag > 0.0f)) {
-            singular = true;
-          } else {
-            const int ppos = __shfl_sync(gmask, pos, plane, RL);
-            if (r == plane) {
-#pragma unroll
-              for (int c = k; c < RL; ++c) prow[c] = row[c];
-            }
-            // the row now at position k moves to the pivot's old position
-            if (pos == k) pos = ppos;
-            if (r == plane) {
-              pos = k;
-              done = true;
-            }
-            __syncwarp(gmask);
-            int ex;
-            pm = frexpf(pm * pmag, &ex);
-            pe += ex;
-            if (!done) {
-              const float2 piv = prow[k];
-              const float inv = 1.0f / pmag;
-              const float2 a = row[k];
-              const float2 f = make_float2((a.x * piv.x + a.y * piv.y) * inv, (a.y * piv.x - a.x * piv.y) * inv);
-#pragma unroll
-              for (int c = k + 1; c < RL; ++c) {
-                const float2 pc = prow[c];
-                row[c].x -= f.x * pc.x - f.y * pc.y;
-                row[c].y -= f.x * pc.y + f.y * pc.x;
-              }
-            }
-            __syncwarp(gmask);
-          }
-        }
-      }
-      if (r == 0 && !singular) acc.add(pm, pe);
-    }
-    // merge the groups' sums (held by their lanes r == 0)
-    acc.warp_merge(RL);
-    double lmax, lsum;
-    acc.lse(lmax, lsum);
-    if (lane == 0) log_ap[job] = lmax == -INFINITY ? -INFINITY : (float)(lmax + log(lsum / (double)T));
-  }
 }
 
 // Thread form for jobs of order m <= MT: every thread runs one whole trial,
@@ -596,8 +487,7 @@ __global__ void __launch_bounds__(TCfg<MT>::WARPS * 32)
 #pragma unroll
               for (int c = k + 1; c < MT; ++c) {
                 float2 z = WT(r, c);
-                z.x -= f.x * pc[c].x - f.y * pc[c].y;
-                z.y -= f.x * pc[c].y + f.y * pc[c].x;
+                cfms(z, f, pc[c]);
                 WT(r, c) = z;
               }
             }
@@ -761,8 +651,7 @@ __global__ void __launch_bounds__(256, 2)
                                               __shfl_sync(0xffffffffu, ps.y, plane, LPG));
 #pragma unroll
                 for (int s = 0; s < RPL; ++s) {
-                  W[s][c].x -= f[s].x * pc.x - f[s].y * pc.y;
-                  W[s][c].y -= f[s].x * pc.y + f[s].y * pc.x;
+                  cfms(W[s][c], f[s], pc);
                 }
               }
             }
@@ -857,14 +746,6 @@ cudaError_t launch_tile(const JobArrays& jobs, int64_t njobs, const uint64_t* ar
   return cudaGetLastError();
 }
 
-template <int RL>
-cudaError_t launch_rows(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, int trials, uint64_t seed,
-                        float* log_ap, cudaStream_t s) {
-  int64_t blocks = (njobs + 3) / 4;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  k_kklll_rows<RL><<<(unsigned)blocks, 128, 0, s>>>(jobs, njobs, arena, trials, seed, log_ap);
-  return cudaGetLastError();
-}
 
 }  // namespace
 
@@ -885,7 +766,7 @@ static int kklll_chunks(int64_t njobs, int max_order, int trials) {
   return (int)((T + ct - 1) / ct);
 }
 
-static bool kklll_uses_parts(int max_order) { return max_order <= 16 || (max_order > 32 && max_order <= 64); }
+static bool kklll_uses_parts(int max_order) { return max_order <= 64; }
 
 size_t kklll_scratch_bytes(int64_t njobs, int max_order, int trials) {
   if (!kklll_uses_parts(max_order)) return 16;
@@ -900,8 +781,9 @@ cudaError_t launch_kklll(const JobArrays& jobs, int64_t njobs, const uint64_t* a
   if (max_order <= 8) return launch_thread<8>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
   if (max_order <= 12) return launch_thread<12>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
   if (max_order <= 16) return launch_lanes<16, 2>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
-  if (max_order <= 32) return launch_rows<32>(jobs, njobs, arena, trials, seed, log_ap, s);
   const int ct = kklll_chunk_trials(njobs, max_order, trials);
+  if (max_order <= 24) return launch_tile<24>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, ct, max_order, s);
+  if (max_order <= 32) return launch_tile<32>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, ct, max_order, s);
   if (max_order <= 40) return launch_tile<40>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, ct, max_order, s);
   if (max_order <= 48) return launch_tile<48>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, ct, max_order, s);
   if (max_order <= 56) return launch_tile<56>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, ct, max_order, s);

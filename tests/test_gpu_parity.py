@@ -314,14 +314,14 @@ def test_batch_of_matrices_one_launch():
 
 # ---------------------------------------------------------------- estimator (K4) and order
 @pytest.mark.parametrize("n,d,trials", [(30, 14, 0), (20, 12, 0), (26, 14, 0), (28, 17, 40), (40, 16, 0),
-                                         (80, 40, 60), (50, 8, 300), (70, 6, 40), (80, 0, 12), (96, 10, 6)])
+                                         (46, 14, 100), (38, 20, 0), (80, 40, 60), (50, 8, 300), (70, 6, 40),
+                                         (80, 0, 12), (96, 10, 6)])
 def test_kklll_matches_oracle(n, d, trials):
     """Thread kernels for job orders <= 8 and 12 (order 11 with 40 trials: a
     partial last chunk of 32), the several-rows-per-lane register kernel up
-    to 16, one row per lane up to 32, the tiled kernels for 40, 48 and 64
-    (parts of 32 trials, the last one partial), the shared-memory kernel
-    above 64 (two pattern words per row); relative 1e-5 on the mean (FP32
-    against fp64)."""
+    to 16, the tiled kernels for 24, 32, 40, 48 and 64 (parts of 32 trials,
+    the last one partial), the shared-memory kernel above 64 (two pattern
+    words per row); relative 1e-5 on the mean (FP32 against fp64)."""
     a = W.regular3(n, 4)
     with pk.Plan([a], split_depth=d, leaf_size=4, kklll_trials=trials, seed=1234) as plan:
         plan.expand()
