@@ -576,6 +576,8 @@ def main():
                     help="skip the e2e, C60 and probe legs (profiler captures)")
     ap.add_argument("--c60-only", action="store_true",
                     help="run only the C60 whole-path leg and print its timings")
+    ap.add_argument("--ordering-only", action="store_true",
+                    help="run only the ordering leg (natural, KKLLL-LPT, learned on a coarse n = 80 split)")
     ap.add_argument("--c100", action="store_true",
                     help="per(A) of the paper's C100 adjacency (Appendix) against its printed total")
     ap.add_argument("--kendall", action="store_true",
@@ -592,6 +594,12 @@ def main():
         import paper_1112_6072_gb300 as pk
         torch.cuda.set_device(0)
         print(json.dumps({"c60": run_c60(pk, torch, args)}))
+        return
+    if args.ordering_only:
+        import torch
+        import paper_1112_6072_gb300 as pk
+        torch.cuda.set_device(0)
+        print(json.dumps({"ordering": run_ordering(pk, torch, args)}))
         return
     if args.kendall:
         import torch
