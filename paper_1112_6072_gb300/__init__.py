@@ -208,22 +208,55 @@ class Plan:
     Options mirror ``perm_opts`` in include/perm.h.
     """
 
-    def __init__(self, mats, split_depth=-1, leaf_size=0, order="lpt", kklll_trials=0, seed=0x5EED,
-                 workers_per_sm=0, chunk_log2=0, stream=None, torch_allocator=False, timeout_ns=0,
-                 model_uses_estimate=True, fused_levels=True, dense_split=False):
-        lib = _lib()
-        self._mats = [np.ascontiguousarray(np.asarray(m, dtype=np.int64)) for m in mats]
-        for m in self._mats:
+    def __init__(self, mats, **opts):
+        mats = [np.ascontiguousarray(np.asarray(m, dtype=np.int64)) for m in mats]
+        for m in mats:
             if m.ndim != 2 or m.shape[0] != m.shape[1]:
                 raise ValueError("square matrices expected")
         # the perm_matrix descriptors, built as one numpy record array (a
-        # ctypes loop costs about 4 us per matrix)
-        desc = np.zeros(len(self._mats), dtype=_MATRIX_DTYPE)
-        desc["n"] = [m.shape[0] for m in self._mats]
-        desc["a"] = [m.__array_interface__["data"][0] for m in self._mats]
+        # ctypes loop costs about 4 us per matrix, reading each array's
+        # address about 1 us: Plan.packed avoids both)
+        desc = np.zeros(len(mats), dtype=_MATRIX_DTYPE)
+        desc["n"] = [m.shape[0] for m in mats]
+        desc["a"] = [m.__array_interface__["data"][0] for m in mats]
         desc["ld"] = np.maximum(desc["n"], 1)
+        self._create(desc, mats, **opts)
+
+    @classmethod
+    def packed(cls, data, orders, **opts):
+        """A plan over matrices stored back to back in one int64 buffer:
+        matrix i, of order orders[i], is data[off_i : off_i + orders[i]**2]
+        in row-major order, off_i the sum of the earlier orders squared.
+        The descriptors come from one prefix sum.  Options as for Plan."""
+        data = np.asarray(data)
+        if data.dtype != np.int64 or not data.flags.c_contiguous:
+            data = np.ascontiguousarray(data, dtype=np.int64)
+        data = data.reshape(-1)
+        orders = np.asarray(orders, dtype=np.int64).reshape(-1)
+        if orders.size == 0 or (orders < 0).any():
+            raise ValueError("orders must be non-negative, at least one matrix")
+        sizes = orders * orders
+        off = np.zeros(orders.size, dtype=np.int64)
+        np.cumsum(sizes[:-1], out=off[1:])
+        if int(off[-1] + sizes[-1]) != data.size:
+            raise ValueError("data must hold exactly the matrices, back to back")
+        desc = np.zeros(orders.size, dtype=_MATRIX_DTYPE)
+        desc["n"] = orders
+        desc["a"] = np.uint64(data.__array_interface__["data"][0]) + (8 * off).astype(np.uint64)
+        desc["ld"] = np.maximum(orders, 1)
+        obj = cls.__new__(cls)
+        obj._create(desc, data, **opts)
+        return obj
+
+    def _create(self, desc, keep, split_depth=-1, leaf_size=0, order="lpt", kklll_trials=0, seed=0x5EED,
+                workers_per_sm=0, chunk_log2=0, stream=None, torch_allocator=False, timeout_ns=0,
+                model_uses_estimate=True, fused_levels=True, dense_split=False):
+        lib = _lib()
+        self._h = None
+        self._keep = keep  # the host matrices the descriptors point into
+        self._count = len(desc)
         self._desc = desc
-        arr = (perm_matrix * len(self._mats)).from_buffer(desc)
+        arr = (perm_matrix * len(desc)).from_buffer(desc)
         o = perm_opts()
         lib.perm_opts_default(ctypes.byref(o))
         o.split_depth = int(split_depth)
@@ -246,7 +279,7 @@ class Plan:
         self._opts = o
         self._stream = o.stream
         h = ctypes.c_void_p()
-        _ck(lib.perm_plan_create(arr, len(self._mats), ctypes.byref(o), ctypes.byref(h)), "perm_plan_create")
+        _ck(lib.perm_plan_create(arr, len(desc), ctypes.byref(o), ctypes.byref(h)), "perm_plan_create")
         self._h = h
         self._jobs = None
         self.njobs = 0
@@ -347,7 +380,7 @@ class Plan:
         return _limbs_to_int(limbs, n.value, s.value)
 
     def results(self):
-        c = len(self._mats)
+        c = self._count
         w = np.zeros(4 * c, dtype=np.uint64)
         _ck(_lib().perm_result_words(self._h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), c),
             "perm_result_words")

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <numeric>
 #include <thread>
@@ -281,6 +282,20 @@ static void free_eval(Mem& M, perm_jobs* J) {
   J->ev = nullptr;
 }
 
+// Host words left uninitialised on allocation: every word is written by
+// the thread that fills its block (a zero fill of the whole arena would run
+// on one thread).
+struct HostWords {
+  std::unique_ptr<uint64_t[]> p;
+  size_t n = 0;
+  void alloc(size_t k) {
+    p.reset(new uint64_t[k > 0 ? k : 1]);
+    n = k;
+  }
+  uint64_t* data() const { return p.get(); }
+  size_t size() const { return n; }
+};
+
 struct perm_plan {
   perm_opts opts{};
   cudaStream_t s = nullptr;
@@ -291,7 +306,7 @@ struct perm_plan {
   bool leaf_only = false;
   std::vector<int32_t> n, w, kbits, depth;
   std::vector<int8_t> trivial;  // 0 none, 1 per = 0, 2 per = 1
-  std::vector<uint64_t> h_arena;
+  HostWords h_arena;
   std::vector<int64_t> h_off;
   std::vector<int32_t> h_nnz;
   int32_t* d_mat_w = nullptr;
@@ -346,6 +361,7 @@ static int count_nnz(const perm_matrix& A) {
 // CSR block of A (nnz nonzeros) into b (blk_words(n, nnz) zeroed words)
 static void put_csr(uint64_t* b, const perm_matrix& A, int nnz) {
   const int n = A.n;
+  std::memset(b, 0, 8 * (size_t)blk_words(n, nnz));
   uint16_t* rp = reinterpret_cast<uint16_t*>(b);
   uint8_t* col = reinterpret_cast<uint8_t*>(b + blk_rp_words(n));
   int64_t* val = reinterpret_cast<int64_t*>(b + blk_rp_words(n) + blk_col_words(nnz));
@@ -399,17 +415,6 @@ extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, 
     if (A.n < 0 || A.n > PERM_MAX_N || A.ld < A.n || (A.n > 0 && !A.a)) return PERM_EINVAL;
     maxn = std::max(maxn, A.n);
   }
-  std::vector<uint8_t> bad(count, 0);
-  parallel_for(count, [&](int32_t i) {
-    const perm_matrix& A = mats[i];
-    for (int r = 0; r < A.n; ++r)
-      for (int c = 0; c < A.n; ++c) {
-        const int64_t v = A.a[(size_t)r * A.ld + c];
-        if (v >= (1ll << 31) || v <= -(1ll << 31)) bad[i] = 1;
-      }
-  });
-  for (uint8_t b : bad)
-    if (b) return PERM_EINVAL;
   perm_plan* P = new perm_plan();
   P->opts = o;
   P->s = (cudaStream_t)o.stream;
@@ -435,10 +440,17 @@ extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, 
   P->trivial.assign(count, 0);
   P->h_off.assign(count, -1);
   P->h_nnz.assign(count, 0);
-  // per matrix, in parallel: trivial cases, ring width from the bound, nonzeros
-  std::vector<uint8_t> over(count, 0);
+  // per matrix, in parallel: entry range, trivial cases, ring width from the
+  // bound, nonzeros
+  std::vector<uint8_t> over(count, 0), bad(count, 0);
   parallel_for(count, [&](int32_t i) {
     const perm_matrix& A = mats[i];
+    for (int r = 0; r < A.n; ++r)
+      for (int c = 0; c < A.n; ++c) {
+        const int64_t v = A.a[(size_t)r * A.ld + c];
+        if (v >= (1ll << 31) || v <= -(1ll << 31)) bad[i] = 1;
+      }
+    if (bad[i]) return;
     P->n[i] = A.n;
     P->depth[i] = P->leaf_only ? 0 : o.split_depth;  // -1: chosen during the expansion
     if (A.n == 0) {
@@ -480,6 +492,11 @@ extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, 
     }
     P->h_nnz[i] = count_nnz(A);
   });
+  for (uint8_t b : bad)
+    if (b) {
+      delete P;
+      return PERM_EINVAL;
+    }
   for (uint8_t b : over)
     if (b) {
       delete P;
@@ -492,7 +509,7 @@ extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, 
     P->h_off[i] = words;
     words += blk_words(P->n[i], P->h_nnz[i]);
   }
-  P->h_arena.assign((size_t)words, 0ull);
+  P->h_arena.alloc((size_t)words);
   parallel_for(count, [&](int32_t i) {
     if (!P->trivial[i]) put_csr(P->h_arena.data() + P->h_off[i], mats[i], P->h_nnz[i]);
   });

@@ -41,3 +41,16 @@ def test_status_strings_without_gpu():
     lib = pk._lib()
     assert lib.perm_status_string(0) == b"ok"
     assert lib.perm_status_string(2).startswith(b"value or bound")
+
+
+def test_packed_plan_rejects_a_buffer_of_the_wrong_size():
+    """Plan.packed checks the buffer against the orders before any library
+    call (so this runs without a GPU)."""
+    import numpy as np
+    import paper_1112_6072_gb300 as pk
+    with pytest.raises(ValueError):
+        pk.Plan.packed(np.zeros(18, dtype=np.int64), [2, 3, 2])  # the matrices hold 4 + 9 + 4 = 17
+    with pytest.raises(ValueError):
+        pk.Plan.packed(np.zeros(4, dtype=np.int64), [2, -1])
+    with pytest.raises(ValueError):
+        pk.Plan.packed(np.zeros(0, dtype=np.int64), [])

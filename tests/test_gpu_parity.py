@@ -302,6 +302,24 @@ def test_c60_both_constructions():
             assert plan.results() == [want, want]
 
 
+def test_packed_plan_matches_list_plan():
+    """Plan.packed (one buffer, matrices back to back) gives the same plan as
+    the list form: same results, equal to the oracle on sampled matrices;
+    orders 0 and 1 included."""
+    mats = (W.leaf_batch(300, seed=99, nmin=4, nmax=14) + [np.zeros((0, 0), dtype=np.int64), np.array([[5]])]
+            + [W.regular3(20, 3)])
+    data = np.concatenate([np.asarray(m, dtype=np.int64).ravel() for m in mats])
+    orders = [m.shape[0] for m in mats]
+    with pk.Plan(mats, order="natural") as a, pk.Plan.packed(data, orders, order="natural") as b:
+        assert a.expand() == b.expand()
+        a.evaluate()
+        b.evaluate()
+        ra, rb = a.results(), b.results()
+    assert ra == rb
+    for i in (0, 1, 150, 299, 300, 301, 302):
+        assert rb[i] == oracle.permanent(mats[i]), i
+
+
 def test_batch_of_matrices_one_launch():
     mats = [W.regular3(n, n) for n in (20, 24, 28, 30)] + [W.sparse_rows(22, 5)]
     with pk.Plan(mats, leaf_size=10) as plan:
