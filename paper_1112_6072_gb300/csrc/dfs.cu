@@ -417,10 +417,14 @@ struct Dfs {
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) key = min(key, __shfl_xor_sync(0xffffffffu, key, d));
       const int k = (int)(key >> 16);
-      if (k <= 8 || (k <= 16 && nmax >= 16)) {
+      const int ka = (int)((key >> 8) & 0xff), kb = (int)(key & 0xff);
+      // 16 N slots: one of the two columns must fit the first 8
+      if (k <= 8 || (k <= 16 && nmax >= 16 && min(__popc(cmask[ka]), __popc(cmask[kb])) <= 8)) {
         path = k <= 8 ? 3 : 4;
-        ca = (int)((key >> 8) & 0xff);
-        cb = (int)(key & 0xff);
+        // Gray column 0: the one touching at most 8 rows
+        const bool a_first = __popc(cmask[ka]) <= 8;
+        ca = a_first ? ka : kb;
+        cb = a_first ? kb : ka;
         while (clast == ca || clast == cb) --clast;
       }
     }
@@ -430,12 +434,14 @@ struct Dfs {
     __syncwarp();
     int slot = lane;
     if (path >= 3) {
-      const uint32_t touched_mask = cmask[ca] | cmask[cb];
-      const bool touched = lane < m && ((touched_mask >> lane) & 1);
+      // the rows of Gray column 0 first, then the other rows of column 1, then the rest
+      const uint32_t am = cmask[ca];
+      const uint32_t tm = am | cmask[cb];
       const uint32_t below = (1u << lane) - 1u;
-      const int kk = __popc(touched_mask);
       const uint32_t valid = m >= 32 ? 0xffffffffu : ((1u << m) - 1u);
-      slot = touched ? __popc(touched_mask & below) : kk + __popc(~touched_mask & valid & below);
+      slot = ((am >> lane) & 1) ? __popc(am & below)
+             : ((tm >> lane) & 1) ? __popc(am) + __popc(tm & ~am & below)
+                                  : __popc(tm) + __popc(~tm & valid & below);
     }
     if (lane < m) {
       int64_t rs = 0, last = 0;

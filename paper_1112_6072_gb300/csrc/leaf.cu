@@ -110,14 +110,19 @@ __device__ int leaf_class(uint32_t job, const JobArrays& jobs, const uint64_t* _
     path = bc == 7 ? P_G7 : (bc == 15 ? P_G15 : P_G31);
     if (bc == 7 && m >= 3) {
       // the column pair touching the fewest rows (lowest pair on ties)
-      int k = 64;
+      int k = 64, pa = 0, pb = 1;
       for (int a = 0; a < m; ++a)
         for (int b = a + 1; b < m; ++b) {
           const int u = __popc(cm[a] | cm[b]);
-          k = u < k ? u : k;
+          if (u < k) {
+            k = u;
+            pa = a;
+            pb = b;
+          }
         }
+      // 16 N slots: one of the two columns must fit the first 8
       if (k <= 8) path = P_F8;
-      else if (k <= 16 && m > 8) path = P_F16;
+      else if (k <= 16 && m > 8 && min(__popc(cm[pa]), __popc(cm[pb])) <= 8) path = P_F16;
     }
   }
   return nmi | ((W == 4) ? 4 : 0) | (path << 3);
@@ -174,8 +179,9 @@ __device__ void load_plain(const uint64_t* __restrict__ arena, int64_t off, int 
 }
 
 // Load a leaf for the blocked walk: the two sparsest columns become Gray
-// columns 0 and 1, the rows they touch come first, the highest remaining
-// column carries the offset.
+// columns 0 and 1 (column 0 the one touching at most 8 rows), the rows of
+// column 0 come first, then the other rows of column 1, then the rest; the
+// highest remaining column carries the offset.
 __device__ void load_blocked(const uint64_t* __restrict__ arena, int64_t off, int m, int nnz, int nmax,
                              int32_t* delta, int32_t* rho0, int32_t* colcnt, int lane) {
   CsrView v = csr_view(arena, off, m, nnz);
@@ -202,23 +208,23 @@ __device__ void load_blocked(const uint64_t* __restrict__ arena, int64_t off, in
   const int cb = (int)(key & 0xff);
   int clast = m - 1;
   while (clast == ca || clast == cb) --clast;
-  // rows touching ca or cb first
-  bool touched = false;
-  if (lane < m)
-    for (int p = v.rowptr[lane]; p < v.rowptr[lane + 1]; ++p) touched = touched || v.col[p] == ca || v.col[p] == cb;
-  const uint32_t tm = __ballot_sync(0xffffffffu, touched);
+  const bool a_first = __popc((unsigned)colcnt[ca]) <= 8;
+  const int g0 = a_first ? ca : cb, g1 = a_first ? cb : ca;  // Gray columns 0 and 1
+  const uint32_t am = (uint32_t)colcnt[g0];
+  const uint32_t tm = am | (uint32_t)colcnt[g1];
   const uint32_t below = (1u << lane) - 1u;
-  const int k = __popc(tm);
   const uint32_t valid = m >= 32 ? 0xffffffffu : ((1u << m) - 1u);
-  const int slot = touched ? __popc(tm & below) : k + __popc(~tm & valid & below);
+  const int slot = ((am >> lane) & 1) ? __popc(am & below)
+                   : ((tm >> lane) & 1) ? __popc(am) + __popc(tm & ~am & below)
+                                        : __popc(tm) + __popc(~tm & valid & below);
   if (lane < m) {
     int64_t rs = 0, last = 0;
     for (int p = v.rowptr[lane]; p < v.rowptr[lane + 1]; ++p) {
       const int c = v.col[p];
       const int64_t a = v.val[p];
       rs += a;
-      // Gray index of physical column c: ca -> 0, cb -> 1, clast -> offset, others in order from 2
-      const int gj = c == ca ? 0 : (c == cb ? 1 : (c == clast ? -1 : 2 + c - (ca < c) - (cb < c) - (clast < c)));
+      // Gray index of physical column c: g0 -> 0, g1 -> 1, clast -> offset, others in order from 2
+      const int gj = c == g0 ? 0 : (c == g1 ? 1 : (c == clast ? -1 : 2 + c - (ca < c) - (cb < c) - (clast < c)));
       if (gj >= 0) delta[gj * nmax + slot] = (int32_t)(2 * a); else last = a;
     }
     rho0[slot] = (int32_t)(2 * last - rs);

@@ -11,7 +11,11 @@
 //     sum_{t<4} (-1)^t prod_i rho_i(g+t)
 //       = prod_{Z} rho_i(g) * sum_{t<4} (-1)^t prod_{N} rho_i(g+t).
 // The Z product and the wide multiply-accumulate happen once per block; the
-// four N products stay in 64 bits (NN = 8) or in the wide ring (NN = 16).
+// four N products stay in 64 bits (NN = 8).  For NN = 16 the rows of Gray
+// column 0 sit in slots [0, 8) (N1) and slots [8, 16) hold none (N2), so the
+// N2 product only changes when column 1 flips and
+//     sum_t (-1)^t P1(t) P2(t) = (P1(0) - P1(1)) P2(0) + (P1(2) - P1(3)) P2(2),
+// two 64 x 64 -> wide products per block.
 // Column j >= 2 flips at code g with j = ctz(g) and updates every row from
 // shared memory (a broadcast, uniform across the warp).
 #pragma once
@@ -49,7 +53,8 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __
   constexpr int GN = NN / 8;
   constexpr int GZ = (NMAX - NN) / 8;
   if (cnt == 0) return wide_from64(0, (T*)nullptr);
-  int32_t rho[NMAX], d0[NN], d1[NN];
+  // column 0 touches only the first 8 slots (NN = 8, and the N1 group of NN = 16)
+  int32_t rho[NMAX], d0[8], d1[NN];
   const int4* r4 = reinterpret_cast<const int4*>(rho0);
   const int4* c0 = reinterpret_cast<const int4*>(delta);
   const int4* c1 = reinterpret_cast<const int4*>(delta + NMAX);
@@ -62,13 +67,16 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __
     rho[4 * k + 3] = v.w;
   }
 #pragma unroll
-  for (int k = 0; k < NN / 4; ++k) {
+  for (int k = 0; k < 2; ++k) {
     const int4 u = c0[k];
-    const int4 w = c1[k];
     d0[4 * k] = u.x;
     d0[4 * k + 1] = u.y;
     d0[4 * k + 2] = u.z;
     d0[4 * k + 3] = u.w;
+  }
+#pragma unroll
+  for (int k = 0; k < NN / 4; ++k) {
+    const int4 w = c1[k];
     d1[4 * k] = w.x;
     d1[4 * k + 1] = w.y;
     d1[4 * k + 2] = w.z;
@@ -112,16 +120,22 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __
         wide_add(acc, wide_mul64(prod_groups<NMAX, W, NN, GZ>(rho), sn));
       }
     } else {
-      T sn = prod_groups<NMAX, W, 0, GN>(rho);
+      static_assert(GN == 2, "N groups of 8 and 8");
+      const int64_t a0 = prod8<NMAX>(rho, 0);
+      const int64_t b0 = prod8<NMAX>(rho, 8);
 #pragma unroll
-      for (int i = 0; i < NN; ++i) rho[i] += d0[i];
-      wide_sub(sn, prod_groups<NMAX, W, 0, GN>(rho));
+      for (int i = 0; i < 8; ++i) rho[i] += d0[i];
+      const int64_t a1 = prod8<NMAX>(rho, 0);
 #pragma unroll
       for (int i = 0; i < NN; ++i) rho[i] += s1 * d1[i];
-      wide_add(sn, prod_groups<NMAX, W, 0, GN>(rho));
+      const int64_t a2 = prod8<NMAX>(rho, 0);
+      const int64_t b2 = prod8<NMAX>(rho, 8);
 #pragma unroll
-      for (int i = 0; i < NN; ++i) rho[i] -= d0[i];
-      wide_sub(sn, prod_groups<NMAX, W, 0, GN>(rho));
+      for (int i = 0; i < 8; ++i) rho[i] -= d0[i];
+      const int64_t a3 = prod8<NMAX>(rho, 0);
+      // |a_t| < 2^56, so the differences fit 64 bits
+      T sn = wide_mul64x64(a0 - a1, b0, (T*)nullptr);
+      wide_add(sn, wide_mul64x64(a2 - a3, b2, (T*)nullptr));
       if constexpr (GZ == 0) {
         wide_add(acc, sn);
       } else if constexpr (GZ == 1) {
