@@ -59,6 +59,55 @@ def test_leaf_batch_signed_and_wide():
     assert got == want
 
 
+def _column_supports(n, supports, seed):
+    """n x n matrix whose column j holds supports[j] entries in 1..3 at random rows."""
+    rng = np.random.default_rng(seed)
+    a = np.zeros((n, n), dtype=np.int64)
+    for j, k in enumerate(supports):
+        rows = rng.choice(n, size=k, replace=False)
+        a[rows, j] = rng.integers(1, 4, size=k)
+    return a
+
+
+def _sparsest_pair(a):
+    """(union, |rows of a|, |rows of b|) of the column pair touching the
+    fewest rows, the lowest pair on ties (the blocked walk's choice)."""
+    nz = a != 0
+    best = None
+    for x in range(a.shape[0]):
+        for y in range(x + 1, a.shape[0]):
+            u = int((nz[:, x] | nz[:, y]).sum())
+            if best is None or u < best[0]:
+                best = (u, int(nz[:, x].sum()), int(nz[:, y].sum()))
+    return best
+
+
+def test_blocked_walk_orientation_and_fallback():
+    """Leaves whose sparsest column pair touches 9-16 rows: with the lower
+    column over 8 rows and the other within 8 (column 1 becomes Gray column
+    0), and with both over 8 (the plain walk); every line holds >= 5 entries,
+    so the depth-first evaluator also takes each matrix as one leaf."""
+    swap = [_column_supports(20, [9] * 19 + [7], s) for s in (2, 4)]
+    plain = [_column_supports(20, [9] * 20, s) for s in (1, 2, 4)]
+    for a in swap:
+        u, ka, kb = _sparsest_pair(a)
+        assert 8 < u <= 16 and ka > 8 and kb <= 8
+    for a in plain:
+        u, ka, kb = _sparsest_pair(a)
+        assert 8 < u <= 16 and ka > 8 and kb > 8
+    mats = swap + plain
+    assert min(int((m != 0).sum(axis=1).min()) for m in mats) >= 5
+    want = [oracle.permanent(m) for m in mats]
+    with pk.Plan(mats) as plan:  # leaf batch
+        plan.expand()
+        plan.evaluate()
+        assert plan.results() == want
+    with pk.Plan(mats, split_depth=0, leaf_size=12) as plan:  # depth-first, one leaf each
+        plan.expand()
+        plan.evaluate()
+        assert plan.results() == want
+
+
 def test_leaf_chunk_sizes_agree():
     mats = W.leaf_batch(24, seed=5, nmin=14, nmax=20)
     res = []
