@@ -202,6 +202,31 @@ class JobRecord:
     nodes: int
 
 
+def packed_descriptors(data, orders):
+    """(buffer, perm_matrix records) for matrices stored back to back in one
+    int64 buffer: record i has n = orders[i], ld = max(n, 1) and the address
+    of data[off_i], off_i the sum of the earlier orders squared.  The buffer
+    returned is the contiguous int64 array the addresses point into (the
+    input itself when it already is one)."""
+    data = np.asarray(data)
+    if data.dtype != np.int64 or not data.flags.c_contiguous:
+        data = np.ascontiguousarray(data, dtype=np.int64)
+    data = data.reshape(-1)
+    orders = np.asarray(orders, dtype=np.int64).reshape(-1)
+    if orders.size == 0 or (orders < 0).any():
+        raise ValueError("orders must be non-negative, at least one matrix")
+    sizes = orders * orders
+    off = np.zeros(orders.size, dtype=np.int64)
+    np.cumsum(sizes[:-1], out=off[1:])
+    if int(off[-1] + sizes[-1]) != data.size:
+        raise ValueError("data must hold exactly the matrices, back to back")
+    desc = np.zeros(orders.size, dtype=_MATRIX_DTYPE)
+    desc["n"] = orders
+    desc["a"] = np.uint64(data.__array_interface__["data"][0]) + (8 * off).astype(np.uint64)
+    desc["ld"] = np.maximum(orders, 1)
+    return data, desc
+
+
 class Plan:
     """A batch of matrices through the whole path: expand, order, evaluate.
 
@@ -228,22 +253,7 @@ class Plan:
         matrix i, of order orders[i], is data[off_i : off_i + orders[i]**2]
         in row-major order, off_i the sum of the earlier orders squared.
         The descriptors come from one prefix sum.  Options as for Plan."""
-        data = np.asarray(data)
-        if data.dtype != np.int64 or not data.flags.c_contiguous:
-            data = np.ascontiguousarray(data, dtype=np.int64)
-        data = data.reshape(-1)
-        orders = np.asarray(orders, dtype=np.int64).reshape(-1)
-        if orders.size == 0 or (orders < 0).any():
-            raise ValueError("orders must be non-negative, at least one matrix")
-        sizes = orders * orders
-        off = np.zeros(orders.size, dtype=np.int64)
-        np.cumsum(sizes[:-1], out=off[1:])
-        if int(off[-1] + sizes[-1]) != data.size:
-            raise ValueError("data must hold exactly the matrices, back to back")
-        desc = np.zeros(orders.size, dtype=_MATRIX_DTYPE)
-        desc["n"] = orders
-        desc["a"] = np.uint64(data.__array_interface__["data"][0]) + (8 * off).astype(np.uint64)
-        desc["ld"] = np.maximum(orders, 1)
+        data, desc = packed_descriptors(data, orders)
         obj = cls.__new__(cls)
         obj._create(desc, data, **opts)
         return obj

@@ -54,3 +54,29 @@ def test_packed_plan_rejects_a_buffer_of_the_wrong_size():
         pk.Plan.packed(np.zeros(4, dtype=np.int64), [2, -1])
     with pytest.raises(ValueError):
         pk.Plan.packed(np.zeros(0, dtype=np.int64), [])
+
+
+def test_packed_descriptors_address_each_matrix():
+    """Each record of a packed batch points at its matrix: the same address
+    as a view of that matrix in the buffer, with its order and row stride."""
+    import numpy as np
+    import paper_1112_6072_gb300 as pk
+    rng = np.random.default_rng(4)
+    orders = [int(x) for x in rng.integers(0, 9, size=40)] + [1, 0, 24]
+    mats = [rng.integers(-3, 4, size=(n, n)).astype(np.int64) for n in orders]
+    data, desc = pk.packed_descriptors(np.concatenate([m.ravel() for m in mats]), orders)
+    off = 0
+    for i, m in enumerate(mats):
+        n = m.shape[0]
+        view = data[off:off + n * n]
+        assert int(desc["n"][i]) == n and int(desc["ld"][i]) == max(n, 1)
+        if n > 0:  # numpy gives an empty slice the buffer's base address; order 0 reads nothing
+            assert int(desc["a"][i]) == view.__array_interface__["data"][0]
+        assert np.array_equal(view.reshape(n, n), m)
+        off += n * n
+    # a contiguous int64 input is used in place, anything else converted once
+    buf = np.arange(4 + 9, dtype=np.int64)
+    same, _ = pk.packed_descriptors(buf, [2, 3])
+    assert same.__array_interface__["data"][0] == buf.__array_interface__["data"][0]
+    conv, d2 = pk.packed_descriptors(buf.astype(np.int32), [2, 3])
+    assert conv.dtype == np.int64 and int(d2["a"][1]) - int(d2["a"][0]) == 8 * 4
