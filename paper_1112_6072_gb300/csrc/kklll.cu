@@ -509,13 +509,14 @@ __global__ void __launch_bounds__(TCfg<MT>::WARPS * 32)
 // of LPG = MT / RPL lanes runs one trial, lane i holding rows i*RPL ..
 // i*RPL+RPL-1 of the trial matrix in registers, so a warp runs 32 / LPG
 // trials side by side with no shared memory.  Rows never move: the pivot of
-// step k is the row not yet pivoted with the largest |z|^2, ties to the row
-// at the lowest position (positions follow the row swaps of partial
-// pivoting, so the pivot sequence is that of the swapping elimination), and
-// the pivot row is broadcast column by column with a shuffle from the lane
-// holding it.  |det W|^2 is the product of the pivots' |z|^2.  A warp takes
-// 32 trials of one job (32 / LPG rounds) and writes their log-sum-exp to
-// part[], which k_kklll_combine merges per job.
+// step k is the row not yet pivoted with the largest |z|^2, ties (within
+// 2^-15 relative) to the row at the lowest position (positions follow the
+// row swaps of partial pivoting, so the pivot sequence is that of the
+// swapping elimination), and the pivot row is broadcast column by column
+// with a shuffle from the lane holding it.  |det W|^2 is the product of the
+// pivots' |z|^2.  A warp takes 32 trials of one job (LPG rounds of 32 / LPG
+// trials) and writes their sum to part[], which k_kklll_combine merges per
+// job.
 template <int MT, int RPL>
 __global__ void __launch_bounds__(256, 2)
     k_kklll_lanes(JobArrays jobs, int64_t njobs, const uint64_t* __restrict__ arena, int trials, uint64_t seed,
