@@ -28,6 +28,13 @@ void set_last_error(const char* what, cudaError_t e) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
 }
 
+void set_last_error_text(const char* what) noexcept {
+  try {
+    g_last_error = what;
+  } catch (...) {
+  }
+}
+
 extern "C" const char* perm_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" const char* perm_status_string(perm_status s) {
@@ -401,8 +408,8 @@ static void parallel_for(int32_t count, F fn) {
   for (auto& t : pool) t.join();
 }
 
-extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, const perm_opts* opts,
-                                        perm_plan_t** out) {
+static perm_status perm_plan_create_impl(const perm_matrix* mats, int32_t count, const perm_opts* opts,
+                                         perm_plan_t** out) {
   if (!out || !mats || count < 1) return PERM_EINVAL;
   *out = nullptr;
   perm_opts o;
@@ -533,6 +540,10 @@ extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, 
   *out = P;
   return PERM_OK;
 }
+extern "C" perm_status perm_plan_create(const perm_matrix* mats, int32_t count, const perm_opts* opts,
+                                        perm_plan_t** out) {
+  return guarded([&] { return perm_plan_create_impl(mats, count, opts, out); });
+}
 
 static void free_jobset(perm_plan* P) {
   perm_jobs* J = P->jobs;
@@ -580,7 +591,7 @@ static const int64_t kFusedWords0 = 1ll << 23;
 static const int64_t kFusedMaxJobs = 1ll << 20;
 static const int64_t kFusedMaxWords = 1ll << 26;
 
-extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64_t* njobs) {
+static perm_status perm_expand_impl(perm_plan_t* P, perm_jobs_t** jobs_out, int64_t* njobs) {
   if (!P) return PERM_EINVAL;
   free_jobset(P);
   P->evaluated = false;
@@ -855,9 +866,12 @@ extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64
   if (njobs) *njobs = ncur;
   return PERM_OK;
 }
+extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64_t* njobs) {
+  return guarded([&] { return perm_expand_impl(P, jobs_out, njobs); });
+}
 
 // ---------------------------------------------------------------- a4: estimate
-extern "C" perm_status perm_estimate(perm_jobs_t* J, float* log_ap) {
+static perm_status perm_estimate_impl(perm_jobs_t* J, float* log_ap) {
   if (!J) return PERM_EINVAL;
   perm_plan* P = J->plan;
   if (J->max_order > PERM_MAX_N) return PERM_EINVAL;
@@ -873,8 +887,11 @@ extern "C" perm_status perm_estimate(perm_jobs_t* J, float* log_ap) {
   }
   return PERM_OK;
 }
+extern "C" perm_status perm_estimate(perm_jobs_t* J, float* log_ap) {
+  return guarded([&] { return perm_estimate_impl(J, log_ap); });
+}
 
-extern "C" perm_status perm_job_features(perm_jobs_t* J, float* feats) {
+static perm_status perm_job_features_impl(perm_jobs_t* J, float* feats) {
   if (!J || !feats) return PERM_EINVAL;
   perm_plan* P = J->plan;
   const bool use_ap = P->opts.model_uses_estimate != 0;
@@ -889,6 +906,9 @@ extern "C" perm_status perm_job_features(perm_jobs_t* J, float* feats) {
   CK(cudaStreamSynchronize(P->s));
   P->M.put(d);
   return PERM_OK;
+}
+extern "C" perm_status perm_job_features(perm_jobs_t* J, float* feats) {
+  return guarded([&] { return perm_job_features_impl(J, feats); });
 }
 
 // ---------------------------------------------------------------- a5, a6: order
@@ -911,7 +931,7 @@ static perm_status sort_queue_by(perm_plan* P, perm_jobs* J, const float* d_keys
   return PERM_OK;
 }
 
-extern "C" perm_status perm_order(perm_jobs_t* J, int32_t kind, uint32_t* order_out) {
+static perm_status perm_order_impl(perm_jobs_t* J, int32_t kind, uint32_t* order_out) {
   if (!J) return PERM_EINVAL;
   perm_plan* P = J->plan;
   const int64_t n = J->n;
@@ -958,6 +978,9 @@ extern "C" perm_status perm_order(perm_jobs_t* J, int32_t kind, uint32_t* order_
     CK(cudaStreamSynchronize(P->s));
   }
   return PERM_OK;
+}
+extern "C" perm_status perm_order(perm_jobs_t* J, int32_t kind, uint32_t* order_out) {
+  return guarded([&] { return perm_order_impl(J, kind, order_out); });
 }
 
 // ---------------------------------------------------------------- a7, a8: evaluate
@@ -1221,7 +1244,7 @@ static perm_status eval_finish(perm_jobs* J, perm_job_result* results) {
   return PERM_OK;
 }
 
-extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, perm_job_result* results) {
+static perm_status perm_eval_batch_impl(perm_jobs_t* J, const uint32_t* order, perm_job_result* results) {
   if (!J) return PERM_EINVAL;
   perm_plan* P = J->plan;
   perm_status st = eval_prepare(J, order);
@@ -1231,8 +1254,11 @@ extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, pe
   CK(cudaEventRecord(P->ev1, P->s));
   return eval_finish(J, results);
 }
+extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, perm_job_result* results) {
+  return guarded([&] { return perm_eval_batch_impl(J, order, results); });
+}
 
-extern "C" perm_status perm_eval_replay(perm_jobs_t* J, perm_job_result* results) {
+static perm_status perm_eval_replay_impl(perm_jobs_t* J, perm_job_result* results) {
   if (!J) return PERM_EINVAL;
   perm_plan* P = J->plan;
   EvalState* E = J->ev;
@@ -1256,17 +1282,26 @@ extern "C" perm_status perm_eval_replay(perm_jobs_t* J, perm_job_result* results
   CK(cudaEventRecord(P->ev1, P->s));
   return eval_finish(J, results);
 }
+extern "C" perm_status perm_eval_replay(perm_jobs_t* J, perm_job_result* results) {
+  return guarded([&] { return perm_eval_replay_impl(J, results); });
+}
 
-extern "C" perm_status perm_last_eval_launches(perm_plan_t* P, int32_t* launches) {
+static perm_status perm_last_eval_launches_impl(perm_plan_t* P, int32_t* launches) {
   if (!P || !launches) return PERM_EINVAL;
   *launches = P->last_launches;
   return PERM_OK;
 }
+extern "C" perm_status perm_last_eval_launches(perm_plan_t* P, int32_t* launches) {
+  return guarded([&] { return perm_last_eval_launches_impl(P, launches); });
+}
 
-extern "C" perm_status perm_last_eval_ms(perm_plan_t* P, float* ms) {
+static perm_status perm_last_eval_ms_impl(perm_plan_t* P, float* ms) {
   if (!P || !ms) return PERM_EINVAL;
   *ms = P->last_ms;
   return PERM_OK;
+}
+extern "C" perm_status perm_last_eval_ms(perm_plan_t* P, float* ms) {
+  return guarded([&] { return perm_last_eval_ms_impl(P, ms); });
 }
 
 // ---------------------------------------------------------------- a8: results
@@ -1299,7 +1334,7 @@ static perm_status result_words(perm_plan* P, std::vector<uint64_t>& words) {
   return PERM_OK;
 }
 
-extern "C" perm_status perm_result_words(perm_plan_t* P, uint64_t* out, int32_t count) {
+static perm_status perm_result_words_impl(perm_plan_t* P, uint64_t* out, int32_t count) {
   if (!P || !out || count < P->count) return PERM_EINVAL;
   std::vector<uint64_t> w;
   perm_status st = result_words(P, w);
@@ -1307,15 +1342,21 @@ extern "C" perm_status perm_result_words(perm_plan_t* P, uint64_t* out, int32_t 
   memcpy(out, w.data(), 32ull * P->count);
   return PERM_OK;
 }
+extern "C" perm_status perm_result_words(perm_plan_t* P, uint64_t* out, int32_t count) {
+  return guarded([&] { return perm_result_words_impl(P, out, count); });
+}
 
-extern "C" perm_status perm_result_bits(perm_plan_t* P, int32_t index, int32_t* bits) {
+static perm_status perm_result_bits_impl(perm_plan_t* P, int32_t index, int32_t* bits) {
   if (!P || !bits || index < 0 || index >= P->count) return PERM_EINVAL;
   *bits = P->kbits[index];
   return PERM_OK;
 }
+extern "C" perm_status perm_result_bits(perm_plan_t* P, int32_t index, int32_t* bits) {
+  return guarded([&] { return perm_result_bits_impl(P, index, bits); });
+}
 
-extern "C" perm_status perm_result(perm_plan_t* P, int32_t index, uint32_t* limbs, int32_t cap, int32_t* nlimbs,
-                                   int32_t* sign) {
+static perm_status perm_result_impl(perm_plan_t* P, int32_t index, uint32_t* limbs, int32_t cap, int32_t* nlimbs,
+                                    int32_t* sign) {
   if (!P || index < 0 || index >= P->count || !nlimbs || !sign) return PERM_EINVAL;
   std::vector<uint64_t> w;
   perm_status st = result_words(P, w);
@@ -1342,9 +1383,13 @@ extern "C" perm_status perm_result(perm_plan_t* P, int32_t index, uint32_t* limb
   for (int k = 0; k < n; ++k) limbs[k] = l[k];
   return PERM_OK;
 }
+extern "C" perm_status perm_result(perm_plan_t* P, int32_t index, uint32_t* limbs, int32_t cap, int32_t* nlimbs,
+                                   int32_t* sign) {
+  return guarded([&] { return perm_result_impl(P, index, limbs, cap, nlimbs, sign); });
+}
 
-extern "C" perm_status perm_jobs_export(perm_jobs_t* J, int64_t* total_entries, int32_t* sizes, int64_t* mats,
-                                        uint64_t* coef, int32_t* matrix) {
+static perm_status perm_jobs_export_impl(perm_jobs_t* J, int64_t* total_entries, int32_t* sizes, int64_t* mats,
+                                         uint64_t* coef, int32_t* matrix) {
   if (!J || !total_entries) return PERM_EINVAL;
   perm_plan* P = J->plan;
   const int64_t n = J->n;
@@ -1382,9 +1427,13 @@ extern "C" perm_status perm_jobs_export(perm_jobs_t* J, int64_t* total_entries, 
   }
   return PERM_OK;
 }
+extern "C" perm_status perm_jobs_export(perm_jobs_t* J, int64_t* total_entries, int32_t* sizes, int64_t* mats,
+                                        uint64_t* coef, int32_t* matrix) {
+  return guarded([&] { return perm_jobs_export_impl(J, total_entries, sizes, mats, coef, matrix); });
+}
 
-extern "C" perm_status perm_exact(const perm_matrix* a, const perm_opts* opts, uint32_t* limbs, int32_t cap,
-                                  int32_t* nlimbs, int32_t* sign) {
+static perm_status perm_exact_impl(const perm_matrix* a, const perm_opts* opts, uint32_t* limbs, int32_t cap,
+                                   int32_t* nlimbs, int32_t* sign) {
   perm_plan_t* P = nullptr;
   perm_status st = perm_plan_create(a, 1, opts, &P);
   if (st != PERM_OK) return st;
@@ -1396,6 +1445,10 @@ extern "C" perm_status perm_exact(const perm_matrix* a, const perm_opts* opts, u
   if (st == PERM_OK) st = perm_result(P, 0, limbs, cap, nlimbs, sign);
   perm_plan_destroy(P);
   return st;
+}
+extern "C" perm_status perm_exact(const perm_matrix* a, const perm_opts* opts, uint32_t* limbs, int32_t cap,
+                                  int32_t* nlimbs, int32_t* sign) {
+  return guarded([&] { return perm_exact_impl(a, opts, limbs, cap, nlimbs, sign); });
 }
 
 // ---------------------------------------------------------------- learned model
@@ -1415,8 +1468,8 @@ struct Scratch {
   }
 };
 
-extern "C" perm_status perm_mlp_grad(const float* params, const float* feats, const float* target, int32_t count,
-                                     void* stream, float* loss, float* grad) {
+static perm_status perm_mlp_grad_impl(const float* params, const float* feats, const float* target, int32_t count,
+                                      void* stream, float* loss, float* grad) {
   if (!params || !feats || !target || count < 1 || !loss || !grad) return PERM_EINVAL;
   Scratch S{(cudaStream_t)stream, {}};
   float* dp = S.get<float>(PERM_MLP_PARAMS);
@@ -1435,9 +1488,13 @@ extern "C" perm_status perm_mlp_grad(const float* params, const float* feats, co
   CK(cudaStreamSynchronize(S.s));
   return PERM_OK;
 }
+extern "C" perm_status perm_mlp_grad(const float* params, const float* feats, const float* target, int32_t count,
+                                     void* stream, float* loss, float* grad) {
+  return guarded([&] { return perm_mlp_grad_impl(params, feats, target, count, stream, loss, grad); });
+}
 
-extern "C" perm_status perm_mlp_train(float* params, const float* feats, const float* target, int32_t count,
-                                      int32_t steps, float lr, void* stream, float* final_loss) {
+static perm_status perm_mlp_train_impl(float* params, const float* feats, const float* target, int32_t count,
+                                       int32_t steps, float lr, void* stream, float* final_loss) {
   if (!params || !feats || !target || count < 1 || steps < 0) return PERM_EINVAL;
   Scratch S{(cudaStream_t)stream, {}};
   float* dp = S.get<float>(PERM_MLP_PARAMS);
@@ -1466,9 +1523,13 @@ extern "C" perm_status perm_mlp_train(float* params, const float* feats, const f
   CK(cudaStreamSynchronize(S.s));
   return PERM_OK;
 }
+extern "C" perm_status perm_mlp_train(float* params, const float* feats, const float* target, int32_t count,
+                                      int32_t steps, float lr, void* stream, float* final_loss) {
+  return guarded([&] { return perm_mlp_train_impl(params, feats, target, count, steps, lr, stream, final_loss); });
+}
 
-extern "C" perm_status perm_mlp_predict(const float* params, const float* feats, int32_t count, void* stream,
-                                        float* pred) {
+static perm_status perm_mlp_predict_impl(const float* params, const float* feats, int32_t count, void* stream,
+                                         float* pred) {
   if (!params || !feats || count < 1 || !pred) return PERM_EINVAL;
   Scratch S{(cudaStream_t)stream, {}};
   float* dp = S.get<float>(PERM_MLP_PARAMS);
@@ -1482,16 +1543,23 @@ extern "C" perm_status perm_mlp_predict(const float* params, const float* feats,
   CK(cudaStreamSynchronize(S.s));
   return PERM_OK;
 }
+extern "C" perm_status perm_mlp_predict(const float* params, const float* feats, int32_t count, void* stream,
+                                        float* pred) {
+  return guarded([&] { return perm_mlp_predict_impl(params, feats, count, stream, pred); });
+}
 
-extern "C" perm_status perm_mlp_attach(perm_plan_t* P, const float* params) {
+static perm_status perm_mlp_attach_impl(perm_plan_t* P, const float* params) {
   if (!P || !params) return PERM_EINVAL;
   P->mlp.assign(params, params + PERM_MLP_PARAMS);
   if (P->jobs) P->jobs->has_order = false;
   return PERM_OK;
 }
+extern "C" perm_status perm_mlp_attach(perm_plan_t* P, const float* params) {
+  return guarded([&] { return perm_mlp_attach_impl(P, params); });
+}
 
 // ---------------------------------------------------------------- measurement
-extern "C" perm_status perm_ubench_imad(int32_t blocks, int32_t iters, void* stream, float* ms, double* rate) {
+static perm_status perm_ubench_imad_impl(int32_t blocks, int32_t iters, void* stream, float* ms, double* rate) {
   if (blocks < 1 || iters < 1 || !ms || !rate) return PERM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   Scratch S{s, {}};
@@ -1510,4 +1578,7 @@ extern "C" perm_status perm_ubench_imad(int32_t blocks, int32_t iters, void* str
   cudaEventDestroy(b);
   *rate = (double)blocks * 256.0 * 16.0 * (double)iters / (*ms * 1e-3);
   return PERM_OK;
+}
+extern "C" perm_status perm_ubench_imad(int32_t blocks, int32_t iters, void* stream, float* ms, double* rate) {
+  return guarded([&] { return perm_ubench_imad_impl(blocks, iters, stream, ms, rate); });
 }

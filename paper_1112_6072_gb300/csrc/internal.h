@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <exception>
 
 #include "../../include/perm.h"
 #include "jobs.cuh"
@@ -195,3 +196,19 @@ cudaError_t launch_ubench_imad(int blocks, int iters, uint32_t* sink, cudaStream
 
 // ---- errors ----------------------------------------------------------------------
 void set_last_error(const char* what, cudaError_t e);
+void set_last_error_text(const char* what) noexcept;
+
+// Runs an entry point's body so that a host exception (a failed host
+// allocation, or a host thread that could not start) becomes PERM_ENOMEM
+// with perm_last_error() set, instead of crossing the C boundary.
+template <class F>
+static perm_status guarded(F&& body) noexcept {
+  try {
+    return body();
+  } catch (const std::exception& e) {
+    set_last_error_text(e.what());
+  } catch (...) {
+    set_last_error_text("host exception");
+  }
+  return PERM_ENOMEM;
+}

@@ -180,8 +180,8 @@ cudaError_t na_scratch(int dev, NoAllocScratch** out) {
 
 }  // namespace
 
-extern "C" perm_status perm_leaf_batch_noalloc(const int64_t* a, int32_t n, int32_t count, uint64_t* out,
-                                               int32_t* status, void* stream) {
+static perm_status perm_leaf_batch_noalloc_impl(const int64_t* a, int32_t n, int32_t count, uint64_t* out,
+                                                int32_t* status, void* stream) {
   if (!a || !out || !status) return PERM_EINVAL;
   if (n < 1 || n > PERM_MAX_LEAF) return PERM_EINVAL;
   if (count < 1 || count > PERM_NOALLOC_MAX_COUNT) return PERM_EINVAL;
@@ -214,4 +214,8 @@ extern "C" perm_status perm_leaf_batch_noalloc(const int64_t* a, int32_t n, int3
     return PERM_ECUDA;
   }
   return PERM_OK;
+}
+extern "C" perm_status perm_leaf_batch_noalloc(const int64_t* a, int32_t n, int32_t count, uint64_t* out,
+                                               int32_t* status, void* stream) {
+  return guarded([&] { return perm_leaf_batch_noalloc_impl(a, n, count, out, status, stream); });
 }
