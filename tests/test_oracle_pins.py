@@ -305,6 +305,64 @@ def test_kklll_estimate_near_permanent():
     assert abs(la - math.log(p)) < 0.35
 
 
+@pytest.mark.parametrize("perm,seed,job", [([1, 2, 0], 3, 0), ([4, 0, 3, 1, 2, 5], 11, 7),
+                                           (list(range(9))[::-1], 2, 3)])
+def test_kklll_permutation_pattern_is_exactly_one(perm, seed, job):
+    """A permutation pattern has per(B) = 1 and |det W|^2 = prod |w|^2 = 1 in
+    every trial (each w a cube root of unity), so log AP = 0 for any trial
+    count and stream position."""
+    m = len(perm)
+    b = np.zeros((m, m), dtype=np.int64)
+    b[np.arange(m), perm] = 1
+    for trials in (1, 5, 40):
+        assert abs(oracle.kklll_log_ap(b, seed=seed, job=job, trials=trials)) < 1e-12
+
+
+def test_kklll_block_diagonal_permutation_blocks():
+    """Block diagonal of 1x1 blocks and permutation blocks (again a
+    permutation pattern, now with blocks of several orders): log AP = 0."""
+    blocks = [np.ones((1, 1)), np.eye(3)[[2, 0, 1]], np.ones((1, 1)), np.eye(4)[[1, 3, 0, 2]]]
+    m = sum(x.shape[0] for x in blocks)
+    b = np.zeros((m, m), dtype=np.int64)
+    k = 0
+    for x in blocks:
+        r = x.shape[0]
+        b[k:k + r, k:k + r] = x
+        k += r
+    assert abs(oracle.kklll_log_ap(b, seed=9, job=4, trials=25)) < 1e-12
+
+
+@pytest.mark.parametrize("seed,job,trials", [(1, 0, 4), (7, 3, 9), (1234, 11, 64), (5, 2, 1)])
+def test_kklll_all_ones_2x2_exact_mean(seed, job, trials):
+    """All-ones 2 x 2 pattern: det W = w00 w11 - w01 w10 = u^(c00+c11) - u^(c01+c10)
+    with u = exp(2 pi i / 3), so |det W|^2 = 0 when c00 + c11 = c01 + c10 (mod 3)
+    and |1 - u|^2 = 3 otherwise.  Reading each trial's draws back with
+    kklll_choice gives the mean as an exact rational 3 k / T, which pins the
+    log of the mean over trials (not a mean of logs) and the all-singular
+    case (-inf)."""
+    b = np.ones((2, 2), dtype=np.int64)
+    k = 0
+    for t in range(trials):
+        c = [oracle.kklll_choice(seed, job, t, e) for e in range(4)]  # e = 2 i + j
+        k += (c[0] + c[3] - c[1] - c[2]) % 3 != 0
+    got = oracle.kklll_log_ap(b, seed=seed, job=job, trials=trials)
+    if k == 0:
+        assert got == -math.inf
+    else:
+        assert abs(got - math.log(3.0 * k / trials)) < 1e-12
+    # a stream where trials differ, so a mean of logs would not agree
+    if 0 < k < trials:
+        assert abs(got - math.log(3.0)) > 1e-3
+
+
+def test_kklll_all_ones_2x2_stream_has_both_outcomes():
+    """The pin above sees both singular and regular trials on this stream."""
+    ks = [(oracle.kklll_choice(1234, 11, t, 0) + oracle.kklll_choice(1234, 11, t, 3)
+           - oracle.kklll_choice(1234, 11, t, 1) - oracle.kklll_choice(1234, 11, t, 2)) % 3 != 0
+          for t in range(64)]
+    assert 0 < sum(ks) < 64
+
+
 # ---------------------------------------------------------------- scheduling
 def test_efficiency_reproduces_table_t5():
     """Tables T5-T7 (C100): printed efficiency = T1 / (m Tm)."""
