@@ -174,6 +174,21 @@ perm_status perm_order(perm_jobs_t* jobs, int32_t kind, uint32_t* order_out);
  * row sum left int32), PERM_ETIMEOUT, PERM_ECUDA. */
 perm_status perm_eval_batch(perm_jobs_t* jobs, const uint32_t* order, perm_job_result* results);
 
+/* a7, a8 over part of the queue (Algorithm PH, Step 3, with the jobs dealt
+ * to several workers -- e.g. one GPU each -- and Step 4's sum taken over
+ * their partial sums).  queue (host) holds count distinct job indices
+ * (0 <= count <= njobs; queue may be NULL when count is 0), evaluated in
+ * that order as by perm_eval_batch; the other jobs are not evaluated: their
+ * records are zero with queue_pos = -1.  Afterwards perm_result,
+ * perm_result_words and perm_result_bits give each matrix's sum over the
+ * evaluated jobs, modulo 2^K (perm_result_bits): the sums of disjoint
+ * sub-queues that together hold every job add up, modulo 2^K, to per(A).  A
+ * matrix without jobs (order 0, or a zero line) contributes 0 to every
+ * sub-queue sum.  Errors as for perm_eval_batch; PERM_EINVAL for a repeated
+ * or out-of-range index. */
+perm_status perm_eval_subset(perm_jobs_t* jobs, const uint32_t* queue, int64_t count,
+                             perm_job_result* results);
+
 /* a7, a8 again, as a CUDA graph: repeat the last perm_eval_batch of this job
  * set (same queue, same buffers).  The first call captures that
  * evaluation's memsets and launches into a graph (on a stream the library
@@ -210,6 +225,17 @@ perm_status perm_result_words(perm_plan_t* plan, uint64_t* out, int32_t count);
  * 2^256, matrix[w] the source matrix (nullable). */
 perm_status perm_jobs_export(perm_jobs_t* jobs, int64_t* total_entries, int32_t* sizes,
                              int64_t* mats, uint64_t* coef, int32_t* matrix);
+
+/* Export chosen jobs only (a sample of a large job set): idx (host) holds
+ * count job indices (repeats allowed).  sizes[k] = order of job idx[k];
+ * *entries = the sum of the orders squared; mats (nullable) receives the
+ * dense row-major jobs back to back (PERM_ESHORTBUF, with sizes and *entries
+ * set, when mats_cap is smaller); coef[k*4..] (nullable) the coefficient
+ * modulo 2^256; matrix[k] (nullable) the source matrix.  PERM_EINVAL for an
+ * index outside [0, njobs). */
+perm_status perm_jobs_select(perm_jobs_t* jobs, const int64_t* idx, int64_t count, int32_t* sizes,
+                             int64_t* mats, int64_t mats_cap, uint64_t* coef, int32_t* matrix,
+                             int64_t* entries);
 
 /* Convenience: per(A) of one matrix (perm_plan_create, perm_expand,
  * perm_order(opts.order), perm_eval_batch, perm_result, perm_plan_destroy). */
@@ -252,21 +278,25 @@ perm_status perm_mlp_predict(const float* params, const float* feats, int32_t co
 perm_status perm_mlp_attach(perm_plan_t* plan, const float* params);
 
 /* ---- allocation-free leaf batch -------------------------------------------------
- * The paper has no counterpart to this entry point; it exists for callers
- * that cannot allocate device memory while they run: code that is recording
- * a CUDA graph (where cudaMalloc is not allowed), hosts whose own allocator
- * must own every device allocation, and real-time loops that allocate only
- * at start-up.  It evaluates count dense matrices of one order n by the
- * leaf Ryser / Nijenhuis-Wilf kernel without allocating anything: no
- * cudaMalloc, no cudaFree, no allocating library call.
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot allocate device memory while they run: a host framework whose own
+ * allocator must own every device allocation (so the library may not call
+ * cudaMalloc behind its back), a latency-bound loop that may not allocate
+ * after start-up (cudaMalloc and cudaFree can synchronise the device and
+ * stall it), or a process working inside a fixed device-memory budget.  It
+ * evaluates count dense matrices of one order n by the leaf Ryser /
+ * Nijenhuis-Wilf kernel and allocates nothing: no cudaMalloc, no cudaFree,
+ * no allocating library call.
  *   a      device, count matrices of order n back to back, row-major int64
- *          (n*n entries each), |a_ij| < 2^30 and every row |sum| < 2^31
- *   n      1 <= n <= PERM_MAX_LEAF
+ *          (n*n entries each), |a_ij| < 2^30 and, for every row i,
+ *          sum_j |a_ij| < 2^31
+ *   n      1 <= n <= PERM_MAX_LEAF, else PERM_EINVAL
  *   count  1 <= count <= PERM_NOALLOC_MAX_COUNT, else PERM_EINVAL
  *   out    device, count*4 words: per(A_k) in 256-bit two's complement
  *   status device, count int32: PERM_OK, or PERM_EOVERFLOW (out set to 0)
- *          when an entry or row sum is out of range or the bound
- *          min(prod row |sums|, prod column |sums|) reaches 2^(254-n)
+ *          when an entry or a row's sum of |a_ij| is out of the range above,
+ *          or when the bound min(prod_i sum_j |a_ij|, prod_j sum_i |a_ij|)
+ *          exceeds 2^(254-n)
  *   stream cudaStream_t; the call only enqueues work and returns.
  * Working memory is one file-scope device array of PERM_NOALLOC_SCRATCH_BYTES
  * that every GPU which loads the library keeps until the process exits.

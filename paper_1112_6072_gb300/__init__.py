@@ -36,6 +36,7 @@ EXPORTED = [
     "perm_result_words", "perm_jobs_export", "perm_exact", "perm_job_features", "perm_mlp_grad",
     "perm_mlp_train", "perm_mlp_predict", "perm_mlp_attach", "perm_ubench_imad",
     "perm_status_string", "perm_last_error", "perm_leaf_batch_noalloc", "perm_eval_replay",
+    "perm_eval_subset", "perm_jobs_select",
 ]
 
 
@@ -101,6 +102,7 @@ def _lib():
         lib.perm_order.argtypes = [vp, ctypes.c_int32, P(ctypes.c_uint32)]
         lib.perm_eval_batch.argtypes = [vp, P(ctypes.c_uint32), P(perm_job_result)]
         lib.perm_eval_replay.argtypes = [vp, P(perm_job_result)]
+        lib.perm_eval_subset.argtypes = [vp, P(ctypes.c_uint32), ctypes.c_int64, P(perm_job_result)]
         lib.perm_last_eval_ms.argtypes = [vp, P(ctypes.c_float)]
         lib.perm_last_eval_launches.argtypes = [vp, P(ctypes.c_int32)]
         lib.perm_result.argtypes = [vp, ctypes.c_int32, P(ctypes.c_uint32), ctypes.c_int32,
@@ -111,6 +113,9 @@ def _lib():
                                          P(ctypes.c_uint64), P(ctypes.c_int32)]
         lib.perm_exact.argtypes = [P(perm_matrix), P(perm_opts), P(ctypes.c_uint32), ctypes.c_int32,
                                    P(ctypes.c_int32), P(ctypes.c_int32)]
+        lib.perm_jobs_select.argtypes = [vp, P(ctypes.c_int64), ctypes.c_int64, P(ctypes.c_int32),
+                                         P(ctypes.c_int64), ctypes.c_int64, P(ctypes.c_uint64),
+                                         P(ctypes.c_int32), P(ctypes.c_int64)]
         lib.perm_job_features.argtypes = [vp, P(ctypes.c_float)]
         f = P(ctypes.c_float)
         lib.perm_mlp_grad.argtypes = [f, f, f, ctypes.c_int32, vp, f, f]
@@ -349,6 +354,27 @@ class Plan:
         _ck(lib.perm_eval_batch(self._jobs, optr, res), "perm_eval_batch")
         return self._records(res, records)
 
+    def evaluate_subset(self, queue, records=False):
+        """Evaluate only the jobs in ``queue`` (distinct job indices, in that
+        order); ``results()`` then holds each matrix's sum over those jobs,
+        modulo 2^K (see ``result_bits``).  Disjoint sub-queues covering every
+        job sum to the permanents (one GPU each, Algorithm PH, Steps 3-4)."""
+        self._need_jobs()
+        qa = np.ascontiguousarray(queue, dtype=np.uint32).reshape(-1)
+        res = (perm_job_result * max(self.njobs, 1))() if records else None
+        _ck(_lib().perm_eval_subset(self._jobs, qa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), qa.size, res),
+            "perm_eval_subset")
+        return self._records(res, records)
+
+    def result_words(self) -> np.ndarray:
+        """Each matrix's result as four little-endian uint64 words (mod 2^256,
+        exact in its low result_bits(i) bits)."""
+        c = self._count
+        w = np.zeros(4 * c, dtype=np.uint64)
+        _ck(_lib().perm_result_words(self._h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), c),
+            "perm_result_words")
+        return w.reshape(c, 4)
+
     def replay(self, records=False):
         """Repeat the last evaluation as a captured CUDA graph."""
         res = (perm_job_result * max(self.njobs, 1))() if records else None
@@ -420,6 +446,44 @@ class Plan:
                                  coef.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                                  mid.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "perm_jobs_export")
         return sizes[:n].copy(), [_words_to_int(coef[4 * j:4 * j + 4]) for j in range(n)], mid[:n].copy()
+
+    def job_orders(self):
+        """(order, source matrix) of every job as two int32 arrays."""
+        self._need_jobs()
+        n = self.njobs
+        tot = ctypes.c_int64()
+        sizes = np.zeros(max(n, 1), dtype=np.int32)
+        mid = np.zeros(max(n, 1), dtype=np.int32)
+        _ck(_lib().perm_jobs_export(self._jobs, ctypes.byref(tot),
+                                    sizes.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), None, None,
+                                    mid.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "perm_jobs_export")
+        return sizes[:n].copy(), mid[:n].copy()
+
+    def jobs_select(self, idx):
+        """Chosen jobs as (matrix index, dense job, coefficient mod 2^256)."""
+        self._need_jobs()
+        lib = _lib()
+        ia = np.ascontiguousarray(idx, dtype=np.int64).reshape(-1)
+        k = ia.size
+        sizes = np.zeros(max(k, 1), dtype=np.int32)
+        coef = np.zeros(4 * max(k, 1), dtype=np.uint64)
+        mid = np.zeros(max(k, 1), dtype=np.int32)
+        ent = ctypes.c_int64()
+        ip = ia.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        _ck(lib.perm_jobs_select(self._jobs, ip, k, sizes.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), None, 0,
+                                 None, None, ctypes.byref(ent)), "perm_jobs_select")
+        mats = np.zeros(max(ent.value, 1), dtype=np.int64)
+        _ck(lib.perm_jobs_select(self._jobs, ip, k, sizes.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 mats.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ent.value,
+                                 coef.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                 mid.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(ent)),
+            "perm_jobs_select")
+        out, off = [], 0
+        for j in range(k):
+            m = int(sizes[j])
+            out.append((int(mid[j]), mats[off:off + m * m].reshape(m, m).copy(), _words_to_int(coef[4 * j:4 * j + 4])))
+            off += m * m
+        return out
 
     def jobs_export(self):
         """The job list as (matrix index, dense job, coefficient mod 2^256)."""
@@ -534,8 +598,9 @@ def ubench_imad(blocks=152 * 8, iters=4096, stream=None):
 
 def leaf_batch_noalloc(a_ptr, n, count, out_ptr, status_ptr, stream=None):
     """Allocation-free leaf batch (perm_leaf_batch_noalloc): for callers that
-    cannot allocate device memory while they run, e.g. while recording a CUDA
-    graph.  All pointers are device addresses the caller owns: ``count``
+    cannot allocate device memory while they run -- a host framework whose
+    allocator owns every device allocation, or a loop that may not allocate
+    after start-up.  All pointers are device addresses the caller owns: ``count``
     row-major int64 n x n matrices, ``count * 4`` uint64 result words (256-bit
     two's complement) and ``count`` int32 statuses.  The work is only
     enqueued on the stream; calls whose work overlaps on the GPU race on the

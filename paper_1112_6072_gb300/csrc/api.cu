@@ -230,6 +230,7 @@ static inline int dfs_group_tile(int g) { return g >= 2 ? 32 : 64; }
 static inline int dfs_group_w(int g) { return (g & 1) ? 4 : 2; }
 
 struct EvalState {
+  int64_t nq = 0;  // queue length (all jobs, or the subset given)
   int64_t nl = 0, nd = 0;
   int64_t db[EVAL_DFS_GROUPS + 1] = {0, 0, 0, 0, 0};  // depth-first group bounds in d_dq
   std::vector<std::pair<int64_t, int64_t>> groups;  // (offset, count) in the grouped leaf queue
@@ -323,6 +324,7 @@ struct perm_plan {
   float last_ms = 0.f;
   int32_t last_launches = 0;
   bool evaluated = false;
+  bool subset = false;  // the last evaluation covered a sub-queue (perm_eval_subset)
   std::vector<float> mlp;
 };
 
@@ -991,24 +993,30 @@ static int dfs_wps(const perm_plan* P, int tile) {
   return tile <= 32 ? 24 : 10;
 }
 
-static perm_status eval_prepare(perm_jobs* J, const uint32_t* order) {
+// order: the queue (nq distinct job indices), or NULL for the order set by
+// perm_order (every job).  Jobs outside the queue are not evaluated: their
+// records stay zero and they add nothing to the sums.
+static perm_status eval_prepare(perm_jobs* J, const uint32_t* order, int64_t nq_in) {
   perm_plan* P = J->plan;
   cudaStream_t s = P->s;
   Mem& M = P->M;
-  const int64_t n = J->n;
+  const int64_t nj = J->n;
   const int leaf_max = std::max(P->L, 2);
   if (J->max_order > leaf_max && J->max_order > PERM_MAX_JOB_N) return PERM_EINVAL;
+  if (order && (nq_in < 0 || nq_in > nj)) return PERM_EINVAL;
+  const int64_t n = order ? nq_in : nj;  // queue length
   free_eval(M, J);
   J->ev = new EvalState();
   EvalState& E = *J->ev;
+  E.nq = n;
   E.d_q = dget<uint32_t>(M, n);
   E.sum = dget<unsigned long long>(M, SUM_WORDS);
   E.ctr = dget<unsigned long long>(M, 1 + EVAL_DFS_GROUPS);
   if (!E.d_q || !E.sum || !E.ctr) return PERM_ENOMEM;
   if (order) {
-    std::vector<uint8_t> seen(n, 0);
+    std::vector<uint8_t> seen(nj, 0);
     for (int64_t k = 0; k < n; ++k) {
-      if (order[k] >= (uint64_t)n || seen[order[k]]) return PERM_EINVAL;
+      if (order[k] >= (uint64_t)nj || seen[order[k]]) return PERM_EINVAL;
       seen[order[k]] = 1;
     }
     if (n) CK(cudaMemcpyAsync(E.d_q, order, 4 * n, cudaMemcpyHostToDevice, s));
@@ -1064,8 +1072,13 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order) {
   E.wide_first = P->L > 16;
   E.chunk = P->opts.chunk_log2 > 0 ? P->opts.chunk_log2 : 10;
   uint64_t leaf_tasks = 0;
-  for (int64_t j = 0; j < n; ++j)
-    if (J->h_m[j] <= leaf_max) leaf_tasks += leaf_tasks_host(J->h_m[j], E.chunk);
+  if (order) {
+    for (int64_t k = 0; k < n; ++k)
+      if (J->h_m[order[k]] <= leaf_max) leaf_tasks += leaf_tasks_host(J->h_m[order[k]], E.chunk);
+  } else {
+    for (int64_t j = 0; j < n; ++j)
+      if (J->h_m[j] <= leaf_max) leaf_tasks += leaf_tasks_host(J->h_m[j], E.chunk);
+  }
   E.owner = dget<uint32_t>(M, (int64_t)std::max<uint64_t>(leaf_tasks, 1));
   int dfs_warps = 0, max_tile = 32;
   for (int g = 0; g < EVAL_DFS_GROUPS; ++g) {
@@ -1219,10 +1232,10 @@ static perm_status eval_finish(perm_jobs* J, perm_job_result* results) {
     CK(cudaMemcpyAsync(st.data(), J->out.status, 4 * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(mat.data(), J->a.mat, 4 * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(nnz.data(), J->a.nnz, 4 * n, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(q.data(), E.d_q, 4 * n, cudaMemcpyDeviceToHost, s));
+    if (E.nq) CK(cudaMemcpyAsync(q.data(), E.d_q, 4 * E.nq, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    std::vector<int32_t> qpos(n);
-    for (int64_t k = 0; k < n; ++k) qpos[q[k]] = (int32_t)k;
+    std::vector<int32_t> qpos(n, -1);
+    for (int64_t k = 0; k < E.nq; ++k) qpos[q[k]] = (int32_t)k;
     for (int64_t j = 0; j < n; ++j) {
       perm_job_result& r = results[j];
       r.matrix = mat[j];
@@ -1244,10 +1257,10 @@ static perm_status eval_finish(perm_jobs* J, perm_job_result* results) {
   return PERM_OK;
 }
 
-static perm_status perm_eval_batch_impl(perm_jobs_t* J, const uint32_t* order, perm_job_result* results) {
+static perm_status eval_run(perm_jobs_t* J, const uint32_t* order, int64_t count, perm_job_result* results) {
   if (!J) return PERM_EINVAL;
   perm_plan* P = J->plan;
-  perm_status st = eval_prepare(J, order);
+  perm_status st = eval_prepare(J, order, count);
   if (st != PERM_OK) return st;
   CK(cudaEventRecord(P->ev0, P->s));
   CK(eval_enqueue(J, P->s));
@@ -1255,7 +1268,20 @@ static perm_status perm_eval_batch_impl(perm_jobs_t* J, const uint32_t* order, p
   return eval_finish(J, results);
 }
 extern "C" perm_status perm_eval_batch(perm_jobs_t* J, const uint32_t* order, perm_job_result* results) {
-  return guarded([&] { return perm_eval_batch_impl(J, order, results); });
+  return guarded([&] {
+    if (J) J->plan->subset = false;
+    return eval_run(J, order, J ? J->n : 0, results);
+  });
+}
+
+extern "C" perm_status perm_eval_subset(perm_jobs_t* J, const uint32_t* queue, int64_t count,
+                                        perm_job_result* results) {
+  if (!J || (!queue && count > 0)) return PERM_EINVAL;
+  static const uint32_t none = 0;
+  return guarded([&] {
+    J->plan->subset = true;
+    return eval_run(J, queue ? queue : &none, count, results);
+  });
 }
 
 static perm_status perm_eval_replay_impl(perm_jobs_t* J, perm_job_result* results) {
@@ -1326,6 +1352,7 @@ static perm_status result_words(perm_plan* P, std::vector<uint64_t>& words) {
     uint64_t* o = &words[4ull * i];
     if (P->trivial[i] == 1) continue;
     if (P->trivial[i] == 2) {
+      if (P->subset) continue;  // a sub-queue sum: the matrix has no job
       o[0] = 1;
       continue;
     }
@@ -1430,6 +1457,55 @@ static perm_status perm_jobs_export_impl(perm_jobs_t* J, int64_t* total_entries,
 extern "C" perm_status perm_jobs_export(perm_jobs_t* J, int64_t* total_entries, int32_t* sizes, int64_t* mats,
                                         uint64_t* coef, int32_t* matrix) {
   return guarded([&] { return perm_jobs_export_impl(J, total_entries, sizes, mats, coef, matrix); });
+}
+
+static perm_status perm_jobs_select_impl(perm_jobs_t* J, const int64_t* idx, int64_t count, int32_t* sizes,
+                                         int64_t* mats, int64_t mats_cap, uint64_t* coef, int32_t* matrix,
+                                         int64_t* entries) {
+  if (!J || count < 0 || (count > 0 && (!idx || !sizes)) || !entries) return PERM_EINVAL;
+  perm_plan* P = J->plan;
+  int64_t tot = 0;
+  for (int64_t k = 0; k < count; ++k) {
+    if (idx[k] < 0 || idx[k] >= J->n) return PERM_EINVAL;
+    sizes[k] = J->h_m[idx[k]];
+    tot += (int64_t)sizes[k] * sizes[k];
+  }
+  *entries = tot;
+  if (mats && mats_cap < tot) return PERM_ESHORTBUF;
+  int64_t o = 0;
+  for (int64_t k = 0; k < count; ++k) {
+    const int64_t j = idx[k];
+    const int m = sizes[k];
+    int64_t off = 0;
+    int32_t nnz = 0, mat = 0;
+    uint64_t cf[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(&off, J->a.off + j, 8, cudaMemcpyDeviceToHost, P->s));
+    CK(cudaMemcpyAsync(&nnz, J->a.nnz + j, 4, cudaMemcpyDeviceToHost, P->s));
+    CK(cudaMemcpyAsync(&mat, J->a.mat + j, 4, cudaMemcpyDeviceToHost, P->s));
+    CK(cudaMemcpyAsync(cf, J->a.coef + 4 * j, 32, cudaMemcpyDeviceToHost, P->s));
+    CK(cudaStreamSynchronize(P->s));
+    if (mats) {
+      const int64_t bw = blk_words(m, nnz);
+      std::vector<uint64_t> blk((size_t)std::max<int64_t>(bw, 1));
+      CK(cudaMemcpyAsync(blk.data(), J->arena + off, 8 * bw, cudaMemcpyDeviceToHost, P->s));
+      CK(cudaStreamSynchronize(P->s));
+      int64_t* d = mats + o;
+      for (int64_t e = 0; e < (int64_t)m * m; ++e) d[e] = 0;
+      CsrView v = csr_view(blk.data(), 0, m, nnz);
+      for (int r = 0; r < m; ++r)
+        for (int q = v.rowptr[r]; q < v.rowptr[r + 1]; ++q) d[(int64_t)r * m + v.col[q]] = v.val[q];
+    }
+    o += (int64_t)m * m;
+    if (coef)
+      for (int w = 0; w < 4; ++w) coef[4 * k + w] = cf[w];
+    if (matrix) matrix[k] = mat;
+  }
+  return PERM_OK;
+}
+extern "C" perm_status perm_jobs_select(perm_jobs_t* J, const int64_t* idx, int64_t count, int32_t* sizes,
+                                        int64_t* mats, int64_t mats_cap, uint64_t* coef, int32_t* matrix,
+                                        int64_t* entries) {
+  return guarded([&] { return perm_jobs_select_impl(J, idx, count, sizes, mats, mats_cap, coef, matrix, entries); });
 }
 
 static perm_status perm_exact_impl(const perm_matrix* a, const perm_opts* opts, uint32_t* limbs, int32_t cap,

@@ -1,8 +1,9 @@
 // Allocation-free variant of the leaf batch (perm_leaf_batch_noalloc).
 //
-// For callers that must not allocate device memory while they run -- code
-// recording a CUDA graph, a host framework whose allocator must own every
-// allocation, or a real-time loop that forbids allocation after start-up.
+// For callers that must not allocate device memory while they run -- a host
+// framework whose allocator must own every allocation, a latency-bound loop
+// that forbids allocation after start-up (cudaMalloc and cudaFree can
+// synchronise the device), or a process held to a fixed memory budget.
 // The caller passes device inputs and outputs; the only other device memory
 // the call touches is the file-scope array below, which every GPU that
 // loads the library holds until the process exits.
@@ -119,8 +120,10 @@ __global__ void __launch_bounds__(NA_WARPS * 32)
 }
 
 // Sigma -> per = (-1)^(n-1) Sigma / 2^(n-1), exact in its low 257 - n bits;
-// sign-extended from there.  The bound min(prod row |sums|, prod column
-// |sums|) must stay below 2^(255 - n), else the status is PERM_EOVERFLOW.
+// sign-extended from there.  The bound min(prod_i sum_j |a_ij|,
+// prod_j sum_i |a_ij|) must not exceed 2^(254 - n) (checked in fp64 with one
+// bit of margin: log2 bound + 1 > 255 - n fails), else the status is
+// PERM_EOVERFLOW.
 __global__ void k_na_finalize(const int64_t* __restrict__ a, int n, int count, const NoAllocScratch* sc,
                               uint64_t* __restrict__ out, int32_t* __restrict__ status) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
