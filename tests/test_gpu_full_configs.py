@@ -79,14 +79,16 @@ def test_mixed_batch_full_size():
         sums = matrix_sums(rec["value"], rec["matrix"], len(mats))
         for i in range(len(mats)):
             assert signed_low(sums[i], bits[i]) == got[i], i
-        # 20 sampled jobs of 10 members, one by one against the oracle
+        # 20 sampled jobs of 10 members (members split into at least two
+        # jobs), one by one against the oracle
         _, mid = p.job_orders()
+        per_member = np.bincount(mid, minlength=len(mats))
         rng = np.random.default_rng(55)
         pick = []
-        for i in rng.choice(len(mats), size=10, replace=False):
+        for i in rng.choice(np.flatnonzero(per_member >= 2), size=10, replace=False):
             idx = np.flatnonzero(mid == i)
-            pick += [int(j) for j in rng.choice(idx, size=min(2, idx.size), replace=False)]
-        assert len(pick) >= 20
+            pick += [int(j) for j in rng.choice(idx, size=2, replace=False)]
+        assert len(pick) == 20
 
         def val(j):
             w = rec["value"][j]
@@ -128,8 +130,10 @@ def _t12():
         for line in f:
             if line.startswith("#") or not line.strip():
                 continue
-            vals.append([int(x) for x in line.split()])
-    return [v for _, v in vals[:-1]], vals[-1][-1]
+            vals.append(line.split())
+    subs = [int(v) for k, v in vals if k != "total"]
+    total = [int(v) for k, v in vals if k == "total"]
+    return subs, total[0]
 
 
 def test_c100_equals_table_t12_total():

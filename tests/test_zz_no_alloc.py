@@ -53,7 +53,7 @@ def run_noalloc(mats, n, calls=2):
 
 
 @pytest.mark.parametrize("n,count,kind", [(14, 96, "leaf"), (20, 12, "leaf"), (9, 200, "signed"),
-                                          (1, 50, "signed"), (24, 3, "leaf"), (30, 2, "ones")])
+                                          (1, 50, "signed"), (24, 1, "leaf"), (30, 2, "ones")])
 def test_noalloc_matches_oracle_and_planned_path_twice(n, count, kind):
     """Orders 1 (no Gray walk), 9, 14 and 20, 24 (the 24-row register
     width) and 30 (the 32-row width, every entry 1: per = 30!)."""
