@@ -104,6 +104,14 @@ typedef struct {
                               is a leaf (Ryser).  1 = such a node is split by Eq. 2 with all three
                               children: merge(j1, j2), merge(j3, j4), and the node with the pivot
                               line's entries at j1..j4 cleared (same order) */
+  int32_t expand_walk;     /* expansion driver: 1 = a traversal in which warps walk the tree depth
+                              first and hand nodes to idle warps, writing only the jobs, which a
+                              sort of their child-index paths puts in natural order (used when
+                              every root block fits its shared-memory buffers, with a fixed depth,
+                              or with the automatic depth for roots of one order without the
+                              three-child split; otherwise, or when its buffers fill, the
+                              level-by-level driver runs); 0 = level by level.  The job list is the
+                              same either way */
 } perm_opts;
 
 /* Fill opts with the defaults above. */
@@ -146,6 +154,11 @@ void perm_plan_destroy(perm_plan_t* plan);
  * *jobs stays owned by the plan (one job set per plan; a second call
  * replaces it).  *njobs receives the job count. */
 perm_status perm_expand(perm_plan_t* plan, perm_jobs_t** jobs, int64_t* njobs);
+
+/* Which driver built the plan's job set: 0 = level by level (one launch
+ * sequence per level), 1 = consecutive levels per cooperative launch,
+ * 2 = the traversal (opts.expand_walk).  PERM_ESTATE before perm_expand. */
+perm_status perm_expand_driver(perm_plan_t* plan, int32_t* driver);
 
 /* a4 -- Algorithm KKLLL (Section 2.3) on each job's 0/1 pattern (Section 3),
  * jobs of any order up to PERM_MAX_N:

@@ -36,7 +36,7 @@ EXPORTED = [
     "perm_result_words", "perm_jobs_export", "perm_exact", "perm_job_features", "perm_mlp_grad",
     "perm_mlp_train", "perm_mlp_predict", "perm_mlp_attach", "perm_ubench_imad",
     "perm_status_string", "perm_last_error", "perm_leaf_batch_noalloc", "perm_eval_replay",
-    "perm_eval_subset", "perm_jobs_select",
+    "perm_eval_subset", "perm_jobs_select", "perm_expand_driver",
 ]
 
 
@@ -71,7 +71,7 @@ class perm_opts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("alloc", alloc_fn_t), ("free", free_fn_t),
                 ("alloc_ctx", ctypes.c_void_p), ("timeout_ns", ctypes.c_int64),
                 ("model_uses_estimate", ctypes.c_int32), ("fused_levels", ctypes.c_int32),
-                ("dense_split", ctypes.c_int32)]
+                ("dense_split", ctypes.c_int32), ("expand_walk", ctypes.c_int32)]
 
 
 class perm_job_result(ctypes.Structure):
@@ -99,6 +99,7 @@ def _lib():
         lib.perm_plan_destroy.restype = None
         lib.perm_expand.argtypes = [vp, P(vp), P(ctypes.c_int64)]
         lib.perm_estimate.argtypes = [vp, P(ctypes.c_float)]
+        lib.perm_expand_driver.argtypes = [vp, P(ctypes.c_int32)]
         lib.perm_order.argtypes = [vp, ctypes.c_int32, P(ctypes.c_uint32)]
         lib.perm_eval_batch.argtypes = [vp, P(ctypes.c_uint32), P(perm_job_result)]
         lib.perm_eval_replay.argtypes = [vp, P(perm_job_result)]
@@ -265,7 +266,7 @@ class Plan:
 
     def _create(self, desc, keep, split_depth=-1, leaf_size=0, order="lpt", kklll_trials=0, seed=0x5EED,
                 workers_per_sm=0, chunk_log2=0, stream=None, torch_allocator=False, timeout_ns=0,
-                model_uses_estimate=True, fused_levels=True, dense_split=False):
+                model_uses_estimate=True, fused_levels=True, dense_split=False, expand_walk=True):
         lib = _lib()
         self._h = None
         self._keep = keep  # the host matrices the descriptors point into
@@ -286,6 +287,7 @@ class Plan:
         o.model_uses_estimate = 1 if model_uses_estimate else 0
         o.fused_levels = 1 if fused_levels else 0
         o.dense_split = 1 if dense_split else 0
+        o.expand_walk = 1 if expand_walk else 0
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator()
@@ -307,6 +309,13 @@ class Plan:
         self._jobs = j
         self.njobs = n.value
         return self.njobs
+
+    @property
+    def expand_driver(self) -> str:
+        """Driver of the last expansion: "levels", "fused" or "walk"."""
+        v = ctypes.c_int32()
+        _ck(_lib().perm_expand_driver(self._h, ctypes.byref(v)), "perm_expand_driver")
+        return ("levels", "fused", "walk")[v.value]
 
     def _need_jobs(self):
         if self._jobs is None:

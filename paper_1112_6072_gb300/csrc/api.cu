@@ -75,6 +75,7 @@ extern "C" void perm_opts_default(perm_opts* o) {
   o->model_uses_estimate = 1;
   o->fused_levels = 1;
   o->dense_split = 0;
+  o->expand_walk = 1;
 }
 
 // ---------------------------------------------------------------- memory
@@ -325,6 +326,7 @@ struct perm_plan {
   int32_t last_launches = 0;
   bool evaluated = false;
   bool subset = false;  // the last evaluation covered a sub-queue (perm_eval_subset)
+  int32_t expand_driver = -1;  // driver of the last expansion: 0 levels, 1 fused levels, 2 traversal
   std::vector<float> mlp;
 };
 
@@ -593,6 +595,228 @@ static const int64_t kFusedWords0 = 1ll << 23;
 static const int64_t kFusedMaxJobs = 1ll << 20;
 static const int64_t kFusedMaxWords = 1ll << 26;
 
+static perm_status finish_jobset(perm_plan* P, perm_jobs* J, perm_jobs_t** jobs_out, int64_t* njobs);
+
+// ---- a3 by the traversal driver (walk.cu) --------------------------------------
+// jobs per traversal (outputs and queue slots) with a fixed depth
+static const int64_t kWalkJobs = 1ll << 19;
+// output slots a warp of the traversal reserves at a time (walk.cu)
+static const int64_t kWalkOutChunk = 16;
+
+struct WalkRoots {
+  std::vector<int32_t> m, nnz, mat, dl;
+  std::vector<int64_t> off;
+};
+
+// Expand the roots by the traversal.  done = false (and PERM_OK) when it does
+// not apply or its buffers filled: the caller then runs the level-by-level
+// driver.  levels_left replays the automatic depth rule from the per-depth
+// counts; with the automatic depth the traversal runs to the end of the tree
+// and is accepted when the rule reaches that depth, else it runs again with
+// the depth the rule stops at.
+template <class LevelsLeft>
+static perm_status expand_by_walk(perm_plan* P, perm_jobs* J, WalkRoots R, int maxd, int max_open0, bool adaptive,
+                                  int64_t target, LevelsLeft levels_left, bool& done) {
+  done = false;
+  Mem& M = P->M;
+  cudaStream_t s = P->s;
+  const int64_t nroots = (int64_t)R.m.size();
+  const int K = P->opts.dense_split ? 3 : 2;
+  const int bpl = K == 3 ? 2 : 1;
+  int maxn = 0, minn = 1 << 30;
+  int64_t sw = 2;
+  for (int64_t r = 0; r < nroots; ++r) {
+    maxn = std::max(maxn, R.m[r]);
+    minn = std::min(minn, R.m[r]);
+    sw = std::max<int64_t>(sw, blk_words(R.m[r], R.nnz[r]));
+  }
+  // the automatic depth's waiting band only matters for roots of several orders (or Eq. 2's third child)
+  if (nroots == 0 || (adaptive && (K == 3 || minn != maxn))) return PERM_OK;
+  int rbits = 0;
+  while ((1ll << rbits) < nroots) ++rbits;
+  const int key_bits = rbits + bpl * maxd;
+  if (key_bits > 127) return PERM_OK;
+  const int hist_len = maxd + 1;
+  const int tile = walk_tile_for(maxn);
+  if (tile == 0) return PERM_OK;
+  int64_t warps = 0;
+  CK(walk_resident_warps(tile, hist_len, P->sms, &warps));
+  if (warps <= 0) return PERM_OK;
+  const int frames = std::max(1, maxd);
+  const int64_t hw = (int64_t)P->h_arena.size();
+  // jobs, plus the slots a warp may leave unused in its last reserved chunk
+  // (at most 64 resident warps per SM)
+  const int64_t jobs_cap = adaptive ? 2 * target : kWalkJobs;
+  const int64_t cap = jobs_cap + (int64_t)P->sms * 64 * kWalkOutChunk;
+  const int64_t chunk = std::max<int64_t>(256, 2 * sw);
+  // blocks: every job's and every handed-over node's, plus each warp's last chunk
+  const int64_t cap_words =
+      ((hw + 1) & ~1ll) + jobs_cap * std::max<int64_t>(96, sw / 2) + (int64_t)P->sms * 64 * chunk;
+  // device buffers
+  WalkArgs A{};
+  A.q_m = dget<int32_t>(M, cap);
+  A.q_nnz = dget<int32_t>(M, cap);
+  A.q_mat = dget<int32_t>(M, cap);
+  A.q_dl = dget<int32_t>(M, cap);
+  A.q_depth = dget<int32_t>(M, cap);
+  A.q_off = dget<int64_t>(M, cap);
+  A.q_coef = dget<uint64_t>(M, 4 * cap);
+  A.q_key = dget<uint64_t>(M, 2 * cap);
+  A.q_ready = dget<int32_t>(M, cap);
+  JobArrays out{};
+  const bool out_ok = alloc_jobs(M, out, cap);
+  uint64_t* out_key = dget<uint64_t>(M, 2 * cap);
+  uint64_t* arena = dget<uint64_t>(M, cap_words);
+  unsigned long long* ctr = dget<unsigned long long>(M, 8);
+  int64_t* undo = dget<int64_t>(M, warps * frames * walk_frame_words(tile));
+  unsigned long long* hist = dget<unsigned long long>(M, 2 * hist_len);
+  int32_t* hmo = dget<int32_t>(M, hist_len);
+  auto release = [&](bool keep_arena) {
+    for (void* p : {(void*)A.q_m, (void*)A.q_nnz, (void*)A.q_mat, (void*)A.q_dl, (void*)A.q_depth, (void*)A.q_off,
+                    (void*)A.q_coef, (void*)A.q_key, (void*)A.q_ready, (void*)out_key, (void*)ctr, (void*)hist,
+                    (void*)hmo, (void*)undo})
+      M.put(p);
+    free_jobs(M, out);
+    if (!keep_arena) M.put(arena);
+  };
+  if (!A.q_m || !A.q_nnz || !A.q_mat || !A.q_dl || !A.q_depth || !A.q_off || !A.q_coef || !A.q_key || !A.q_ready ||
+      !out_ok || !out_key || !arena || !ctr || !hist || !hmo || !undo) {
+    release(false);
+    return PERM_OK;  // too large for the traversal's buffers: the level-by-level driver grows its own
+  }
+  A.cap_q = cap;
+  A.q_head = ctr + 0;
+  A.q_tail = ctr + 1;
+  A.outstanding = ctr + 2;
+  A.arena_used = ctr + 3;
+  A.out_used = ctr + 4;
+  A.emitted = ctr + 5;
+  A.err = reinterpret_cast<int32_t*>(ctr + 6);
+  A.arena = arena;
+  A.cap_words = cap_words;
+  A.arena_chunk = chunk;
+  A.out = out;
+  A.out_key = out_key;
+  A.cap_out = cap;
+  A.hist_nodes = hist;
+  A.hist_term = hist + hist_len;
+  A.hist_maxopen = hmo;
+  A.hist_len = hist_len;
+  A.leaf_size = P->L;
+  A.kslots = K;
+  A.bits_per_level = bpl;
+  A.key_levels = maxd;
+  A.undo = undo;
+  A.undo_words_per_warp = (int64_t)frames * walk_frame_words(tile);
+  A.max_rel_depth = frames;
+  A.warps_cap = warps;
+  // an idle warp waits for the others' remaining work: at least a second,
+  // whatever the evaluation watchdog
+  A.timeout_ns = std::max<int64_t>(P->opts.timeout_ns > 0 ? P->opts.timeout_ns : 10000000000ll, 1000000000ll);
+  // roots: blocks back to back at the start of the arena, queue slots [0, nroots)
+  std::vector<uint64_t> coef(4 * nroots, 0ull), key(2 * nroots, 0ull);
+  std::vector<int32_t> depth0(nroots, 0), ones(nroots, 1);
+  for (int64_t r = 0; r < nroots; ++r) {
+    coef[4 * r] = 1;
+    const u128 k = (u128)r << (bpl * maxd);
+    key[2 * r] = (uint64_t)k;
+    key[2 * r + 1] = (uint64_t)(k >> 64);
+  }
+  CK(cudaMemcpyAsync(arena, P->h_arena.data(), 8 * hw, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(A.q_m, R.m.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(A.q_nnz, R.nnz.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(A.q_mat, R.mat.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(A.q_depth, depth0.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(A.q_off, R.off.data(), 8 * nroots, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(A.q_coef, coef.data(), 32 * nroots, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(A.q_key, key.data(), 16 * nroots, cudaMemcpyHostToDevice, s));
+  bool fixed_rerun = false;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    CK(cudaMemcpyAsync(A.q_dl, R.dl.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(A.q_ready, 0, 4 * (size_t)cap, s));
+    CK(cudaMemcpyAsync(A.q_ready, ones.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(out_key, 0xff, 16 * (size_t)cap, s));
+    CK(cudaMemsetAsync(hist, 0, 16 * (size_t)hist_len, s));
+    CK(cudaMemsetAsync(hmo, 0, 4 * (size_t)hist_len, s));
+    unsigned long long c0[8] = {0, (unsigned long long)nroots, (unsigned long long)nroots,
+                                (unsigned long long)((hw + 1) & ~1ll), 0, 0, 0, 0};
+    CK(cudaMemcpyAsync(ctr, c0, sizeof(c0), cudaMemcpyHostToDevice, s));
+    int grid = 0;
+    CK(launch_expand_walk(A, tile, P->sms, &grid, s));
+    unsigned long long c1[8];
+    std::vector<unsigned long long> hh(2 * hist_len);
+    std::vector<int32_t> hm(hist_len);
+    CK(cudaMemcpyAsync(c1, ctr, sizeof(c1), cudaMemcpyDeviceToHost, s));
+    if (adaptive && !fixed_rerun) {
+      CK(cudaMemcpyAsync(hh.data(), hist, 16 * hist_len, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hm.data(), hmo, 4 * hist_len, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    const int32_t err = (int32_t)(c1[6] & 0xffffffffu);
+    if (grid == 0 || err == WALK_FULL) {
+      release(false);
+      return PERM_OK;
+    }
+    if (err != 0) {
+      release(false);
+      return (perm_status)err;
+    }
+    if (adaptive && !fixed_rerun) {
+      // replay the automatic depth rule on the per-depth counts
+      int64_t count = nroots, tcum = 0;
+      int mopen = max_open0, D = 0;
+      for (int level = 0;; ++level) {
+        if (!levels_left(level, count, mopen) || level >= maxd) {
+          D = level;
+          break;
+        }
+        tcum += (int64_t)hh[hist_len + level];
+        count = tcum + (int64_t)hh[level + 1];
+        mopen = hm[level + 1];
+      }
+      if (hh[D] != hh[hist_len + D]) {
+        // the rule stops above the end of the tree: the cut at depth D, as a fixed depth
+        for (int64_t r = 0; r < nroots; ++r) R.dl[r] = D;
+        fixed_rerun = true;
+        continue;
+      }
+    }
+    // the jobs in path-key order
+    const int64_t used = (int64_t)c1[4] < cap ? (int64_t)c1[4] : cap;
+    const int64_t nj = (int64_t)c1[5];
+    uint64_t* kb = dget<uint64_t>(M, 2 * std::max<int64_t>(used, 1));
+    uint32_t* ib = dget<uint32_t>(M, 2 * std::max<int64_t>(used, 1));
+    const size_t tb = sort_tmp_bytes_u64(std::max<int64_t>(used, 1));
+    void* tmp = M.get(tb);
+    JobArrays fin{};
+    const bool fin_ok = alloc_jobs(M, fin, std::max<int64_t>(nj, 1));
+    if (!kb || !ib || !tmp || !fin_ok) {
+      M.put(kb);
+      M.put(ib);
+      M.put(tmp);
+      free_jobs(M, fin);
+      release(false);
+      return PERM_ENOMEM;
+    }
+    CK(launch_walk_order(out_key, used, key_bits, kb, kb + used, ib, ib + used, tmp, tb, s));
+    CK(launch_walk_gather(ib + used, nj, out, fin, s));
+    CK(cudaStreamSynchronize(s));
+    M.put(kb);
+    M.put(ib);
+    M.put(tmp);
+    release(true);
+    J->n = nj;
+    J->a = fin;
+    J->arena = arena;
+    J->arena_words = (int64_t)std::min<unsigned long long>(c1[3], (unsigned long long)cap_words);
+    P->expand_driver = 2;
+    done = true;
+    return PERM_OK;
+  }
+  release(false);
+  return PERM_OK;
+}
+
 static perm_status perm_expand_impl(perm_plan_t* P, perm_jobs_t** jobs_out, int64_t* njobs) {
   if (!P) return PERM_EINVAL;
   free_jobset(P);
@@ -625,6 +849,27 @@ static perm_status perm_expand_impl(perm_plan_t* P, perm_jobs_t** jobs_out, int6
   perm_jobs* J = new perm_jobs();
   J->plan = P;
   P->jobs = J;
+  // about 2^17 jobs per matrix, at most 2^21 for a batch (enough queue for
+  // every worker many times over)
+  const int64_t target = kTargetJobs * std::min<int64_t>(16, std::max<int64_t>(1, nroots));
+  // automatic depth: split while a job still to split is above
+  // PERM_MAX_JOB_N, or above kSoftOrder while the jobs number fewer than
+  // kSoftCapJobs, or while there are fewer jobs than the target; each
+  // level splits only the jobs within kSplitBand orders of the largest one
+  // still to split (the largest jobs first, so the matrices of a batch end
+  // with jobs of similar order), the others wait
+  auto levels_left = [&](int level, int64_t n, int mopen) {
+    if (level >= maxd || n <= 0) return false;
+    if (!adaptive) return true;
+    return mopen > PERM_MAX_JOB_N || (mopen > kSoftOrder && n < kSoftCapJobs) || (n < target && mopen > 0);
+  };
+  if (P->opts.expand_walk && nroots > 0) {
+    WalkRoots WR{rm, rnnz, rmat, rdl, roff};
+    bool done = false;
+    const perm_status st = expand_by_walk(P, J, WR, maxd, max_open, adaptive, target, levels_left, done);
+    if (st != PERM_OK) return st;
+    if (done) return finish_jobset(P, J, jobs_out, njobs);
+  }
   // ping-pong job arrays and arenas, grown geometrically and reused across levels
   JobBuf jb[2];
   Grow ar[2], g_words, g_base, g_valid, g_pos, g_tmp;
@@ -656,25 +901,13 @@ static perm_status perm_expand_impl(perm_plan_t* P, perm_jobs_t** jobs_out, int6
   int max_order = maxn;
   int64_t cur_arena_words = (int64_t)P->h_arena.size();  // roots sit back to back
   int64_t used_words = cur_arena_words;                    // words of the current jobs' blocks
-  // about 2^17 jobs per matrix, at most 2^21 for a batch (enough queue for
-  // every worker many times over)
-  const int64_t target = kTargetJobs * std::min<int64_t>(16, std::max<int64_t>(1, nroots));
-  // automatic depth: split while a job still to split is above
-  // PERM_MAX_JOB_N, or above kSoftOrder while the jobs number fewer than
-  // kSoftCapJobs, or while there are fewer jobs than the target; each
-  // level splits only the jobs within kSplitBand orders of the largest one
-  // still to split (the largest jobs first, so the matrices of a batch end
-  // with jobs of similar order), the others wait
-  auto levels_left = [&](int level, int64_t n, int mopen) {
-    if (level >= maxd || n <= 0) return false;
-    if (!adaptive) return true;
-    return mopen > PERM_MAX_JOB_N || (mopen > kSoftOrder && n < kSoftCapJobs) || (n < target && mopen > 0);
-  };
   auto split_floor = [&](int mopen) { return adaptive ? mopen - kSplitBand : 0; };
   // child slots per parent: Eq. 2's third child needs a third slot
   const int K = P->opts.dense_split ? 3 : 2;
   int level0 = 0;
+  bool used_fused = false;
   if (P->opts.fused_levels && levels_left(0, ncur, max_open)) {
+    used_fused = true;
     // consecutive levels in one cooperative launch; buffers start small and
     // grow by 4x (the current level copied over) when the frontier outgrows
     // them, up to kFusedMaxJobs / kFusedMaxWords
@@ -826,6 +1059,7 @@ static perm_status perm_expand_impl(perm_plan_t* P, perm_jobs_t** jobs_out, int6
     max_open = (int)st[4];
   }
   M.put(d_stat);
+  P->expand_driver = used_fused ? 1 : 0;
   // the current buffers become the job set; the rest is released
   J->n = ncur;
   J->a = jb[cb].view();
@@ -841,6 +1075,15 @@ static perm_status perm_expand_impl(perm_plan_t* P, perm_jobs_t** jobs_out, int6
   M.put(g_valid.p);
   M.put(g_pos.p);
   M.put(g_tmp.p);
+  return finish_jobset(P, J, jobs_out, njobs);
+}
+
+// The job set's host copies of orders and matrices, and its output arrays.
+static perm_status finish_jobset(perm_plan* P, perm_jobs* J, perm_jobs_t** jobs_out, int64_t* njobs) {
+  Mem& M = P->M;
+  cudaStream_t s = P->s;
+  const int64_t ncur = J->n;
+  const JobArrays cur = J->a;
   J->h_m.resize(ncur);
   J->h_mat.resize(ncur);
   if (ncur > 0) {
@@ -870,6 +1113,16 @@ static perm_status perm_expand_impl(perm_plan_t* P, perm_jobs_t** jobs_out, int6
 }
 extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64_t* njobs) {
   return guarded([&] { return perm_expand_impl(P, jobs_out, njobs); });
+}
+
+static perm_status perm_expand_driver_impl(perm_plan_t* P, int32_t* driver) {
+  if (!P || !driver) return PERM_EINVAL;
+  if (P->expand_driver < 0) return PERM_ESTATE;
+  *driver = P->expand_driver;
+  return PERM_OK;
+}
+extern "C" perm_status perm_expand_driver(perm_plan_t* P, int32_t* driver) {
+  return guarded([&] { return perm_expand_driver_impl(P, driver); });
 }
 
 // ---------------------------------------------------------------- a4: estimate

@@ -31,6 +31,10 @@ size_t scan_tmp_bytes_i32(int64_t n);
 cudaError_t sort_desc_f32(const float* keys_in, float* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
                           int64_t n, void* tmp, size_t tmp_bytes, cudaStream_t s);
 size_t sort_tmp_bytes_f32(int64_t n);
+// Stable sort of (key, value) pairs by ascending key bits [0, end_bit) of 64-bit keys.
+cudaError_t sort_asc_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+                         int64_t n, int end_bit, void* tmp, size_t tmp_bytes, cudaStream_t s);
+size_t sort_tmp_bytes_u64(int64_t n);
 // Stable sort of (key, value) pairs by ascending key bits [0, end_bit).
 cudaError_t sort_asc_u32(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
                          int64_t n, int end_bit, void* tmp, size_t tmp_bytes, cudaStream_t s);
@@ -149,6 +153,68 @@ cudaError_t launch_child_capacity(const JobArrays& parent, int64_t np, int kslot
 // left and order above cut (zero them first).
 cudaError_t launch_compact_jobs(const JobArrays& src, const int32_t* valid, const int32_t* pos, int64_t nslots,
                                 JobArrays dst, int cut, long long* stat, cudaStream_t s);
+
+// ---- K1 traversal driver (walk.cu) ----------------------------------------------
+// The walk's internal status when a buffer (arena, outputs, queue) is full:
+// the host then uses the level-by-level driver.
+#define WALK_FULL 200
+struct WalkArgs {
+  // global queue of nodes handed between warps; the roots start in it
+  int32_t* q_m;
+  int32_t* q_nnz;
+  int32_t* q_mat;
+  int32_t* q_dl;
+  int32_t* q_depth;
+  int64_t* q_off;
+  uint64_t* q_coef;   // 4 words per node
+  uint64_t* q_key;    // 2 words per node (path key, low word first)
+  int32_t* q_ready;   // 1 once slot t is written (zero it first)
+  int64_t cap_q;
+  unsigned long long* q_head;  // tickets taken
+  unsigned long long* q_tail;  // slots reserved
+  unsigned long long* outstanding;  // queued nodes plus busy warps (two's complement count)
+  // blocks: the roots' blocks first, then bump-allocated in chunks
+  uint64_t* arena;
+  int64_t cap_words;
+  int64_t arena_chunk;
+  unsigned long long* arena_used;
+  // jobs, in slots reserved kOutChunk at a time (unused slots keep key ~0)
+  JobArrays out;
+  uint64_t* out_key;  // 2 words per slot
+  int64_t cap_out;
+  unsigned long long* out_used;
+  unsigned long long* emitted;
+  // per depth: nodes, jobs, largest order still to split
+  unsigned long long* hist_nodes;
+  unsigned long long* hist_term;
+  int32_t* hist_maxopen;
+  int32_t hist_len;
+  int32_t leaf_size;
+  int32_t kslots;
+  int32_t bits_per_level;
+  int32_t key_levels;
+  // per-warp undo stacks (tile.cuh frames) for warps_cap warps
+  int64_t* undo;
+  int64_t undo_words_per_warp;
+  int32_t max_rel_depth;  // frames per warp
+  int64_t warps_cap;
+  int64_t timeout_ns;
+  int32_t* err;
+};
+// tile width for roots of this order (0: above the tiles; use the level-by-level driver)
+int walk_tile_for(int max_order);
+size_t walk_smem_bytes(int tile, int hist_len);
+int64_t walk_frame_words(int tile);
+// warps of the launch (every block resident)
+cudaError_t walk_resident_warps(int tile, int hist_len, int sms, int64_t* warps);
+// *grid = blocks launched (0: the kernel does not fit; use the level-by-level driver)
+cudaError_t launch_expand_walk(const WalkArgs& a, int tile, int sms, int* grid, cudaStream_t s);
+// perm = slots [0, n) in ascending path-key order; keys use bits [0, key_bits]
+// (two passes when key_bits >= 64)
+cudaError_t launch_walk_order(const uint64_t* key2, int64_t n, int key_bits, uint64_t* kbuf, uint64_t* kbuf2,
+                              uint32_t* ibuf, uint32_t* perm, void* tmp, size_t tmp_bytes, cudaStream_t s);
+cudaError_t launch_walk_gather(const uint32_t* perm, int64_t n, const JobArrays& src, const JobArrays& dst,
+                               cudaStream_t s);
 
 // ---- K3 depth-first evaluator --------------------------------------------------
 struct DfsArgs {

@@ -46,6 +46,17 @@ size_t sort_tmp_bytes_f32(int64_t n) {
   return b;
 }
 
+cudaError_t sort_asc_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+                         int64_t n, int end_bit, void* tmp, size_t tmp_bytes, cudaStream_t s) {
+  return cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys_in, keys_out, vals_in, vals_out, n, 0, end_bit, s);
+}
+size_t sort_tmp_bytes_u64(int64_t n) {
+  size_t b = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, b, (const uint64_t*)nullptr, (uint64_t*)nullptr, (const uint32_t*)nullptr,
+                                  (uint32_t*)nullptr, n, 0, 64);
+  return b;
+}
+
 cudaError_t sort_asc_u32(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
                          int64_t n, int end_bit, void* tmp, size_t tmp_bytes, cudaStream_t s) {
   return cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys_in, keys_out, vals_in, vals_out, n, 0, end_bit, s);

@@ -174,13 +174,29 @@ def test_invalid_arguments_rejected():
 
 
 # ---------------------------------------------------------------- expansion (K1)
-@pytest.mark.parametrize("fused", [True, False])
-@pytest.mark.parametrize("n,seed,d,L", [(10, 1, 3, 2), (16, 2, 6, 4), (24, 3, 10, 8), (36, 1, 20, 16)])
-def test_job_list_matches_oracle(n, seed, d, L, fused):
-    a = W.regular3(n, seed)
-    with pk.Plan([a], split_depth=d, leaf_size=L, fused_levels=fused) as plan:
+DRIVERS = {"walk": dict(expand_walk=True), "fused": dict(expand_walk=False, fused_levels=True),
+           "levels": dict(expand_walk=False, fused_levels=False)}
+
+
+def _driver_jobs(mats, driver, **kw):
+    with pk.Plan(mats, **DRIVERS[driver], **kw) as plan:
         plan.expand()
-        got = plan.jobs_export()
+        return plan.jobs_export(), plan.expand_driver
+
+
+def _same_jobs(got, want):
+    assert len(got) == len(want)
+    for (gi, gm, gc), (wi, wm, wc) in zip(got, want):
+        assert gi == wi and gm.shape == wm.shape and (gm == wm).all() and gc == wc
+
+
+@pytest.mark.parametrize("driver", list(DRIVERS))
+@pytest.mark.parametrize("n,seed,d,L", [(10, 1, 3, 2), (16, 2, 6, 4), (24, 3, 10, 8), (36, 1, 20, 16)])
+def test_job_list_matches_oracle(n, seed, d, L, driver):
+    a = W.regular3(n, seed)
+    got, used = _driver_jobs([a], driver, split_depth=d, leaf_size=L)
+    if driver == "walk":
+        assert used == "walk"
     want = oracle.jobs(a, d, L)
     assert len(got) == len(want)
     for (mi, gm, gc), (wm, wc) in zip(got, want):
@@ -189,30 +205,28 @@ def test_job_list_matches_oracle(n, seed, d, L, fused):
         assert gc == wc % (1 << 256)
 
 
-@pytest.mark.parametrize("fused", [True, False])
-def test_job_list_signed_sparse(fused):
+@pytest.mark.parametrize("driver", list(DRIVERS))
+def test_job_list_signed_sparse(driver):
     a = W.random_small(14, 77, lo=-2, hi=2, density=0.25)
     a[np.arange(14), np.arange(14)] = 1  # no zero line
-    with pk.Plan([a], split_depth=5, leaf_size=3, fused_levels=fused) as plan:
-        plan.expand()
-        got = plan.jobs_export()
+    got, _ = _driver_jobs([a], driver, split_depth=5, leaf_size=3)
     want = oracle.jobs(a, 5, 3)
     assert len(got) == len(want)
     for (_, gm, gc), (wm, wc) in zip(got, want):
         assert (gm == wm).all() and gc == wc % (1 << 256)
 
 
-@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("driver", list(DRIVERS))
 @pytest.mark.parametrize("seed", [1, 2, 3])
-def test_dense_split_job_list_matches_oracle(seed, fused):
+def test_dense_split_job_list_matches_oracle(seed, driver):
     """Eq. 2 with the third child (s >= 5): the expansion's job list equals
     the oracle's, and some jobs kept their order through a level."""
     a = W.random_small(12, 500 + seed, lo=1, hi=2, density=0.75)
     # every line holds at least five nonzeros, so the root takes three children
     assert min((a != 0).sum(axis=0).min(), (a != 0).sum(axis=1).min()) >= 5
-    with pk.Plan([a], split_depth=4, leaf_size=3, dense_split=True, fused_levels=fused) as plan:
-        plan.expand()
-        got = plan.jobs_export()
+    got, used = _driver_jobs([a], driver, split_depth=4, leaf_size=3, dense_split=True)
+    if driver == "walk":
+        assert used == "walk"
     want = oracle.jobs(a, 4, 3, three=True)
     assert len(got) == len(want) > 0
     for (_, gm, gc), (wm, wc) in zip(got, want):
@@ -220,30 +234,11 @@ def test_dense_split_job_list_matches_oracle(seed, fused):
     assert any(m.shape[0] > 12 - 4 for _, m, _ in got)
 
 
-@pytest.mark.parametrize("n,d,L", [(14, 0, 6), (16, 3, 8), (18, 6, 10), (20, 2, 12)])
-def test_dense_split_permanents(n, d, L):
-    """Dense 0/1 matrices (s >= 5 everywhere): the depth-first evaluator's
-    three-child frames and the expansion give the oracle's permanent, the
-    same as the paper's rule (Ryser at s >= 5)."""
-    a = W.random_small(n, 600 + n, lo=0, hi=1, density=0.6)
-    want = oracle.permanent(a)
-    for dense in (True, False):
-        with pk.Plan([a], split_depth=d, leaf_size=L, dense_split=dense) as plan:
-            plan.expand()
-            plan.evaluate()
-            assert plan.result(0) == want, dense
-
-
-def _export(mats, fused, **kw):
-    with pk.Plan(mats, fused_levels=fused, **kw) as plan:
-        plan.expand()
-        return plan.jobs_export()
-
-
 @pytest.mark.parametrize("case", ["c60", "batch", "regular80", "signed30"])
-def test_fused_levels_same_jobs(case):
-    """The single-launch multi-level expansion (with its buffer growth and
-    hand-over to per-level launches) yields the per-level job list."""
+def test_drivers_same_jobs(case):
+    """The traversal, the single-launch multi-level expansion (with its
+    buffer growth and hand-over to per-level launches) and the per-level
+    launches yield one job list."""
     if case == "c60":
         mats, kw = [W.c60(60)], dict(leaf_size=12)
     elif case == "batch":
@@ -255,11 +250,40 @@ def test_fused_levels_same_jobs(case):
         a = W.random_small(30, 9, lo=-3, hi=3, density=0.15)
         a[np.arange(30), (np.arange(30) * 7) % 30] = 2
         mats, kw = [a], dict(split_depth=12, leaf_size=5)
-    got = _export(mats, True, **kw)
-    want = _export(mats, False, **kw)
-    assert len(got) == len(want) > 0
-    for (gi, gm, gc), (wi, wm, wc) in zip(got, want):
-        assert gi == wi and gm.shape == wm.shape and (gm == wm).all() and gc == wc
+    want, _ = _driver_jobs(mats, "levels", **kw)
+    assert len(want) > 0
+    for driver in ("fused", "walk"):
+        got, used = _driver_jobs(mats, driver, **kw)
+        if driver == "walk":
+            # roots above the traversal's 64-wide tile go level by level
+            assert used == ("fused" if case == "regular80" else "walk")
+        _same_jobs(got, want)
+
+
+@pytest.mark.parametrize("case,expect", [("c60_L12", "walk"), ("c60_L8", "walk"), ("same_order_batch", "walk"),
+                                         ("mixed_orders", "fused"), ("regular80", "fused")])
+def test_walk_automatic_depth(case, expect):
+    """Automatic depth: the traversal runs to the end of the tree and replays
+    the level rule on its per-depth counts -- accepted when the rule reaches
+    the end (C60, leaf order 12: 78,425 jobs), run again at the depth the
+    rule stops at (leaf order 8: the count passes 2^17 one level above the
+    end), or handed to the level-by-level driver (its buffers fill for
+    n = 80; matrices of several orders need the waiting band).  The job list
+    is the per-level driver's in every case."""
+    if case == "c60_L12":
+        mats, kw = [W.c60(60)], dict(leaf_size=12)
+    elif case == "c60_L8":
+        mats, kw = [W.c60(60)], dict(leaf_size=8)
+    elif case == "same_order_batch":
+        mats, kw = [W.regular3(30, s) for s in (1, 2, 3)], dict(leaf_size=10)
+    elif case == "mixed_orders":
+        mats, kw = [W.regular3(n, 1) for n in (24, 30)], dict(leaf_size=10)
+    else:
+        mats, kw = [W.regular3(80, 2)], dict(leaf_size=12)
+    want, _ = _driver_jobs(mats, "levels", **kw)
+    got, used = _driver_jobs(mats, "walk", **kw)
+    assert used == expect
+    _same_jobs(got, want)
 
 
 # ---------------------------------------------------------------- hybrid end to end (K1+K3+K2+K6)
