@@ -637,12 +637,21 @@ static perm_status expand_by_walk(perm_plan* P, perm_jobs* J, WalkRoots R, int m
   const int key_bits = rbits + bpl * maxd;
   if (key_bits > 127) return PERM_OK;
   const int hist_len = maxd + 1;
-  const int tile = walk_tile_for(maxn);
-  if (tile == 0) return PERM_OK;
-  int64_t warps = 0;
-  CK(walk_resident_warps(tile, hist_len, P->sms, &warps));
-  if (warps <= 0) return PERM_OK;
-  const int frames = std::max(1, maxd);
+  if (walk_tile_for(maxn) == 0) return PERM_OK;
+  // phases: a 64-wide tile for the nodes above order 32, which hands the
+  // nodes of order <= 32 to a 32-wide tile (more warps per SM)
+  const bool wide_phase = maxn > 32;
+  const int stage = (int)std::min<int64_t>((sw + 1) & ~1ll, 512);
+  int64_t warps32 = 0, warps64 = 0;
+  CK(walk_resident_warps(32, stage, hist_len, P->sms, &warps32));
+  if (wide_phase) CK(walk_resident_warps(64, stage, hist_len, P->sms, &warps64));
+  if (warps32 <= 0 || (wide_phase && warps64 <= 0)) return PERM_OK;
+  // undo frames: a path below its subtree root is at most the order span of its phase
+  // (Eq. 2's third child keeps the order: then the whole depth)
+  const int frames32 = std::max(1, K == 3 ? maxd : std::min(maxd, 32));
+  const int frames64 = std::max(1, K == 3 ? maxd : std::min(maxd, 64));
+  const int64_t undo_words = std::max(warps32 * frames32 * walk_frame_words(32),
+                                      wide_phase ? warps64 * frames64 * walk_frame_words(64) : 0);
   const int64_t hw = (int64_t)P->h_arena.size();
   // jobs, plus the slots a warp may leave unused in its last reserved chunk
   // (at most 64 resident warps per SM)
@@ -653,40 +662,52 @@ static perm_status expand_by_walk(perm_plan* P, perm_jobs* J, WalkRoots R, int m
   const int64_t cap_words =
       ((hw + 1) & ~1ll) + jobs_cap * std::max<int64_t>(96, sw / 2) + (int64_t)P->sms * 64 * chunk;
   // device buffers
-  WalkArgs A{};
-  A.q_m = dget<int32_t>(M, cap);
-  A.q_nnz = dget<int32_t>(M, cap);
-  A.q_mat = dget<int32_t>(M, cap);
-  A.q_dl = dget<int32_t>(M, cap);
-  A.q_depth = dget<int32_t>(M, cap);
-  A.q_off = dget<int64_t>(M, cap);
-  A.q_coef = dget<uint64_t>(M, 4 * cap);
-  A.q_key = dget<uint64_t>(M, 2 * cap);
-  A.q_ready = dget<int32_t>(M, cap);
+  auto alloc_queue = [&](WalkQueue& Q, int64_t n) {
+    Q.m = dget<int32_t>(M, n);
+    Q.nnz = dget<int32_t>(M, n);
+    Q.mat = dget<int32_t>(M, n);
+    Q.dl = dget<int32_t>(M, n);
+    Q.depth = dget<int32_t>(M, n);
+    Q.off = dget<int64_t>(M, n);
+    Q.coef = dget<uint64_t>(M, 4 * n);
+    Q.key = dget<uint64_t>(M, 2 * n);
+    Q.ready = dget<int32_t>(M, n);
+    Q.cap = n;
+    return Q.m && Q.nnz && Q.mat && Q.dl && Q.depth && Q.off && Q.coef && Q.key && Q.ready;
+  };
+  auto free_queue = [&](WalkQueue& Q) {
+    for (void* p : {(void*)Q.m, (void*)Q.nnz, (void*)Q.mat, (void*)Q.dl, (void*)Q.depth, (void*)Q.off,
+                    (void*)Q.coef, (void*)Q.key, (void*)Q.ready})
+      M.put(p);
+  };
+  WalkQueue Q1{}, Q2{};
+  const bool q_ok = alloc_queue(Q1, cap) && alloc_queue(Q2, cap);
   JobArrays out{};
   const bool out_ok = alloc_jobs(M, out, cap);
   uint64_t* out_key = dget<uint64_t>(M, 2 * cap);
   uint64_t* arena = dget<uint64_t>(M, cap_words);
-  unsigned long long* ctr = dget<unsigned long long>(M, 8);
-  int64_t* undo = dget<int64_t>(M, warps * frames * walk_frame_words(tile));
+  // [0, 1] work queue head, tail; [2] outstanding; [3] arena words; [4] output slots;
+  // [5] jobs; [6] status; [7, 8] hand-over queue head, tail
+  unsigned long long* ctr = dget<unsigned long long>(M, 10);
   unsigned long long* hist = dget<unsigned long long>(M, 2 * hist_len);
   int32_t* hmo = dget<int32_t>(M, hist_len);
+  int64_t* undo = dget<int64_t>(M, undo_words);
   auto release = [&](bool keep_arena) {
-    for (void* p : {(void*)A.q_m, (void*)A.q_nnz, (void*)A.q_mat, (void*)A.q_dl, (void*)A.q_depth, (void*)A.q_off,
-                    (void*)A.q_coef, (void*)A.q_key, (void*)A.q_ready, (void*)out_key, (void*)ctr, (void*)hist,
-                    (void*)hmo, (void*)undo})
-      M.put(p);
+    free_queue(Q1);
+    free_queue(Q2);
+    for (void* p : {(void*)out_key, (void*)ctr, (void*)hist, (void*)hmo, (void*)undo}) M.put(p);
     free_jobs(M, out);
     if (!keep_arena) M.put(arena);
   };
-  if (!A.q_m || !A.q_nnz || !A.q_mat || !A.q_dl || !A.q_depth || !A.q_off || !A.q_coef || !A.q_key || !A.q_ready ||
-      !out_ok || !out_key || !arena || !ctr || !hist || !hmo || !undo) {
+  if (!q_ok || !out_ok || !out_key || !arena || !ctr || !hist || !hmo || !undo) {
     release(false);
     return PERM_OK;  // too large for the traversal's buffers: the level-by-level driver grows its own
   }
-  A.cap_q = cap;
-  A.q_head = ctr + 0;
-  A.q_tail = ctr + 1;
+  Q1.head = ctr + 0;
+  Q1.tail = ctr + 1;
+  Q2.head = ctr + 7;
+  Q2.tail = ctr + 8;
+  WalkArgs A{};
   A.outstanding = ctr + 2;
   A.arena_used = ctr + 3;
   A.out_used = ctr + 4;
@@ -706,10 +727,8 @@ static perm_status expand_by_walk(perm_plan* P, perm_jobs* J, WalkRoots R, int m
   A.kslots = K;
   A.bits_per_level = bpl;
   A.key_levels = maxd;
+  A.stage_words = stage;
   A.undo = undo;
-  A.undo_words_per_warp = (int64_t)frames * walk_frame_words(tile);
-  A.max_rel_depth = frames;
-  A.warps_cap = warps;
   // an idle warp waits for the others' remaining work: at least a second,
   // whatever the evaluation watchdog
   A.timeout_ns = std::max<int64_t>(P->opts.timeout_ns > 0 ? P->opts.timeout_ns : 10000000000ll, 1000000000ll);
@@ -723,27 +742,47 @@ static perm_status expand_by_walk(perm_plan* P, perm_jobs* J, WalkRoots R, int m
     key[2 * r + 1] = (uint64_t)(k >> 64);
   }
   CK(cudaMemcpyAsync(arena, P->h_arena.data(), 8 * hw, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(A.q_m, R.m.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(A.q_nnz, R.nnz.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(A.q_mat, R.mat.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(A.q_depth, depth0.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(A.q_off, R.off.data(), 8 * nroots, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(A.q_coef, coef.data(), 32 * nroots, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(A.q_key, key.data(), 16 * nroots, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(Q1.m, R.m.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(Q1.nnz, R.nnz.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(Q1.mat, R.mat.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(Q1.depth, depth0.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(Q1.off, R.off.data(), 8 * nroots, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(Q1.coef, coef.data(), 32 * nroots, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(Q1.key, key.data(), 16 * nroots, cudaMemcpyHostToDevice, s));
   bool fixed_rerun = false;
   for (int attempt = 0; attempt < 2; ++attempt) {
-    CK(cudaMemcpyAsync(A.q_dl, R.dl.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(A.q_ready, 0, 4 * (size_t)cap, s));
-    CK(cudaMemcpyAsync(A.q_ready, ones.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(Q1.dl, R.dl.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(Q1.ready, 0, 4 * (size_t)cap, s));
+    CK(cudaMemsetAsync(Q2.ready, 0, 4 * (size_t)cap, s));
+    CK(cudaMemcpyAsync(Q1.ready, ones.data(), 4 * nroots, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(out_key, 0xff, 16 * (size_t)cap, s));
     CK(cudaMemsetAsync(hist, 0, 16 * (size_t)hist_len, s));
     CK(cudaMemsetAsync(hmo, 0, 4 * (size_t)hist_len, s));
-    unsigned long long c0[8] = {0, (unsigned long long)nroots, (unsigned long long)nroots,
-                                (unsigned long long)((hw + 1) & ~1ll), 0, 0, 0, 0};
+    unsigned long long c0[10] = {0, (unsigned long long)nroots, (unsigned long long)nroots,
+                                 (unsigned long long)((hw + 1) & ~1ll), 0, 0, 0, 0, 0, 0};
     CK(cudaMemcpyAsync(ctr, c0, sizeof(c0), cudaMemcpyHostToDevice, s));
-    int grid = 0;
-    CK(launch_expand_walk(A, tile, P->sms, &grid, s));
-    unsigned long long c1[8];
+    int grid = 1;
+    if (wide_phase) {
+      A.q = Q1;
+      A.hand = Q2;
+      A.handover_order = 32;
+      A.undo_words_per_warp = (int64_t)frames64 * walk_frame_words(64);
+      A.max_rel_depth = frames64;
+      A.warps_cap = warps64;
+      CK(launch_expand_walk(A, 64, P->sms, &grid, s));
+      // the narrower phase's work: the nodes handed over
+      CK(cudaMemcpyAsync(ctr + 2, ctr + 8, 8, cudaMemcpyDeviceToDevice, s));
+    }
+    if (grid > 0) {
+      A.q = wide_phase ? Q2 : Q1;
+      A.hand = WalkQueue{};
+      A.handover_order = 0;
+      A.undo_words_per_warp = (int64_t)frames32 * walk_frame_words(32);
+      A.max_rel_depth = frames32;
+      A.warps_cap = warps32;
+      CK(launch_expand_walk(A, 32, P->sms, &grid, s));
+    }
+    unsigned long long c1[10];
     std::vector<unsigned long long> hh(2 * hist_len);
     std::vector<int32_t> hm(hist_len);
     CK(cudaMemcpyAsync(c1, ctr, sizeof(c1), cudaMemcpyDeviceToHost, s));

@@ -158,27 +158,32 @@ cudaError_t launch_compact_jobs(const JobArrays& src, const int32_t* valid, cons
 // The walk's internal status when a buffer (arena, outputs, queue) is full:
 // the host then uses the level-by-level driver.
 #define WALK_FULL 200
+// A queue of subtree roots handed between warps (ticket per waiting warp).
+struct WalkQueue {
+  int32_t* m;
+  int32_t* nnz;
+  int32_t* mat;
+  int32_t* dl;
+  int32_t* depth;
+  int64_t* off;
+  uint64_t* coef;   // 4 words per node
+  uint64_t* key;    // 2 words per node (path key, low word first)
+  int32_t* ready;   // 1 once slot t is written (zero it first)
+  int64_t cap;
+  unsigned long long* head;  // tickets taken
+  unsigned long long* tail;  // slots reserved
+};
 struct WalkArgs {
-  // global queue of nodes handed between warps; the roots start in it
-  int32_t* q_m;
-  int32_t* q_nnz;
-  int32_t* q_mat;
-  int32_t* q_dl;
-  int32_t* q_depth;
-  int64_t* q_off;
-  uint64_t* q_coef;   // 4 words per node
-  uint64_t* q_key;    // 2 words per node (path key, low word first)
-  int32_t* q_ready;   // 1 once slot t is written (zero it first)
-  int64_t cap_q;
-  unsigned long long* q_head;  // tickets taken
-  unsigned long long* q_tail;  // slots reserved
-  unsigned long long* outstanding;  // queued nodes plus busy warps (two's complement count)
+  WalkQueue q;      // work: the roots (or the nodes handed over by the wider phase) and donated siblings
+  WalkQueue hand;   // nodes of order <= handover_order, for the narrower phase
+  int32_t handover_order;  // 0: walk every node here
+  unsigned long long* outstanding;  // nodes in q not yet taken plus busy warps (two's complement count)
   // blocks: the roots' blocks first, then bump-allocated in chunks
   uint64_t* arena;
   int64_t cap_words;
   int64_t arena_chunk;
   unsigned long long* arena_used;
-  // jobs, in slots reserved kOutChunk at a time (unused slots keep key ~0)
+  // jobs, in slots reserved a few at a time (unused slots keep key ~0)
   JobArrays out;
   uint64_t* out_key;  // 2 words per slot
   int64_t cap_out;
@@ -193,6 +198,7 @@ struct WalkArgs {
   int32_t kslots;
   int32_t bits_per_level;
   int32_t key_levels;
+  int32_t stage_words;  // words of a warp's staging copy of a block (larger blocks are read from L2)
   // per-warp undo stacks (tile.cuh frames) for warps_cap warps
   int64_t* undo;
   int64_t undo_words_per_warp;
@@ -203,10 +209,10 @@ struct WalkArgs {
 };
 // tile width for roots of this order (0: above the tiles; use the level-by-level driver)
 int walk_tile_for(int max_order);
-size_t walk_smem_bytes(int tile, int hist_len);
+size_t walk_smem_bytes(int tile, int stage_words, int hist_len);
 int64_t walk_frame_words(int tile);
 // warps of the launch (every block resident)
-cudaError_t walk_resident_warps(int tile, int hist_len, int sms, int64_t* warps);
+cudaError_t walk_resident_warps(int tile, int stage_words, int hist_len, int sms, int64_t* warps);
 // *grid = blocks launched (0: the kernel does not fit; use the level-by-level driver)
 cudaError_t launch_expand_walk(const WalkArgs& a, int tile, int sms, int* grid, cudaStream_t s);
 // perm = slots [0, n) in ascending path-key order; keys use bits [0, key_bits]

@@ -135,13 +135,17 @@ struct Eq2Tile {
 
   // Apply child c; returns false when a merged entry leaves E.
   __device__ bool apply(int lv, const Frame& f, const int64_t* pv, int c) {
+    return apply_to(frame_words(lv) + 13, f, pv, c);
+  }
+  // The same with the overwritten line saved at saved[0 .. TILE) and its
+  // mask at saved[-1] (a frame of the undo stack, or a scratch line).
+  __device__ bool apply_to(int64_t* saved, const Frame& f, const int64_t* pv, int c) {
     int kind, x;
     child_kind(f.k, c, kind, x);
     if (kind == 3) {
       clear_four(f, pv, false);
       return true;
     }
-    int64_t* saved = frame_words(lv) + 13;
     bool ok = true;
     if (!f.is_col) {
       const int i = f.idx;
@@ -215,6 +219,9 @@ struct Eq2Tile {
   }
 
   __device__ void undo_child(int lv, const Frame& f, const int64_t* pv, const u256& pcoef, int c) {
+    undo_from(frame_words(lv) + 13, f, pv, pcoef, c);
+  }
+  __device__ void undo_from(const int64_t* saved, const Frame& f, const int64_t* pv, const u256& pcoef, int c) {
     int kind, x;
     child_kind(f.k, c, kind, x);
     coef = pcoef;
@@ -222,7 +229,6 @@ struct Eq2Tile {
       clear_four(f, pv, true);
       return;
     }
-    const int64_t* saved = frame_words(lv) + 13;
     if (!f.is_col) {
       const int i = f.idx;
       R |= bit64(i);

@@ -40,13 +40,21 @@ namespace {
 
 typedef int32_t WE;              // tile entries
 constexpr int kOutChunk = 16;    // output slots a warp reserves at a time (as api.cu sizes them)
-constexpr int kCheckEvery = 16;  // nodes between looks at the error flag and the waiting warps
+constexpr int kCheckEvery = 16;   // nodes between looks at the error flag and the waiting warps while none wait
+constexpr int kCheckWaiting = 4;  // the same while warps wait
 
 template <int TILE>
 struct WalkCfg {
   static constexpr int WARPS = TILE <= 32 ? 8 : 4;  // warps per block
-  static constexpr size_t WARP_BYTES = TileCfg<TILE, WE>::TILE_BYTES + TileCfg<TILE, WE>::MASK_BYTES;
+  static constexpr int MINB = TILE <= 32 ? 3 : 2;   // blocks per SM the registers are sized for
+  // tile, masks and a scratch line (the in-place children's saved line); the staging copy follows
+  static constexpr size_t FIXED_BYTES =
+      TileCfg<TILE, WE>::TILE_BYTES + TileCfg<TILE, WE>::MASK_BYTES + sizeof(int64_t) * (TILE + 2);
 };
+
+__host__ __device__ __forceinline__ size_t walk_warp_bytes(int tile, int stage_words) {
+  return (tile <= 32 ? WalkCfg<32>::FIXED_BYTES : WalkCfg<64>::FIXED_BYTES) + sizeof(uint64_t) * (size_t)stage_words;
+}
 
 __device__ __forceinline__ int volatile_ld(const int32_t* p) { return *(const volatile int32_t*)p; }
 __device__ __forceinline__ unsigned long long volatile_ld(const unsigned long long* p) {
@@ -82,18 +90,19 @@ __device__ __forceinline__ int64_t walk_alloc(const WalkArgs& A, WarpCtx& W, int
 // CSR block in the arena; returns its offset (-1 when the arena is full),
 // its order and its nonzeros.
 template <int TILE>
-__device__ int64_t compact_tile(const WalkArgs& A, WarpCtx& W, const Eq2Tile<TILE, WE>& D, int& m_out,
-                                int& nnz_out) {
+__device__ __noinline__ int64_t compact_tile(const WalkArgs& A, WarpCtx& W, const WE* __restrict__ T,
+                                             const uint64_t* __restrict__ rowbits, uint64_t R, uint64_t C,
+                                             int& m_out, int& nnz_out) {
   constexpr int S = TileCfg<TILE, WE>::STRIDE;
   constexpr int RPL = TILE / 32;
   const int lane = W.lane;
-  const int m = __popcll(D.R);
+  const int m = __popcll(R);
   int cnt[RPL], row[RPL];
 #pragma unroll
   for (int t = 0; t < RPL; ++t) {
     const int k = lane + 32 * t;
-    row[t] = k < m ? nth_bit(D.R, k) : 0;
-    cnt[t] = k < m ? __popcll(D.rowbits[row[t]] & D.C) : 0;
+    row[t] = k < m ? nth_bit(R, k) : 0;
+    cnt[t] = k < m ? __popcll(rowbits[row[t]] & C) : 0;
   }
   int offs[RPL];
   int nnz = 0;
@@ -111,7 +120,10 @@ __device__ int64_t compact_tile(const WalkArgs& A, WarpCtx& W, const Eq2Tile<TIL
   m_out = m;
   nnz_out = nnz;
   const int64_t o = walk_alloc(A, W, blk_words(m, nnz));
-  if (o < 0) return -1;
+  if (o < 0) {
+    __syncwarp();
+    return -1;
+  }
   uint64_t* blk = A.arena + o;
   uint16_t* rowptr = reinterpret_cast<uint16_t*>(blk);
   uint8_t* colp = reinterpret_cast<uint8_t*>(blk + blk_rp_words(m));
@@ -123,22 +135,25 @@ __device__ int64_t compact_tile(const WalkArgs& A, WarpCtx& W, const Eq2Tile<TIL
     if (k < m) {
       rowptr[k] = (uint16_t)offs[t];
       const int r = row[t];
-      uint64_t cm = D.rowbits[r] & D.C;
+      uint64_t cm = rowbits[r] & C;
       int w = offs[t];
       while (cm) {
         const int c = __ffsll((long long)cm) - 1;
         cm &= cm - 1;
-        colp[w] = (uint8_t)__popcll(D.C & (bit64(c) - 1));
-        valp[w] = (int64_t)D.T[r * S + c];
+        colp[w] = (uint8_t)__popcll(C & (bit64(c) - 1));
+        valp[w] = (int64_t)T[r * S + c];
         ++w;
       }
     }
   }
+  // a lane read rows other lanes own: every read done before any lane
+  // changes the tile again (an undo writes each lane's own rows)
+  __syncwarp();
   return o;
 }
 
 // Write a job's header and path key; its block is at off.
-__device__ void walk_emit(const WalkArgs& A, WarpCtx& W, int m, int nnz, int64_t off, int mat, int depth,
+__device__ __noinline__ void walk_emit(const WalkArgs& A, WarpCtx& W, int m, int nnz, int64_t off, int mat, int depth,
                           const u256& coef, uint64_t key_lo, uint64_t key_hi, unsigned* h_term) {
   if (W.o_pos >= W.o_end) {
     unsigned long long b = 0;
@@ -166,29 +181,30 @@ __device__ void walk_emit(const WalkArgs& A, WarpCtx& W, int m, int nnz, int64_t
   W.emitted += 1;
 }
 
-// Hand a node (block at off, written by this warp) to the global queue.
-__device__ void walk_push(const WalkArgs& A, int lane, int m, int nnz, int64_t off, int mat, int dl, int depth,
-                          const u256& coef, uint64_t key_lo, uint64_t key_hi) {
+// Append a node (block at off, written by this warp) to queue Q; counted as
+// outstanding work when Q is this phase's work queue.
+__device__ __noinline__ void walk_push(const WalkArgs& A, const WalkQueue& Q, bool work, int lane, int m, int nnz, int64_t off,
+                          int mat, int dl, int depth, const u256& coef, uint64_t key_lo, uint64_t key_hi) {
   __syncwarp();
   __threadfence();  // every lane's part of the block before the slot is published
   __syncwarp();
   if (lane == 0) {
-    atomicAdd(A.outstanding, 1ull);
-    const unsigned long long t = atomicAdd(A.q_tail, 1ull);
-    if ((int64_t)t >= A.cap_q) {
+    if (work) atomicAdd(A.outstanding, 1ull);
+    const unsigned long long t = atomicAdd(Q.tail, 1ull);
+    if ((int64_t)t >= Q.cap) {
       atomicCAS(A.err, 0, WALK_FULL);
     } else {
-      A.q_m[t] = m;
-      A.q_nnz[t] = nnz;
-      A.q_mat[t] = mat;
-      A.q_dl[t] = dl;
-      A.q_depth[t] = depth;
-      A.q_off[t] = off;
-      for (int w = 0; w < 4; ++w) A.q_coef[4 * t + w] = coef.w[w];
-      A.q_key[2 * t] = key_lo;
-      A.q_key[2 * t + 1] = key_hi;
+      Q.m[t] = m;
+      Q.nnz[t] = nnz;
+      Q.mat[t] = mat;
+      Q.dl[t] = dl;
+      Q.depth[t] = depth;
+      Q.off[t] = off;
+      for (int w = 0; w < 4; ++w) Q.coef[4 * t + w] = coef.w[w];
+      Q.key[2 * t] = key_lo;
+      Q.key[2 * t + 1] = key_hi;
       __threadfence();
-      *(volatile int32_t*)(A.q_ready + t) = 1;
+      *(volatile int32_t*)(Q.ready + t) = 1;
     }
   }
   __syncwarp();
@@ -211,21 +227,25 @@ __device__ __forceinline__ void key_set(uint64_t& lo, uint64_t& hi, int t, uint6
 __device__ __forceinline__ uint64_t blk_word(const uint64_t* b, int64_t k) { return __ldcg(b + k); }
 
 template <int TILE>
-__global__ void __launch_bounds__(WalkCfg<TILE>::WARPS * 32) k_expand_walk(WalkArgs A) {
+__global__ void __launch_bounds__(WalkCfg<TILE>::WARPS * 32, WalkCfg<TILE>::MINB) k_expand_walk(WalkArgs A) {
   constexpr int S = TileCfg<TILE, WE>::STRIDE;
   constexpr int NW = WalkCfg<TILE>::WARPS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  unsigned char* base = smem_raw + (size_t)wib * WalkCfg<TILE>::WARP_BYTES;
+  const size_t warp_bytes = walk_warp_bytes(TILE, A.stage_words);
+  unsigned char* base = smem_raw + (size_t)wib * warp_bytes;
   Eq2Tile<TILE, WE> D;
   D.T = reinterpret_cast<WE*>(base);
   D.rowbits = reinterpret_cast<uint64_t*>(base + TileCfg<TILE, WE>::TILE_BYTES);
   D.colbits = D.rowbits + TILE;
   D.lane = lane;
+  // scratch line of the in-place children: mask at [-1], line at [0, TILE)
+  int64_t* scratch = reinterpret_cast<int64_t*>(D.colbits + TILE) + 2;
+  uint64_t* stage = reinterpret_cast<uint64_t*>(base + WalkCfg<TILE>::FIXED_BYTES);
   const int64_t gwarp = (int64_t)blockIdx.x * NW + wib;
   D.undo = A.undo + gwarp * A.undo_words_per_warp;
-  unsigned* h_nodes = reinterpret_cast<unsigned*>(smem_raw + (size_t)NW * WalkCfg<TILE>::WARP_BYTES);
+  unsigned* h_nodes = reinterpret_cast<unsigned*>(smem_raw + (size_t)NW * warp_bytes);
   unsigned* h_term = h_nodes + A.hist_len;
   int* h_mo = reinterpret_cast<int*>(h_term + A.hist_len);
   for (int k = threadIdx.x; k < A.hist_len; k += blockDim.x) {
@@ -245,26 +265,32 @@ __global__ void __launch_bounds__(WalkCfg<TILE>::WARPS * 32) k_expand_walk(WalkA
   W.o_pos = W.o_end = 0;
   W.emitted = 0;
   int since_check = 0;
-  bool waiting = true;  // other warps wait for work (looked up every kCheckEvery nodes, or while true)
+  bool waiting = true;  // other warps wait for work: hand them siblings (looked up every few nodes)
 
   for (;;) {
-    // ---- a subtree root from the global queue
+    // ---- a subtree root from the work queue
     unsigned long long ticket = 0;
-    if (lane == 0) ticket = atomicAdd(A.q_head, 1ull);
+    if (lane == 0) ticket = atomicAdd(A.q.head, 1ull);
     ticket = __shfl_sync(0xffffffffu, ticket, 0);
     int got = 0;
     if (lane == 0) {
+      // poll this ticket's own slot, the shared counters only every 8th time,
+      // with a growing pause: thousands of idle warps must not hammer one L2 line
+      unsigned pause = 64;
       for (unsigned spins = 0;; ++spins) {
-        if ((int64_t)ticket < A.cap_q && volatile_ld(A.q_ready + ticket) != 0) {
+        if ((int64_t)ticket < A.q.cap && volatile_ld(A.q.ready + ticket) != 0) {
           got = 1;
           break;
         }
-        if ((long long)volatile_ld(A.outstanding) <= 0 || volatile_ld(A.err) != 0) break;
-        if ((spins & 63u) == 63u && globaltimer_ns() - t_start > (uint64_t)A.timeout_ns) {
-          atomicCAS(A.err, 0, PERM_ETIMEOUT);
-          break;
+        if ((spins & 7u) == 7u) {
+          if ((long long)volatile_ld(A.outstanding) <= 0 || volatile_ld(A.err) != 0) break;
+          if (globaltimer_ns() - t_start > (uint64_t)A.timeout_ns) {
+            atomicCAS(A.err, 0, PERM_ETIMEOUT);
+            break;
+          }
         }
-        __nanosleep(128);
+        __nanosleep(pause);
+        if (pause < 2048) pause *= 2;
       }
       __threadfence();
     }
@@ -272,26 +298,42 @@ __global__ void __launch_bounds__(WalkCfg<TILE>::WARPS * 32) k_expand_walk(WalkA
     if (!got) break;
     __threadfence();
     const int64_t t = (int64_t)ticket;
-    const int m0 = __ldcg(A.q_m + t), nnz0 = __ldcg(A.q_nnz + t), mat = __ldcg(A.q_mat + t);
-    const int dl0 = __ldcg(A.q_dl + t), depth0 = __ldcg(A.q_depth + t);
-    const int64_t off0 = __ldcg(A.q_off + t);
-    for (int w = 0; w < 4; ++w) D.coef.w[w] = __ldcg(A.q_coef + 4 * t + w);
-    uint64_t key_lo = __ldcg(A.q_key + 2 * t), key_hi = __ldcg(A.q_key + 2 * t + 1);
+    const int m0 = __ldcg(A.q.m + t), nnz0 = __ldcg(A.q.nnz + t), mat = __ldcg(A.q.mat + t);
+    const int dl0 = __ldcg(A.q.dl + t), depth0 = __ldcg(A.q.depth + t);
+    const int64_t off0 = __ldcg(A.q.off + t);
+    for (int w = 0; w < 4; ++w) D.coef.w[w] = __ldcg(A.q.coef + 4 * t + w);
+    uint64_t key_lo = __ldcg(A.q.key + 2 * t), key_hi = __ldcg(A.q.key + 2 * t + 1);
     bool stop = m0 > TILE;
-    // ---- the node into the tile
-    for (int k = lane; k < TILE * S; k += 32) D.T[k] = 0;
-    for (int k = lane; k < TILE; k += 32) D.rowbits[k] = D.colbits[k] = 0;
-    __syncwarp();
+    // ---- the node into the tile: its block staged with 16-byte L2 reads,
+    // the tile's first m0 rows cleared
+    const int64_t bw = blk_words(m0, nnz0);
+    const bool staged = bw <= A.stage_words;
     const uint64_t* blk = A.arena + off0;
+    if (staged) {
+      const uint4* s4 = reinterpret_cast<const uint4*>(blk);
+      uint4* d4 = reinterpret_cast<uint4*>(stage);
+      for (int64_t k = lane; k < bw / 2; k += 32) d4[k] = __ldcg(s4 + k);
+    }
+    {
+      const int rows = stop ? 0 : m0;
+      int4* t4 = reinterpret_cast<int4*>(D.T);
+      const int n4 = (int)((sizeof(WE) * (size_t)rows * S + 15) / 16);
+      for (int k = lane; k < n4; k += 32) t4[k] = make_int4(0, 0, 0, 0);
+      for (int k = lane; k < TILE; k += 32) D.rowbits[k] = D.colbits[k] = 0;
+    }
+    __syncwarp();
     const int rpw = (int)blk_rp_words(m0), cw = (int)blk_col_words(nnz0);
+    const uint16_t* srp = reinterpret_cast<const uint16_t*>(stage);
+    const uint8_t* scol = reinterpret_cast<const uint8_t*>(stage + rpw);
+    const int64_t* sval = reinterpret_cast<const int64_t*>(stage + rpw + cw);
     bool fits = true;
     for (int r = lane; r < m0 && !stop; r += 32) {
-      const int b = (int)((blk_word(blk, r / 4) >> (16 * (r % 4))) & 0xffff);
-      const int e = (int)((blk_word(blk, (r + 1) / 4) >> (16 * ((r + 1) % 4))) & 0xffff);
+      const int b = staged ? srp[r] : (int)((blk_word(blk, r / 4) >> (16 * (r % 4))) & 0xffff);
+      const int e = staged ? srp[r + 1] : (int)((blk_word(blk, (r + 1) / 4) >> (16 * ((r + 1) % 4))) & 0xffff);
       uint64_t rb = 0;
       for (int q = b; q < e; ++q) {
-        const int c = (int)((blk_word(blk, rpw + q / 8) >> (8 * (q % 8))) & 0xff);
-        const int64_t x = (int64_t)blk_word(blk, rpw + cw + q);
+        const int c = staged ? scol[q] : (int)((blk_word(blk, rpw + q / 8) >> (8 * (q % 8))) & 0xff);
+        const int64_t x = staged ? sval[q] : (int64_t)blk_word(blk, rpw + cw + q);
         if ((int64_t)(WE)x != x) fits = false;
         D.T[r * S + c] = (WE)x;
         rb |= bit64(c);
@@ -306,113 +348,146 @@ __global__ void __launch_bounds__(WalkCfg<TILE>::WARPS * 32) k_expand_walk(WalkA
       stop = true;
     }
     D.R = D.C = (m0 == 64) ? ~0ull : (bit64(m0) - 1);
-    // ---- depth-first walk of the subtree: rel = depth of the current node below its root
+    // ---- depth-first walk of the subtree: rel = depth of the current node below its root.
+    // One call site per tile operation (the kernel's code stays small enough
+    // for the instruction cache): a visit either writes the node out, or
+    // splits it -- children that are jobs (or that go to waiting warps)
+    // applied and undone with the scratch line -- and then moves into child
+    // `next`, or backs up to the next child not yet walked.
     int rel = 0;
     bool done = stop;
     while (!done) {
       const int depth = depth0 + rel;
-      if (++since_check >= kCheckEvery || waiting) {
-        since_check = 0;
-        int e = 0, wt = 0;
-        if (lane == 0) {
-          e = volatile_ld(A.err);
-          wt = volatile_ld(A.q_head) > volatile_ld(A.q_tail) ? 1 : 0;
-        }
-        if (__shfl_sync(0xffffffffu, e, 0) != 0) break;  // another warp failed: abandon the walk
-        waiting = __shfl_sync(0xffffffffu, wt, 0) != 0;
+      // the error flag and the waiting warps: every kCheckWaiting nodes while
+      // warps wait, else every kCheckEvery nodes
+      const bool check = ++since_check >= (waiting ? kCheckWaiting : kCheckEvery);
+      unsigned long long q_h = 0, q_t = 0;
+      int e = 0;
+      if (check && lane == 0) {
+        q_h = __ldcg(A.q.head);
+        q_t = __ldcg(A.q.tail);
+        e = __ldcg(A.err);
       }
-      if (lane == 0 && depth < A.hist_len) atomicAdd(h_nodes + depth, 1u);
       const unsigned long long key = D.pivot_key();
       const int s = (int)(key >> 17);
       const int mact = __popcll(D.R);
       const int dl = dl0 - rel;
       const bool open = dl > 0 && mact > cut;
-      if (open && lane == 0 && depth < A.hist_len) atomicMax(h_mo + depth, mact);
-      bool descend = false;
-      if (s > 0 && (!open || (s >= 5 && !three))) {
-        // a job
-        int mj, nj;
-        const int64_t o = compact_tile<TILE>(A, W, D, mj, nj);
-        if (o >= 0) walk_emit(A, W, mj, nj, o, mat, depth, D.coef, key_lo, key_hi, h_term);
-      } else if (s > 0) {
-        if (rel >= A.max_rel_depth) {
-          if (lane == 0) atomicCAS(A.err, 0, WALK_FULL);
-          break;
+      if (check) {
+        since_check = 0;
+        if (__shfl_sync(0xffffffffu, e, 0) != 0) break;  // another warp failed: abandon the walk
+        waiting = __shfl_sync(0xffffffffu, q_h > q_t ? 1 : 0, 0) != 0;
+      }
+      Frame f;
+      int64_t pv[4] = {0, 0, 0, 0};
+      u256 pcoef = D.coef;
+      int next = -1;
+      bool failed = false;
+      if (s > 0) {
+        const bool handover = open && mact <= A.handover_order;
+        if (!handover && lane == 0 && depth < A.hist_len) {
+          atomicAdd(h_nodes + depth, 1u);
+          if (open) atomicMax(h_mo + depth, mact);
         }
-        Frame f;
-        f.is_col = (int)((key >> 16) & 1);
-        f.idx = (int)(key & 0xffff);
-        f.k = s;
-        f.child = 0;
-        int64_t pv[4] = {0, 0, 0, 0};
-        uint64_t line = f.is_col ? (D.colbits[f.idx] & D.R) : (D.rowbits[f.idx] & D.C);
-        for (int q = 0; q < 4; ++q) {
-          if (line) {
-            const int c = __ffsll((long long)line) - 1;
-            line &= line - 1;
-            f.pos[q] = c;
-            pv[q] = (int64_t)(f.is_col ? D.T[c * S + f.idx] : D.T[f.idx * S + c]);
-          } else {
-            f.pos[q] = 0;
+        if (handover || !open || (s >= 5 && !three)) {
+          // a job, or a node for the narrower phase (which counts it)
+          int mj, nj;
+          const int64_t o = compact_tile<TILE>(A, W, D.T, D.rowbits, D.R, D.C, mj, nj);
+          if (o >= 0) {
+            if (handover)
+              walk_push(A, A.hand, false, lane, mj, nj, o, mat, dl, depth, D.coef, key_lo, key_hi);
+            else
+              walk_emit(A, W, mj, nj, o, mat, depth, D.coef, key_lo, key_hi, h_term);
           }
-        }
-        const int nch = Eq2Tile<TILE, WE>::nchildren(s);
-        const u256 pcoef = D.coef;
-        D.store_frame(rel, f, pv, pcoef);
-        __syncwarp();
-        bool failed = false;
-        if (waiting && nch > 1) {
-          // hand the other children to the waiting warps, go on with child 0
-          for (int c = 1; c < nch && !failed; ++c) {
-            if (!D.apply(rel, f, pv, c)) {
+        } else {
+          f.is_col = (int)((key >> 16) & 1);
+          f.idx = (int)(key & 0xffff);
+          f.k = s;
+          f.child = 0;
+          uint64_t line = f.is_col ? (D.colbits[f.idx] & D.R) : (D.rowbits[f.idx] & D.C);
+          for (int q = 0; q < 4; ++q) {
+            f.pos[q] = 0;
+            if (line) {
+              const int c = __ffsll((long long)line) - 1;
+              line &= line - 1;
+              f.pos[q] = c;
+              pv[q] = (int64_t)(f.is_col ? D.T[c * S + f.idx] : D.T[f.idx * S + c]);
+            }
+          }
+          const int nch = Eq2Tile<TILE, WE>::nchildren(s);
+          // every child a job: all of them written out in place; else the
+          // children after the first go to waiting warps, if any
+          const bool inplace = dl - 1 <= 0 || (mact - 1 <= cut && s < 5);
+          if (!inplace) {
+            if (rel >= A.max_rel_depth) {
+              if (lane == 0) atomicCAS(A.err, 0, WALK_FULL);
+              break;
+            }
+            D.store_frame(rel, f, pv, pcoef);
+            __syncwarp();
+          }
+          const int c1 = inplace || waiting ? nch : 1;
+          for (int c = inplace ? 0 : 1; c < c1; ++c) {
+            if (!D.apply_to(scratch, f, pv, c)) {
               failed = true;
-            } else {
+            } else if (!inplace || (D.pivot_key() >> 17) > 0) {  // a child holding a zero line is dropped
+              if (inplace && lane == 0 && depth + 1 < A.hist_len) atomicAdd(h_nodes + depth + 1, 1u);
               int mj, nj;
-              const int64_t o = compact_tile<TILE>(A, W, D, mj, nj);
+              const int64_t o = compact_tile<TILE>(A, W, D.T, D.rowbits, D.R, D.C, mj, nj);
               uint64_t klo = key_lo, khi = key_hi;
               key_set(klo, khi, depth + 1, (uint64_t)c, bpl, levels);
-              if (o >= 0) walk_push(A, lane, mj, nj, o, mat, dl - 1, depth + 1, D.coef, klo, khi);
+              if (o >= 0) {
+                if (inplace)
+                  walk_emit(A, W, mj, nj, o, mat, depth + 1, D.coef, klo, khi, h_term);
+                else
+                  walk_push(A, A.q, true, lane, mj, nj, o, mat, dl - 1, depth + 1, D.coef, klo, khi);
+              }
             }
-            D.undo_child(rel, f, pv, pcoef, c);
+            D.undo_from(scratch, f, pv, pcoef, c);
           }
-          D.set_child(rel, 1 << 8);  // child 0, the others handed over
-          __syncwarp();
-        }
-        if (failed || !D.apply(rel, f, pv, 0)) {
-          if (lane == 0) atomicCAS(A.err, 0, WALK_FULL);
-          break;
-        }
-        key_set(key_lo, key_hi, depth + 1, 0, bpl, levels);
-        ++rel;
-        descend = true;
-      }
-      if (descend) continue;
-      // ---- back up to the next child not yet walked
-      for (;;) {
-        if (rel == 0) {
-          done = true;
-          break;
-        }
-        Frame f;
-        int64_t pv[4];
-        u256 pc;
-        D.load_frame(rel - 1, f, pv, pc);
-        const int c = f.child & 0xff;
-        const bool handed = (f.child >> 8) != 0;
-        D.undo_child(rel - 1, f, pv, pc, c);
-        if (!handed && c + 1 < Eq2Tile<TILE, WE>::nchildren(f.k)) {
-          D.set_child(rel - 1, c + 1);
-          __syncwarp();
-          if (!D.apply(rel - 1, f, pv, c + 1)) {
+          if (failed) {
             if (lane == 0) atomicCAS(A.err, 0, WALK_FULL);
-            done = true;
+            break;
           }
-          key_set(key_lo, key_hi, depth0 + rel, (uint64_t)(c + 1), bpl, levels);
-          break;
+          if (!inplace) {
+            if (c1 > 1) {
+              D.set_child(rel, 1 << 8);  // child 0, the others handed over
+              __syncwarp();
+            }
+            next = 0;
+          }
         }
-        key_set(key_lo, key_hi, depth0 + rel, 0, bpl, levels);
-        --rel;
       }
+      // ---- the move: into child `next` of this node, or back up to the next child not yet walked
+      int lv = rel, c = next;
+      if (c < 0) {
+        for (;;) {
+          if (rel == 0) {
+            done = true;
+            break;
+          }
+          D.load_frame(rel - 1, f, pv, pcoef);
+          const int cc = f.child & 0xff;
+          const bool handed = (f.child >> 8) != 0;
+          D.undo_child(rel - 1, f, pv, pcoef, cc);
+          key_set(key_lo, key_hi, depth0 + rel, 0, bpl, levels);
+          if (!handed && cc + 1 < Eq2Tile<TILE, WE>::nchildren(f.k)) {
+            lv = rel - 1;
+            c = cc + 1;
+            D.set_child(lv, c);
+            __syncwarp();
+            break;
+          }
+          --rel;
+        }
+        if (done) break;
+      }
+      if (!D.apply(lv, f, pv, c)) {
+        if (lane == 0) atomicCAS(A.err, 0, WALK_FULL);
+        break;
+      }
+      key_set(key_lo, key_hi, depth0 + lv + 1, (uint64_t)c, bpl, levels);
+      rel = lv + 1;
     }
     // the subtree is done (or abandoned after an error): this warp is idle again
     __syncwarp();
@@ -456,8 +531,8 @@ __global__ void k_walk_keys_perm(const uint64_t* __restrict__ key2, const uint32
 }
 
 template <int TILE>
-cudaError_t walk_blocks_per_sm(int hist_len, int* per_sm) {
-  const size_t smem = walk_smem_bytes(TILE, hist_len);
+cudaError_t walk_blocks_per_sm(int stage_words, int hist_len, int* per_sm) {
+  const size_t smem = walk_smem_bytes(TILE, stage_words, hist_len);
   cudaError_t e = cudaFuncSetAttribute(k_expand_walk<TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_expand_walk<TILE>, WalkCfg<TILE>::WARPS * 32, smem);
@@ -466,13 +541,13 @@ cudaError_t walk_blocks_per_sm(int hist_len, int* per_sm) {
 template <int TILE>
 cudaError_t launch_walk_tile(const WalkArgs& a, int sms, int* grid, cudaStream_t s) {
   int per_sm = 0;
-  cudaError_t e = walk_blocks_per_sm<TILE>(a.hist_len, &per_sm);
+  cudaError_t e = walk_blocks_per_sm<TILE>(a.stage_words, a.hist_len, &per_sm);
   if (e != cudaSuccess) return e;
   *grid = 0;
   // every block resident at once: a waiting warp never waits on a block that has not started
   const int g = sms * per_sm;
   if (per_sm < 1 || (int64_t)g * WalkCfg<TILE>::WARPS > a.warps_cap) return cudaSuccess;
-  k_expand_walk<TILE><<<g, WalkCfg<TILE>::WARPS * 32, walk_smem_bytes(TILE, a.hist_len), s>>>(a);
+  k_expand_walk<TILE><<<g, WalkCfg<TILE>::WARPS * 32, walk_smem_bytes(TILE, a.stage_words, a.hist_len), s>>>(a);
   e = cudaGetLastError();
   if (e == cudaSuccess) *grid = g;
   return e;
@@ -482,17 +557,17 @@ cudaError_t launch_walk_tile(const WalkArgs& a, int sms, int* grid, cudaStream_t
 
 int walk_tile_for(int max_order) { return max_order <= 32 ? 32 : (max_order <= 64 ? 64 : 0); }
 
-size_t walk_smem_bytes(int tile, int hist_len) {
-  const size_t warp = tile <= 32 ? WalkCfg<32>::WARP_BYTES : WalkCfg<64>::WARP_BYTES;
+size_t walk_smem_bytes(int tile, int stage_words, int hist_len) {
   const int warps = tile <= 32 ? WalkCfg<32>::WARPS : WalkCfg<64>::WARPS;
-  return warp * warps + 3 * sizeof(int32_t) * (size_t)hist_len;
+  return walk_warp_bytes(tile, stage_words) * warps + 3 * sizeof(int32_t) * (size_t)hist_len;
 }
 
 int64_t walk_frame_words(int tile) { return tile <= 32 ? TileCfg<32, WE>::FRAME_WORDS : TileCfg<64, WE>::FRAME_WORDS; }
 
-cudaError_t walk_resident_warps(int tile, int hist_len, int sms, int64_t* warps) {
+cudaError_t walk_resident_warps(int tile, int stage_words, int hist_len, int sms, int64_t* warps) {
   int per_sm = 0;
-  cudaError_t e = tile <= 32 ? walk_blocks_per_sm<32>(hist_len, &per_sm) : walk_blocks_per_sm<64>(hist_len, &per_sm);
+  cudaError_t e = tile <= 32 ? walk_blocks_per_sm<32>(stage_words, hist_len, &per_sm)
+                             : walk_blocks_per_sm<64>(stage_words, hist_len, &per_sm);
   *warps = (int64_t)sms * per_sm * (tile <= 32 ? WalkCfg<32>::WARPS : WalkCfg<64>::WARPS);
   return e;
 }
