@@ -160,6 +160,11 @@ perm_status perm_expand(perm_plan_t* plan, perm_jobs_t** jobs, int64_t* njobs);
  * 2 = the traversal (opts.expand_walk).  PERM_ESTATE before perm_expand. */
 perm_status perm_expand_driver(perm_plan_t* plan, int32_t* driver);
 
+/* Device time of the last perm_expand (ms): events on the plan's stream
+ * around its uploads, kernels, and (traversal) key sort and gather.
+ * PERM_ESTATE before perm_expand. */
+perm_status perm_last_expand_ms(perm_plan_t* plan, float* ms);
+
 /* a4 -- Algorithm KKLLL (Section 2.3) on each job's 0/1 pattern (Section 3),
  * jobs of any order up to PERM_MAX_N:
  * log of the mean over trials of |det W|^2, W_ij a cube root of unity drawn

@@ -36,7 +36,7 @@ EXPORTED = [
     "perm_result_words", "perm_jobs_export", "perm_exact", "perm_job_features", "perm_mlp_grad",
     "perm_mlp_train", "perm_mlp_predict", "perm_mlp_attach", "perm_ubench_imad",
     "perm_status_string", "perm_last_error", "perm_leaf_batch_noalloc", "perm_eval_replay",
-    "perm_eval_subset", "perm_jobs_select", "perm_expand_driver",
+    "perm_eval_subset", "perm_jobs_select", "perm_expand_driver", "perm_last_expand_ms",
 ]
 
 
@@ -100,6 +100,7 @@ def _lib():
         lib.perm_expand.argtypes = [vp, P(vp), P(ctypes.c_int64)]
         lib.perm_estimate.argtypes = [vp, P(ctypes.c_float)]
         lib.perm_expand_driver.argtypes = [vp, P(ctypes.c_int32)]
+        lib.perm_last_expand_ms.argtypes = [vp, P(ctypes.c_float)]
         lib.perm_order.argtypes = [vp, ctypes.c_int32, P(ctypes.c_uint32)]
         lib.perm_eval_batch.argtypes = [vp, P(ctypes.c_uint32), P(perm_job_result)]
         lib.perm_eval_replay.argtypes = [vp, P(perm_job_result)]
@@ -405,6 +406,13 @@ class Plan:
     def last_eval_ms(self) -> float:
         v = ctypes.c_float()
         _ck(_lib().perm_last_eval_ms(self._h, ctypes.byref(v)), "perm_last_eval_ms")
+        return v.value
+
+    @property
+    def last_expand_ms(self) -> float:
+        """Device time of the last expansion (ms)."""
+        v = ctypes.c_float()
+        _ck(_lib().perm_last_expand_ms(self._h, ctypes.byref(v)), "perm_last_expand_ms")
         return v.value
 
     @property

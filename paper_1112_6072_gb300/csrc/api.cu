@@ -321,8 +321,10 @@ struct perm_plan {
   int32_t* d_mat_w = nullptr;
   unsigned long long* d_mat_acc = nullptr;
   perm_jobs* jobs = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last evaluation
+  cudaEvent_t xe0 = nullptr, xe1 = nullptr;  // around the last expansion
   float last_ms = 0.f;
+  float last_expand_ms = 0.f;
   int32_t last_launches = 0;
   bool evaluated = false;
   bool subset = false;  // the last evaluation covered a sub-queue (perm_eval_subset)
@@ -535,6 +537,8 @@ static perm_status perm_plan_create_impl(const perm_matrix* mats, int32_t count,
   if (e == cudaSuccess) e = cudaMemsetAsync(P->d_mat_acc, 0, 32ull * count, P->s);
   if (e == cudaSuccess) e = cudaEventCreate(&P->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&P->ev1);
+  if (e == cudaSuccess) e = cudaEventCreate(&P->xe0);
+  if (e == cudaSuccess) e = cudaEventCreate(&P->xe1);
   if (e != cudaSuccess) {
     set_last_error("plan upload", e);
     P->M.release_all();
@@ -575,6 +579,8 @@ extern "C" void perm_plan_destroy(perm_plan_t* P) {
   P->M.release_all();
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
+  if (P->xe0) cudaEventDestroy(P->xe0);
+  if (P->xe1) cudaEventDestroy(P->xe1);
   cudaStreamSynchronize(P->s);
   delete P;
 }
@@ -861,6 +867,7 @@ static perm_status perm_expand_impl(perm_plan_t* P, perm_jobs_t** jobs_out, int6
   free_jobset(P);
   P->evaluated = false;
   cudaStream_t s = P->s;
+  CK(cudaEventRecord(P->xe0, s));
   Mem& M = P->M;
   // roots
   std::vector<int32_t> rm, rnnz, rmat, rdl;
@@ -1123,6 +1130,7 @@ static perm_status finish_jobset(perm_plan* P, perm_jobs* J, perm_jobs_t** jobs_
   cudaStream_t s = P->s;
   const int64_t ncur = J->n;
   const JobArrays cur = J->a;
+  CK(cudaEventRecord(P->xe1, s));
   J->h_m.resize(ncur);
   J->h_mat.resize(ncur);
   if (ncur > 0) {
@@ -1130,6 +1138,7 @@ static perm_status finish_jobset(perm_plan* P, perm_jobs* J, perm_jobs_t** jobs_
     CK(cudaMemcpyAsync(J->h_mat.data(), cur.mat, 4 * ncur, cudaMemcpyDeviceToHost, s));
   }
   CK(cudaStreamSynchronize(s));
+  CK(cudaEventElapsedTime(&P->last_expand_ms, P->xe0, P->xe1));
   J->max_order = 0;
   for (int32_t v : J->h_m) J->max_order = std::max(J->max_order, (int)v);
   // outputs
@@ -1152,6 +1161,16 @@ static perm_status finish_jobset(perm_plan* P, perm_jobs* J, perm_jobs_t** jobs_
 }
 extern "C" perm_status perm_expand(perm_plan_t* P, perm_jobs_t** jobs_out, int64_t* njobs) {
   return guarded([&] { return perm_expand_impl(P, jobs_out, njobs); });
+}
+
+static perm_status perm_last_expand_ms_impl(perm_plan_t* P, float* ms) {
+  if (!P || !ms) return PERM_EINVAL;
+  if (P->expand_driver < 0) return PERM_ESTATE;
+  *ms = P->last_expand_ms;
+  return PERM_OK;
+}
+extern "C" perm_status perm_last_expand_ms(perm_plan_t* P, float* ms) {
+  return guarded([&] { return perm_last_expand_ms_impl(P, ms); });
 }
 
 static perm_status perm_expand_driver_impl(perm_plan_t* P, int32_t* driver) {
