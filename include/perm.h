@@ -64,7 +64,7 @@ typedef enum {
 /* A dense integer matrix in host memory, row-major: a[i * ld + j]. */
 typedef struct {
   int32_t n;          /* order, 0 <= n <= PERM_MAX_N; n = 0 has per = 1 */
-  const int64_t* a;   /* entries; |a_ij| < 2^31 */
+  const int64_t* a;   /* entries; |a_ij| < 2^31 (any int64 on the residue path, opts.modulus) */
   int64_t ld;         /* leading dimension, ld >= n */
 } perm_matrix;
 
@@ -112,6 +112,15 @@ typedef struct {
                               three-child split; otherwise, or when its buffers fill, the
                               level-by-level driver runs); 0 = level by level.  The job list is the
                               same either way */
+  uint32_t modulus;        /* 0 = exact: results in a 2^K ring proven wide enough (else
+                              PERM_EOVERFLOW).  An odd prime p < 2^31 = the residue path: every
+                              entry (any int64; reduced first), merged entry, coefficient and
+                              Ryser sum is taken modulo p (Eq. 2 and Ryser's formula are
+                              identities over any commutative ring, so per(A) mod p is exact
+                              however large per(A) is); results are residues in [0, p)
+                              (perm_result_words word 0, perm_result a non-negative value,
+                              perm_result_bits 0).  Residues for several primes and perm_crt give
+                              per(A) itself.  PERM_EINVAL if p is not an odd prime below 2^31 */
 } perm_opts;
 
 /* Fill opts with the defaults above. */
@@ -140,7 +149,9 @@ typedef struct {
  * of Section 3 is implicit), choose the exact width K per matrix and upload
  * them.  *out is owned by the library; release it with perm_plan_destroy.
  * Errors: PERM_EINVAL (count < 1, null pointers, n out of range, ld < n,
- * |a_ij| >= 2^31), PERM_EOVERFLOW (bound too large), PERM_ECUDA, PERM_ENOMEM. */
+ * |a_ij| >= 2^31 on the exact path, a modulus that is not an odd prime below
+ * 2^31), PERM_EOVERFLOW (bound too large for the exact path), PERM_ECUDA,
+ * PERM_ENOMEM. */
 perm_status perm_plan_create(const perm_matrix* mats, int32_t count, const perm_opts* opts,
                              perm_plan_t** out);
 void perm_plan_destroy(perm_plan_t* plan);
@@ -230,12 +241,28 @@ perm_status perm_result(perm_plan_t* plan, int32_t index, uint32_t* limbs, int32
                         int32_t* nlimbs, int32_t* sign);
 
 /* The number of exact low bits K of matrix `index` (results are exact
- * modulo 2^K and |per(A)| < 2^(K-1) is proven). */
+ * modulo 2^K and |per(A)| < 2^(K-1) is proven); 0 on the residue path. */
 perm_status perm_result_bits(perm_plan_t* plan, int32_t index, int32_t* bits);
 
 /* All results at once: out[i*4 .. i*4+3] = per(A_i) modulo 2^256 (two's
- * complement words, exact in the low perm_result_bits bits). */
+ * complement words, exact in the low perm_result_bits bits); on the residue
+ * path per(A_i) mod p in word 0 and zero words above. */
 perm_status perm_result_words(perm_plan_t* plan, uint64_t* out, int32_t count);
+
+/* Residue path, reconstruction -- integers from residues by the Chinese
+ * remainder theorem (Garner's mixed-radix form), for results taken modulo
+ * several primes (opts.modulus).  residues (host) holds count rows of k
+ * values, residues[v * k + i] = x_v mod primes[i] (< primes[i]); primes
+ * (host): k distinct odd primes below 2^31, 1 <= k <= 64.  Output (host):
+ * limbs[v * (k + 1) ..] = |x_v| in k + 1 little-endian uint32 limbs,
+ * signs[v] in {-1, 0, +1}.  Every x_v with |x_v| < M / 2, M the product of
+ * the primes, comes back exactly (the balanced residue).  Runs on the
+ * stream (nullable) and returns when the results are in host memory.
+ * Errors: PERM_EINVAL (k or count out of range, a prime repeated or not an
+ * odd prime below 2^31, a residue not below its prime), PERM_ECUDA,
+ * PERM_ENOMEM. */
+perm_status perm_crt(const uint32_t* residues, const uint32_t* primes, int32_t k, int32_t count,
+                     uint32_t* limbs, int32_t* signs, void* stream);
 
 /* Export the job list for inspection (two-call protocol: with sizes == NULL
  * only *total_entries is set).  sizes[w] = order, mats receives the dense

@@ -36,7 +36,7 @@ EXPORTED = [
     "perm_result_words", "perm_jobs_export", "perm_exact", "perm_job_features", "perm_mlp_grad",
     "perm_mlp_train", "perm_mlp_predict", "perm_mlp_attach", "perm_ubench_imad",
     "perm_status_string", "perm_last_error", "perm_leaf_batch_noalloc", "perm_eval_replay",
-    "perm_eval_subset", "perm_jobs_select", "perm_expand_driver", "perm_last_expand_ms",
+    "perm_eval_subset", "perm_jobs_select", "perm_expand_driver", "perm_last_expand_ms", "perm_crt",
 ]
 
 
@@ -71,7 +71,8 @@ class perm_opts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("alloc", alloc_fn_t), ("free", free_fn_t),
                 ("alloc_ctx", ctypes.c_void_p), ("timeout_ns", ctypes.c_int64),
                 ("model_uses_estimate", ctypes.c_int32), ("fused_levels", ctypes.c_int32),
-                ("dense_split", ctypes.c_int32), ("expand_walk", ctypes.c_int32)]
+                ("dense_split", ctypes.c_int32), ("expand_walk", ctypes.c_int32),
+                ("modulus", ctypes.c_uint32)]
 
 
 class perm_job_result(ctypes.Structure):
@@ -126,6 +127,8 @@ def _lib():
         lib.perm_mlp_attach.argtypes = [vp, f]
         lib.perm_ubench_imad.argtypes = [ctypes.c_int32, ctypes.c_int32, vp, f, P(ctypes.c_double)]
         lib.perm_leaf_batch_noalloc.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp]
+        lib.perm_crt.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), ctypes.c_int32, ctypes.c_int32,
+                                 P(ctypes.c_uint32), P(ctypes.c_int32), vp]
         lib.perm_status_string.argtypes = [ctypes.c_int]
         lib.perm_status_string.restype = ctypes.c_char_p
         lib.perm_last_error.argtypes = []
@@ -267,7 +270,7 @@ class Plan:
 
     def _create(self, desc, keep, split_depth=-1, leaf_size=0, order="lpt", kklll_trials=0, seed=0x5EED,
                 workers_per_sm=0, chunk_log2=0, stream=None, torch_allocator=False, timeout_ns=0,
-                model_uses_estimate=True, fused_levels=True, dense_split=False, expand_walk=True):
+                model_uses_estimate=True, fused_levels=True, dense_split=False, expand_walk=True, modulus=0):
         lib = _lib()
         self._h = None
         self._keep = keep  # the host matrices the descriptors point into
@@ -289,6 +292,7 @@ class Plan:
         o.fused_levels = 1 if fused_levels else 0
         o.dense_split = 1 if dense_split else 0
         o.expand_walk = 1 if expand_walk else 0
+        o.modulus = int(modulus)
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator()
@@ -625,3 +629,20 @@ def leaf_batch_noalloc(a_ptr, n, count, out_ptr, status_ptr, stream=None):
     _ck(_lib().perm_leaf_batch_noalloc(ctypes.c_void_p(int(a_ptr)), int(n), int(count),
                                        ctypes.c_void_p(int(out_ptr)), ctypes.c_void_p(int(status_ptr)),
                                        ctypes.c_void_p(_stream_handle(stream))), "perm_leaf_batch_noalloc")
+
+
+def crt(residues, primes, stream=None):
+    """Integers from their residues (perm_crt): residues[v][i] is value v
+    modulo primes[i] (distinct odd primes below 2^31); every value of
+    absolute value below half the product of the primes comes back exactly
+    (the balanced residue)."""
+    pr = np.ascontiguousarray(primes, dtype=np.uint32).reshape(-1)
+    k = pr.size
+    r = np.ascontiguousarray(residues, dtype=np.uint32).reshape(-1, k)
+    count = r.shape[0]
+    limbs = np.zeros((count, k + 1), dtype=np.uint32)
+    signs = np.zeros(count, dtype=np.int32)
+    u32 = ctypes.POINTER(ctypes.c_uint32)
+    _ck(_lib().perm_crt(r.ctypes.data_as(u32), pr.ctypes.data_as(u32), k, count, limbs.ctypes.data_as(u32),
+                        signs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_handle(stream)), "perm_crt")
+    return [_limbs_to_int(limbs[v], k + 1, int(signs[v])) for v in range(count)]

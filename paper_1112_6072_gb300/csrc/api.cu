@@ -330,6 +330,7 @@ struct perm_plan {
   bool subset = false;  // the last evaluation covered a sub-queue (perm_eval_subset)
   int32_t expand_driver = -1;  // driver of the last expansion: 0 levels, 1 fused levels, 2 traversal
   std::vector<float> mlp;
+  ModP mod{0u, 0u, 0u};        // p = 0: the exact ring path; else the residue path modulo p
 };
 
 // ---------------------------------------------------------------- a1: plan
@@ -428,7 +429,25 @@ static perm_status perm_plan_create_impl(const perm_matrix* mats, int32_t count,
     if (A.n < 0 || A.n > PERM_MAX_N || A.ld < A.n || (A.n > 0 && !A.a)) return PERM_EINVAL;
     maxn = std::max(maxn, A.n);
   }
+  // residue path: every entry reduced into [0, p) first (a copy); the rest
+  // of the set-up then sees residues, and no magnitude bound applies
+  std::vector<std::vector<int64_t>> red;
+  std::vector<perm_matrix> red_mats;
+  if (o.modulus) {
+    if (!modp_is_odd_prime(o.modulus)) return PERM_EINVAL;
+    red.resize(count);
+    red_mats.resize(count);
+    parallel_for(count, [&](int32_t i) {
+      const perm_matrix& A = mats[i];
+      red[i].resize((size_t)A.n * A.n + 1);
+      for (int r = 0; r < A.n; ++r)
+        for (int c = 0; c < A.n; ++c) red[i][(size_t)r * A.n + c] = mod_of(A.a[(size_t)r * A.ld + c], o.modulus);
+      red_mats[i] = perm_matrix{A.n, red[i].data(), std::max<int32_t>(A.n, 1)};
+    });
+    mats = red_mats.data();
+  }
   perm_plan* P = new perm_plan();
+  P->mod = o.modulus ? modp_make(o.modulus) : ModP{0u, 0u, 0u};
   P->opts = o;
   P->s = (cudaStream_t)o.stream;
   P->M.opts = o;
@@ -486,6 +505,12 @@ static perm_status perm_plan_create_impl(const perm_matrix* mats, int32_t count,
       P->trivial[i] = 1;
       P->w[i] = 2;
       P->kbits[i] = 64;
+      return;
+    }
+    if (o.modulus) {  // results are residues: one ring width, no bound
+      P->w[i] = 2;
+      P->kbits[i] = 0;
+      P->h_nnz[i] = count_nnz(A);
       return;
     }
     bool binary;
@@ -738,6 +763,7 @@ static perm_status expand_by_walk(perm_plan* P, perm_jobs* J, WalkRoots R, int m
   // an idle warp waits for the others' remaining work: at least a second,
   // whatever the evaluation watchdog
   A.timeout_ns = std::max<int64_t>(P->opts.timeout_ns > 0 ? P->opts.timeout_ns : 10000000000ll, 1000000000ll);
+  A.mod = P->mod.p;
   // roots: blocks back to back at the start of the arena, queue slots [0, nroots)
   std::vector<uint64_t> coef(4 * nroots, 0ull), key(2 * nroots, 0ull);
   std::vector<int32_t> depth0(nroots, 0), ones(nroots, 1);
@@ -1002,6 +1028,7 @@ static perm_status perm_expand_impl(perm_plan_t* P, perm_jobs_t** jobs_out, int6
       }
       F.cap_jobs = cap_jobs;
       F.cap_words = cap_words;
+      F.mod = P->mod.p;
       F.slots = slots.view();
       F.valid = reinterpret_cast<int32_t*>(g_valid.p);
       F.kslots = K;
@@ -1083,6 +1110,7 @@ static perm_status perm_expand_impl(perm_plan_t* P, perm_jobs_t** jobs_out, int6
     A.kslots = K;
     A.leaf_size = P->L;
     A.split_floor = split_floor(max_open);
+    A.mod = P->mod.p;
     A.err = reinterpret_cast<int32_t*>(d_stat);
     CK(launch_expand_level(A, max_order, s));
     CK(scan_exclusive_i32(valid, pos, K * ncur, g_tmp.p, g_tmp.cap, s));
@@ -1350,7 +1378,7 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order, int64_t nq_
   if (!E.d_g || !keys || !vals || !sort_tmp) return PERM_ENOMEM;
   std::vector<unsigned long long> h(EVAL_KEYS, 0ull);
   if (n) {
-    CK(launch_eval_keys(E.d_q, n, J->a, J->arena, P->d_mat_w, leaf_max, keys, vals, hist, s));
+    CK(launch_eval_keys(E.d_q, n, J->a, J->arena, P->d_mat_w, leaf_max, P->mod.p != 0, keys, vals, hist, s));
     CK(sort_asc_u32(keys, keys + n, vals, E.d_g, n, 7, sort_tmp, sort_b, s));
     CK(cudaMemcpyAsync(h.data(), hist, 8 * EVAL_KEYS, cudaMemcpyDeviceToHost, s));
   }
@@ -1429,6 +1457,7 @@ static DfsArgs dfs_args(perm_jobs* J, int g, const uint32_t* queue, int64_t nq) 
   D.timeout_ns = P->opts.timeout_ns > 0 ? P->opts.timeout_ns : 10000000000ll;
   D.three = P->opts.dense_split ? 1 : 0;
   D.max_depth = E.frames;
+  D.mod = P->mod;
   return D;
 }
 
@@ -1471,10 +1500,10 @@ static cudaError_t eval_enqueue(perm_jobs* J, cudaStream_t s) {
       const int64_t o = E.groups[g].first;
       EQ(launch_leaf_batch(E.d_lq + o, E.groups[g].second, E.group_cls[g], E.prefix + o, E.owner, o, J->a,
                            J->arena, E.chunk,
-                           E.ctr, J->out, P->sms, s));
+                           E.ctr, J->out, P->mod, P->sms, s));
       ++launches;
     }
-    EQ(launch_leaf_finalize(E.d_lq, E.nl, J->a, J->out, P->d_mat_acc, s));
+    EQ(launch_leaf_finalize(E.d_lq, E.nl, J->a, J->out, P->d_mat_acc, P->mod.p, s));
     ++launches;
   }
   if (E.nd > 0 && !E.wide_first) {
@@ -1667,7 +1696,10 @@ static perm_status result_words(perm_plan* P, std::vector<uint64_t>& words) {
       o[0] = 1;
       continue;
     }
-    low_bits_signed(&raw[4ull * i], P->kbits[i], o);
+    if (P->mod.p)
+      o[0] = raw[4ull * i] % P->mod.p;  // a sum of residues: the residue of per(A_i)
+    else
+      low_bits_signed(&raw[4ull * i], P->kbits[i], o);
   }
   return PERM_OK;
 }
@@ -1686,7 +1718,7 @@ extern "C" perm_status perm_result_words(perm_plan_t* P, uint64_t* out, int32_t 
 
 static perm_status perm_result_bits_impl(perm_plan_t* P, int32_t index, int32_t* bits) {
   if (!P || !bits || index < 0 || index >= P->count) return PERM_EINVAL;
-  *bits = P->kbits[index];
+  *bits = P->mod.p ? 0 : P->kbits[index];  // residues carry no ring width
   return PERM_OK;
 }
 extern "C" perm_status perm_result_bits(perm_plan_t* P, int32_t index, int32_t* bits) {

@@ -20,7 +20,9 @@
 // Variants: tile entries int32 (more warps per SM) or int64, and leaves of
 // up to 16 or up to 32 rows.  A job that the narrow variant cannot hold (an
 // entry leaving int32, a leaf above 16 rows) reports DFS_RETRY and the host
-// runs it again on the int64 / 32-row variant.
+// runs it again on the int64 / 32-row variant.  On the residue path (W = 0)
+// the entries are residues modulo a prime p and the leaves take the modular
+// walk of ryser_mod.cuh.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -28,6 +30,7 @@
 #include "internal.h"
 #include "ryser.cuh"
 #include "ryser4.cuh"
+#include "ryser_mod.cuh"
 #include "tile.cuh"
 #include "wide.cuh"
 
@@ -108,10 +111,73 @@ struct Dfs : Eq2Tile<TILE, E> {
   int32_t* delta;
   int32_t* rho0;
   uint32_t* cmask;
+  ModP mod;
 
   // Ryser on the active sub-matrix; adds coef * per into acc (lane 0).
   // Returns a status: 0, PERM_EOVERFLOW, PERM_EINVAL, or DFS_RETRY.
   __device__ int leaf(u256& acc) {
+    if constexpr (W == 0)
+      return leaf_mod(acc);
+    else
+      return leaf_ring(acc);
+  }
+
+  // The residue path: acc.w[0] = (acc.w[0] + coef * per) mod p.
+  __device__ int leaf_mod(u256& acc) {
+    const uint32_t p = mod.p;
+    const int m = __popcll(R);
+    if (m == 1) {
+      const int r = __ffsll((long long)R) - 1, c = __ffsll((long long)C) - 1;
+      if (lane == 0) acc.w[0] = (acc.w[0] + coef.w[0] % p * (uint64_t)(uint32_t)T[r * S + c]) % p;
+      return 0;
+    }
+    if (m > PERM_MAX_LEAF) return PERM_EINVAL;
+    if (m > LN) return DFS_RETRY;
+    const int nmax = LN <= 16 ? 16 : nmax_for(m);
+    uint32_t* d = reinterpret_cast<uint32_t*>(delta);
+    uint32_t* r0 = reinterpret_cast<uint32_t*>(rho0);
+    const int cols = m - 1;
+    for (int k = lane; k < cols * nmax; k += 32) d[k] = 0;
+    __syncwarp();
+    if (lane < m) {
+      const int myrow = nth_bit(R, lane);
+      uint64_t cm = rowbits[myrow] & C;
+      uint32_t rs = 0, last = 0;
+      while (cm) {
+        const int c = __ffsll((long long)cm) - 1;
+        cm &= cm - 1;
+        const int jj = __popcll(C & (bit64(c) - 1));  // leaf column of c
+        const uint32_t a = (uint32_t)T[myrow * S + c];
+        rs = mod_add(rs, a, p);
+        if (jj < cols) d[jj * nmax + lane] = to_mont(mod_add(a, a, p), mod); else last = a;
+      }
+      r0[lane] = to_mont(mod_sub(mod_add(last, last, p), rs, p), mod);
+    }
+    for (int i = m + lane; i < nmax; i += 32) r0[i] = to_mont(1u, mod);
+    __syncwarp();
+    const int e = m - 1;
+    const int lanes = e <= 5 ? 1 << (e - 1) : 32;
+    const uint64_t cnt = e <= 5 ? 2 : 1ull << (e - 5);
+    const uint64_t gb = (uint64_t)lane * cnt, mc = lane < lanes ? cnt : 0;
+    uint32_t sg;
+    if constexpr (LN <= 16) {
+      sg = ryser_lane_mod<16>(d, r0, m, gb, mc, mod);
+    } else {
+      if (nmax == 8) sg = ryser_lane_mod<8>(d, r0, m, gb, mc, mod);
+      else if (nmax == 16) sg = ryser_lane_mod<16>(d, r0, m, gb, mc, mod);
+      else if (nmax == 24) sg = ryser_lane_mod<24>(d, r0, m, gb, mc, mod);
+      else sg = ryser_lane_mod<32>(d, r0, m, gb, mc, mod);
+    }
+    sg = warp_sum_mod(sg, p);
+    if (lane == 0) {
+      const uint32_t per = nw_per_mod(from_mont(sg, mod), m, p);
+      acc.w[0] = (acc.w[0] + (uint64_t)per * (coef.w[0] % p)) % p;
+    }
+    __syncwarp();
+    return 0;
+  }
+
+  __device__ int leaf_ring(u256& acc) {
     const int m = __popcll(R);
     if (m == 1) {
       const int r = __ffsll((long long)R) - 1, c = __ffsll((long long)C) - 1;
@@ -272,6 +338,8 @@ __global__ void __launch_bounds__(DfsCfg<TILE, E>::WARPS * 32, DfsCfg<TILE, E>::
   const int64_t gwarp = (int64_t)blockIdx.x * Cfg::WARPS + wib;
   D.undo = A.undo + gwarp * A.undo_words_per_warp;
   D.lane = lane;
+  D.mod = A.mod;
+  D.modp = A.mod.p;
   const int cut = A.leaf_size > 2 ? A.leaf_size : 2;
 
   for (;;) {
@@ -444,6 +512,7 @@ cudaError_t launch_dfs_w(const DfsArgs& a, int tile, bool wide, int num_sms, int
 
 cudaError_t launch_dfs(const DfsArgs& a, int tile, bool wide, int W, int num_sms, int warps_per_sm, cudaStream_t s) {
   if (a.nq <= 0) return cudaSuccess;
+  if (a.mod.p) return launch_dfs_w<0>(a, tile, wide, num_sms, warps_per_sm, s);
   if (W == 2) return launch_dfs_w<2>(a, tile, wide, num_sms, warps_per_sm, s);
   return launch_dfs_w<4>(a, tile, wide, num_sms, warps_per_sm, s);
 }

@@ -6,9 +6,16 @@
 #include <cstdint>
 
 #include "jobs.cuh"
+#include "modp.cuh"
 
-// checked a*x + b*y in int64
-__device__ __forceinline__ bool mad2_checked(int64_t a, int64_t x, int64_t b, int64_t y, int64_t& out) {
+// checked a*x + b*y in int64; with a modulus (the residue path, all four
+// operands residues) the result reduced modulo it, which cannot overflow
+__device__ __forceinline__ bool mad2_checked(int64_t a, int64_t x, int64_t b, int64_t y, int64_t& out,
+                                             uint32_t mod = 0) {
+  if (mod) {
+    out = (int64_t)mod_mad2((uint64_t)a, (uint64_t)x, (uint64_t)b, (uint64_t)y, mod);
+    return true;
+  }
   __int128 r = (__int128)a * x + (__int128)b * y;
   out = (int64_t)r;
   return r == (__int128)out;
@@ -23,6 +30,7 @@ struct ChildSpec {
   int64_t fac;    // scalar factor (minor)
   int zcol, zidx; // merge 3: pivot is a column (1) or a row (0), and its index
   int zp[4];      // merge 3: the cleared positions along the pivot line
+  uint32_t mod;   // 0, or the residue path's modulus (merged entries reduced modulo it)
 };
 
 constexpr int kNone = 1 << 30;
@@ -41,7 +49,7 @@ __device__ __forceinline__ bool child_row(const CsrView& v, const ChildSpec& cs,
       if (c == cs.q) xq = v.val[t];
     }
     int64_t mv;
-    ok = mad2_checked(cs.a, xq, cs.b, xp, mv);
+    ok = mad2_checked(cs.a, xq, cs.b, xp, mv, cs.mod);
     bool done = false;
     for (int t = b; t < e; ++t) {
       const int c = v.col[t];
@@ -76,7 +84,7 @@ __device__ __forceinline__ bool child_row(const CsrView& v, const ChildSpec& cs,
       const int64_t xq = cj == c ? v.val[j++] : 0;
       if (c == cs.del_col) continue;
       int64_t mv;
-      if (!mad2_checked(cs.a, xq, cs.b, xp, mv)) ok = false;
+      if (!mad2_checked(cs.a, xq, cs.b, xp, mv, cs.mod)) ok = false;
       if (mv != 0) emit(c - (c > cs.del_col), mv);
     }
   } else {

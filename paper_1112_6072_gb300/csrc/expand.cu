@@ -118,6 +118,7 @@ struct ExpandCtx {
   int32_t leaf_size;
   int32_t split_floor;            // parents of a lower order wait for a later level
   int32_t kslots;                 // child slots per parent: 2, or 3 with the three-child option
+  uint32_t mod;                   // 0, or the residue path's modulus
   int32_t* err;
 };
 
@@ -294,6 +295,7 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, const Grp<LW>& G, i
     }
     const int mc = kind == 3 ? m : m - 1;
     ChildSpec cs;
+    cs.mod = X.mod;
     cs.fac = 1;
     cs.merge = 0;
     cs.p = cs.q = 0;
@@ -399,7 +401,13 @@ __device__ void expand_parent(const ExpandCtx& X, int64_t p, const Grp<LW>& G, i
         X.child.off[slot] = o;
         X.child.mat[slot] = X.parent.mat[p];
         X.child.depth_left[slot] = dl - 1;
-        u256 cc = cs.fac == 1 ? pcoef : u256_mul_s64(pcoef, cs.fac);
+        u256 cc = pcoef;
+        if (cs.fac != 1) {
+          if (X.mod)
+            cc.w[0] = pcoef.w[0] % X.mod * (uint64_t)cs.fac % X.mod;  // residues: the upper words stay 0
+          else
+            cc = u256_mul_s64(pcoef, cs.fac);
+        }
         for (int w = 0; w < 4; ++w) X.child.coef[4 * slot + w] = cc.w[w];
         wm.order = max(wm.order, mc);
         if (dl - 1 > 0 && mc > cut) wm.open = max(wm.open, mc);
@@ -426,6 +434,7 @@ __global__ void __launch_bounds__(kLevelWarps * 32) k_expand_level(ExpandLevelAr
   X.leaf_size = A.leaf_size;
   X.split_floor = A.split_floor;
   X.kslots = A.kslots;
+  X.mod = A.mod;
   X.err = A.err;
   const int64_t nwarps = (int64_t)gridDim.x * kLevelWarps;
   WarpMax wm;  // unused: the compaction takes the level's maxima
@@ -544,6 +553,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_expand_front(ExpandFrontArgs 
     X.leaf_size = F.leaf_size;
     X.split_floor = F.adaptive ? S.max_open - F.band : 0;
     X.kslots = F.kslots;
+    X.mod = F.mod;
     X.err = F.err;
     const int64_t p0 = S.ncur * b / G, p1 = S.ncur * (b + 1) / G;
     WarpMax wm;

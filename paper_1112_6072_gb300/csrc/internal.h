@@ -8,6 +8,7 @@
 
 #include "../../include/perm.h"
 #include "jobs.cuh"
+#include "modp.cuh"
 
 // Evaluation keys of a queue: leaf jobs (order <= leaf_max) get their kernel
 // variant (nmax index | W bit | path << 3, < 64), the others the
@@ -56,8 +57,9 @@ cudaError_t launch_retry_collect(const uint32_t* dq, int64_t n, RetryBounds boun
 // ---- K2 leaf batch -----------------------------------------------------------
 // Evaluation key (see EVAL_KEY_DFS) of every queue position, the queue's
 // jobs in vals, and the key histogram (zero it first, EVAL_KEYS entries).
+// modular: the residue path (every leaf job takes the modular variant).
 cudaError_t launch_eval_keys(const uint32_t* queue, int64_t n, const JobArrays& jobs, const uint64_t* arena,
-                             const int32_t* mat_w, int leaf_max, uint32_t* keys, uint32_t* vals,
+                             const int32_t* mat_w, int leaf_max, bool modular, uint32_t* keys, uint32_t* vals,
                              unsigned long long* hist, cudaStream_t stream);
 // Ryser tasks of every queued leaf job, their exclusive scan (nq + 1
 // entries) and the task owner map: owner[t] = queue position of task t's job
@@ -68,14 +70,16 @@ cudaError_t launch_leaf_tasks(const uint32_t* queue, int64_t nq, const JobArrays
 uint64_t leaf_tasks_host(int m, int chunk_log2);
 // One variant group of leaf jobs in queue order: the group starts at queue
 // position qbase of the grouped queue; queue and prefix are its slices (nq
-// and nq + 1 entries), owner the whole map.
+// and nq + 1 entries), owner the whole map.  mod: the modulus of the
+// residue path (used by the modular variant only).
 cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int cls, const uint64_t* prefix,
                               const uint32_t* owner, int64_t qbase, const JobArrays& jobs, const uint64_t* arena,
-                              int chunk_log2, unsigned long long* task_counter, const JobOut& out, int num_sms,
-                              cudaStream_t stream);
-// Sigma -> coef * per for every leaf job, summed into the matrix accumulators.
+                              int chunk_log2, unsigned long long* task_counter, const JobOut& out, const ModP& mod,
+                              int num_sms, cudaStream_t stream);
+// Sigma -> coef * per for every leaf job, summed into the matrix accumulators
+// (modp != 0: residues modulo modp).
 cudaError_t launch_leaf_finalize(const uint32_t* queue, int64_t nq, const JobArrays& jobs, const JobOut& out,
-                                 unsigned long long* mat_acc, cudaStream_t stream);
+                                 unsigned long long* mat_acc, uint32_t modp, cudaStream_t stream);
 
 // ---- K1 expansion (one level) ---------------------------------------------------
 // Parents [0, np) in arena_in.  Children go to slots Kp .. Kp + K - 1 of the
@@ -93,6 +97,7 @@ struct ExpandLevelArgs {
   int32_t kslots;
   int32_t leaf_size;
   int32_t split_floor;  // parents of a lower order (with depth left, above the leaf order) wait
+  uint32_t mod;     // 0, or the residue path's modulus: entries and coefficients reduced modulo it
   int32_t* err;     // device flag: first error status
 };
 cudaError_t launch_expand_level(const ExpandLevelArgs& a, int max_order, cudaStream_t s);
@@ -140,6 +145,7 @@ struct ExpandFrontArgs {
   unsigned long long* lvl_words;
   int32_t* lvl_maxo;
   int32_t* lvl_maxopen;
+  uint32_t mod;     // as in ExpandLevelArgs
   int32_t* err;
 };
 // *grid = blocks launched, 0 when the device has no cooperative launch (the
@@ -205,6 +211,7 @@ struct WalkArgs {
   int32_t max_rel_depth;  // frames per warp
   int64_t warps_cap;
   int64_t timeout_ns;
+  uint32_t mod;     // as in ExpandLevelArgs
   int32_t* err;
 };
 // tile width for roots of this order (0: above the tiles; use the level-by-level driver)
@@ -238,6 +245,7 @@ struct DfsArgs {
   int64_t timeout_ns;
   int32_t three;          // s >= 5 nodes split by Eq. 2's three children (else leaves)
   int32_t max_depth;      // undo frames per warp
+  ModP mod;               // p = 0: the ring path; else every value modulo p (W is ignored)
 };
 // Internal job status of the narrow depth-first variant (int32 tile, leaves
 // up to 16 rows): the job needs the wide variant (int64 tile, leaves up to 32).

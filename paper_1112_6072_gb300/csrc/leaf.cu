@@ -9,8 +9,9 @@
 // (8/16/24/32 rows), ring width W (2 or 4 words) and path -- the blocked
 // walk of ryser4.cuh with 8 or 16 "N" slots when the row sums fit 7 bits
 // and the two sparsest columns touch at most 16 rows, else the plain walk
-// of ryser.cuh with the 7-, 15- or 31-bit product tree.  Each variant is its
-// own kernel, so each gets the registers it needs and no more.
+// of ryser.cuh with the 7-, 15- or 31-bit product tree.  On the residue
+// path every leaf takes the modular walk of ryser_mod.cuh.  Each variant is
+// its own kernel, so each gets the registers it needs and no more.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -19,13 +20,14 @@
 #include "jobs.cuh"
 #include "ryser.cuh"
 #include "ryser4.cuh"
+#include "ryser_mod.cuh"
 
 namespace {
 
 constexpr int LEAF_WARPS = 8;  // warps per block
 
 // path codes
-constexpr int P_G7 = 0, P_G15 = 1, P_G31 = 2, P_F8 = 3, P_F16 = 4, P_BAD = 7;
+constexpr int P_G7 = 0, P_G15 = 1, P_G31 = 2, P_F8 = 3, P_F16 = 4, P_MOD = 5, P_BAD = 7;
 
 struct LeafSmem {
   int32_t delta[LEAF_WARPS][(PERM_MAX_LEAF - 1) * 32];
@@ -83,8 +85,9 @@ __global__ void k_leaf_task_counts(const uint32_t* __restrict__ queue, int64_t n
 
 // Kernel variant of a leaf job: nmax index | W (4 -> bit 2) | path << 3.
 __device__ int leaf_class(uint32_t job, const JobArrays& jobs, const uint64_t* __restrict__ arena,
-                          const int32_t* __restrict__ mat_w) {
+                          const int32_t* __restrict__ mat_w, bool modular) {
   const int m = jobs.m[job];
+  if (modular) return (m <= 8 ? 0 : (m <= 16 ? 1 : (m <= 24 ? 2 : 3))) | (P_MOD << 3);
   const int nnz = jobs.nnz[job];
   CsrView v = csr_view(arena, jobs.off[job], m, nnz);
   uint32_t cm[PERM_MAX_LEAF];  // rows holding a nonzero, per column
@@ -133,7 +136,7 @@ __device__ int leaf_class(uint32_t job, const JobArrays& jobs, const uint64_t* _
 // EVAL_KEY_DFS + 2 * (order <= 32) + (W == 4) -- and a histogram of the keys.
 __global__ void k_eval_keys(const uint32_t* __restrict__ queue, int64_t n, JobArrays jobs,
                             const uint64_t* __restrict__ arena, const int32_t* __restrict__ mat_w, int leaf_max,
-                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                            bool modular, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                             unsigned long long* __restrict__ hist) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool act = q < n;
@@ -142,7 +145,7 @@ __global__ void k_eval_keys(const uint32_t* __restrict__ queue, int64_t n, JobAr
     const uint32_t job = queue[q];
     const int m = jobs.m[job];
     if (m <= leaf_max)
-      key = (uint32_t)leaf_class(job, jobs, arena, mat_w);
+      key = (uint32_t)leaf_class(job, jobs, arena, mat_w, modular);
     else
       key = EVAL_KEY_DFS + (m <= 32 ? 2u : 0u) + (mat_w[jobs.mat[job]] == 4 ? 1u : 0u);
     keys[q] = key;
@@ -233,11 +236,36 @@ __device__ void load_blocked(const uint64_t* __restrict__ arena, int64_t off, in
   __syncwarp();
 }
 
+// Load a leaf for the modular walk: as load_plain, with the entries (residues
+// in [0, p)) doubled and summed modulo p and stored in Montgomery form.
+__device__ void load_mod(const uint64_t* __restrict__ arena, int64_t off, int m, int nnz, int nmax, uint32_t* delta,
+                         uint32_t* rho0, int lane, const ModP& M) {
+  CsrView v = csr_view(arena, off, m, nnz);
+  const int cols = m - 1;
+  for (int k = lane; k < cols * nmax; k += 32) delta[k] = 0;
+  __syncwarp();
+  for (int i = lane; i < nmax; i += 32) {
+    if (i >= m) {
+      rho0[i] = to_mont(1u, M);
+      continue;
+    }
+    uint32_t rs = 0, last = 0;
+    for (int p = v.rowptr[i]; p < v.rowptr[i + 1]; ++p) {
+      const int c = v.col[p];
+      const uint32_t a = (uint32_t)v.val[p];
+      rs = mod_add(rs, a, M.p);
+      if (c < cols) delta[c * nmax + i] = to_mont(mod_add(a, a, M.p), M); else last = a;
+    }
+    rho0[i] = to_mont(mod_sub(mod_add(last, last, M.p), rs, M.p), M);
+  }
+  __syncwarp();
+}
+
 template <int NMAX, int W, int PATH>
 __global__ void __launch_bounds__(LEAF_WARPS * 32)
     k_leaf_batch(const uint32_t* __restrict__ queue, int64_t nq, const uint64_t* __restrict__ prefix,
                  const uint32_t* __restrict__ owner, int64_t qbase, JobArrays jobs, const uint64_t* __restrict__ arena, int chunk_log2,
-                 unsigned long long* __restrict__ task_counter, JobOut out) {
+                 unsigned long long* __restrict__ task_counter, JobOut out, ModP mod) {
   __shared__ __align__(16) LeafSmem sm;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -265,7 +293,10 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32)
       cur_q = q;
       m = jobs.m[job];
       if (m >= 2) {
-        if (PATH == P_F8 || PATH == P_F16)
+        if constexpr (PATH == P_MOD)
+          load_mod(arena, jobs.off[job], m, jobs.nnz[job], NMAX, reinterpret_cast<uint32_t*>(delta),
+                   reinterpret_cast<uint32_t*>(rho0), lane, mod);
+        else if (PATH == P_F8 || PATH == P_F16)
           load_blocked(arena, jobs.off[job], m, jobs.nnz[job], NMAX, delta, rho0, sm.colcnt[wib], lane);
         else
           load_plain(arena, jobs.off[job], m, jobs.nnz[job], NMAX, delta, rho0, lane);
@@ -287,7 +318,11 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32)
       const uint64_t cnt = 1ull << clog;
       const uint64_t gb = (lt * 32 + lane) * cnt;
       const uint64_t mycnt = lane < lanes ? cnt : 0;  // idle lanes of small jobs contribute zero
-      if (PATH == P_F8 && m >= 3) {
+      if constexpr (PATH == P_MOD) {
+        const uint32_t sm_ = ryser_lane_mod<NMAX>(reinterpret_cast<const uint32_t*>(delta),
+                                                  reinterpret_cast<const uint32_t*>(rho0), m, gb, mycnt, mod);
+        words[0] = from_mont(warp_sum_mod(sm_, mod.p), mod);  // Sigma mod p, a plain residue
+      } else if (PATH == P_F8 && m >= 3) {
         run_lane4<NMAX, 8, W>(delta, rho0, m, gb, mycnt, words);
       } else if (PATH == P_F16 && m >= 3) {
         if constexpr (NMAX >= 16) run_lane4<NMAX, 16, W>(delta, rho0, m, gb, mycnt, words);
@@ -319,8 +354,10 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32)
 // Leaf jobs: Sigma -> per(job) = (-1)^(m-1) Sigma / 2^(m-1), times the
 // job's coefficient; the result replaces acc[job] and is added into the
 // job's matrix accumulator (Algorithm PH, Step 4).
+// On the residue path (modp != 0) Sigma is a residue (the sum of the
+// tasks' residues in word 0) and so is the result.
 __global__ void k_leaf_finalize(const uint32_t* __restrict__ queue, int64_t nq, JobArrays jobs,
-                                JobOut out, unsigned long long* __restrict__ mat_acc) {
+                                JobOut out, unsigned long long* __restrict__ mat_acc, uint32_t modp) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   u256 v = u256_zero();
   int mat = -1;
@@ -329,15 +366,20 @@ __global__ void k_leaf_finalize(const uint32_t* __restrict__ queue, int64_t nq, 
     mat = jobs.mat[job];
     if (out.status[job] == 0) {
       const int m = jobs.m[job];
-      u256 s;
-      for (int k = 0; k < 4; ++k) s.w[k] = out.acc[4ll * job + k];
-      if (m >= 2) {
-        s = u256_shr(s, m - 1);
-        if ((m - 1) & 1) s = u256_neg(s);
+      if (modp) {
+        const uint32_t per = nw_per_mod((uint32_t)(out.acc[4ll * job] % modp), m, modp);
+        v.w[0] = (uint64_t)per * (jobs.coef[4ll * job] % modp) % modp;
+      } else {
+        u256 s;
+        for (int k = 0; k < 4; ++k) s.w[k] = out.acc[4ll * job + k];
+        if (m >= 2) {
+          s = u256_shr(s, m - 1);
+          if ((m - 1) & 1) s = u256_neg(s);
+        }
+        u256 c;
+        for (int k = 0; k < 4; ++k) c.w[k] = jobs.coef[4ll * job + k];
+        v = u256_mul(s, c);
       }
-      u256 c;
-      for (int k = 0; k < 4; ++k) c.w[k] = jobs.coef[4ll * job + k];
-      v = u256_mul(s, c);
       for (int k = 0; k < 4; ++k) out.acc[4ll * job + k] = v.w[k];
       out.nodes[job] = 1;
     }
@@ -362,7 +404,8 @@ __global__ void k_leaf_reject(const uint32_t* __restrict__ queue, int64_t nq, Jo
 template <int NMAX, int W, int PATH>
 cudaError_t launch_variant(const uint32_t* queue, int64_t nq, const uint64_t* prefix, const uint32_t* owner,
                            int64_t qbase, const JobArrays& jobs, const uint64_t* arena, int chunk_log2,
-                           unsigned long long* task_counter, const JobOut& out, int num_sms, cudaStream_t stream) {
+                           unsigned long long* task_counter, const JobOut& out, const ModP& mod, int num_sms,
+                           cudaStream_t stream) {
   static int per_sm = 0;
   if (per_sm == 0) {
     cudaError_t e =
@@ -371,16 +414,17 @@ cudaError_t launch_variant(const uint32_t* queue, int64_t nq, const uint64_t* pr
     if (per_sm < 1) per_sm = 1;
   }
   k_leaf_batch<NMAX, W, PATH><<<num_sms * per_sm, LEAF_WARPS * 32, 0, stream>>>(
-      queue, nq, prefix, owner, qbase, jobs, arena, chunk_log2, task_counter, out);
+      queue, nq, prefix, owner, qbase, jobs, arena, chunk_log2, task_counter, out, mod);
   return cudaGetLastError();
 }
 
-#define LEAF_ARGS queue, nq, prefix, owner, qbase, jobs, arena, chunk_log2, task_counter, out, num_sms, stream
+#define LEAF_ARGS queue, nq, prefix, owner, qbase, jobs, arena, chunk_log2, task_counter, out, mod, num_sms, stream
 
 template <int NMAX, int W>
 cudaError_t launch_path(int path, const uint32_t* queue, int64_t nq, const uint64_t* prefix, const uint32_t* owner,
                         int64_t qbase, const JobArrays& jobs, const uint64_t* arena, int chunk_log2,
-                        unsigned long long* task_counter, const JobOut& out, int num_sms, cudaStream_t stream) {
+                        unsigned long long* task_counter, const JobOut& out, const ModP& mod, int num_sms,
+                        cudaStream_t stream) {
   switch (path) {
     case P_G7: return launch_variant<NMAX, W, P_G7>(LEAF_ARGS);
     case P_G15: return launch_variant<NMAX, W, P_G15>(LEAF_ARGS);
@@ -389,6 +433,9 @@ cudaError_t launch_path(int path, const uint32_t* queue, int64_t nq, const uint6
     case P_F16:
       if constexpr (NMAX >= 16) return launch_variant<NMAX, W, P_F16>(LEAF_ARGS);
       return cudaErrorInvalidValue;
+    case P_MOD:  // one ring width: the residues need none
+      if constexpr (W == 2) return launch_variant<NMAX, 2, P_MOD>(LEAF_ARGS);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }
@@ -396,11 +443,11 @@ cudaError_t launch_path(int path, const uint32_t* queue, int64_t nq, const uint6
 }  // namespace
 
 cudaError_t launch_eval_keys(const uint32_t* queue, int64_t n, const JobArrays& jobs, const uint64_t* arena,
-                             const int32_t* mat_w, int leaf_max, uint32_t* keys, uint32_t* vals,
+                             const int32_t* mat_w, int leaf_max, bool modular, uint32_t* keys, uint32_t* vals,
                              unsigned long long* hist, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  k_eval_keys<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(queue, n, jobs, arena, mat_w, leaf_max, keys, vals,
-                                                               hist);
+  k_eval_keys<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(queue, n, jobs, arena, mat_w, leaf_max, modular, keys,
+                                                               vals, hist);
   return cudaGetLastError();
 }
 
@@ -430,7 +477,7 @@ uint64_t leaf_tasks_host(int m, int chunk_log2) {
 cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int cls, const uint64_t* prefix,
                               const uint32_t* owner, int64_t qbase, const JobArrays& jobs, const uint64_t* arena,
                               int chunk_log2,
-                              unsigned long long* task_counter, const JobOut& out, int num_sms,
+                              unsigned long long* task_counter, const JobOut& out, const ModP& mod, int num_sms,
                               cudaStream_t stream) {
   if (nq <= 0) return cudaSuccess;
   const int path = cls >> 3;
@@ -458,8 +505,8 @@ cudaError_t launch_leaf_batch(const uint32_t* queue, int64_t nq, int cls, const 
 }
 
 cudaError_t launch_leaf_finalize(const uint32_t* queue, int64_t nq, const JobArrays& jobs, const JobOut& out,
-                                 unsigned long long* mat_acc, cudaStream_t stream) {
+                                 unsigned long long* mat_acc, uint32_t modp, cudaStream_t stream) {
   if (nq <= 0) return cudaSuccess;
-  k_leaf_finalize<<<(unsigned)((nq + 255) / 256), 256, 0, stream>>>(queue, nq, jobs, out, mat_acc);
+  k_leaf_finalize<<<(unsigned)((nq + 255) / 256), 256, 0, stream>>>(queue, nq, jobs, out, mat_acc, modp);
   return cudaGetLastError();
 }

@@ -9,10 +9,13 @@
 // restores it.  Nonzero patterns are kept as bit masks per row (rowbits) and
 // per column (colbits), so a line count is one popcount against the active
 // masks.  With the three-child option, Eq. 2's third child clears the pivot
-// line's first four entries in place (the frame holds their values).
+// line's first four entries in place (the frame holds their values).  On
+// the residue path (modp != 0) the entries are residues modulo modp and
+// merged entries and coefficients are reduced modulo modp.
 #pragma once
 #include <cstdint>
 
+#include "modp.cuh"
 #include "wide.cuh"
 
 template <int TILE, typename E>
@@ -65,6 +68,23 @@ struct Eq2Tile {
   int lane;
   uint64_t R, C;
   u256 coef;
+  uint32_t modp = 0;  // 0: exact entries; else residues modulo this prime
+
+  // a*x + b*y into a tile entry (false when it leaves E; never on the residue path)
+  __device__ __forceinline__ bool mad2(int64_t a, int64_t x, int64_t b, int64_t y, E& out) const {
+    if (modp) {
+      out = (E)mod_mad2((uint64_t)a, (uint64_t)x, (uint64_t)b, (uint64_t)y, modp);
+      return true;
+    }
+    return tile_mad2<E>(a, x, b, y, out);
+  }
+  // coef *= v (Eq. 2's scalar factor of a minor)
+  __device__ __forceinline__ void mul_coef(int64_t v) {
+    if (modp)
+      coef.w[0] = coef.w[0] % modp * (uint64_t)v % modp;
+    else
+      coef = u256_mul_s64(coef, v);
+  }
 
   __device__ int64_t* frame_words(int lv) { return undo + (int64_t)lv * TileCfg<TILE, E>::FRAME_WORDS; }
 
@@ -152,7 +172,7 @@ struct Eq2Tile {
       if (kind == 2) {
         R &= ~bit64(i);
         C &= ~bit64(f.pos[x]);
-        coef = u256_mul_s64(coef, pv[x]);
+        mul_coef(pv[x]);
         return true;
       }
       const int p = f.pos[x], q = f.pos[x + 1];
@@ -167,7 +187,7 @@ struct Eq2Tile {
         if ((R >> r) & 1) {
           const E old = T[r * S + p];
           E nv;
-          if (!tile_mad2<E>(a, T[r * S + q], b, old, nv)) ok = false;
+          if (!mad2(a, T[r * S + q], b, old, nv)) ok = false;
           saved[r] = old;
           T[r * S + p] = nv;
           nz = nv != 0;
@@ -185,7 +205,7 @@ struct Eq2Tile {
       if (kind == 2) {
         C &= ~bit64(j);
         R &= ~bit64(f.pos[x]);
-        coef = u256_mul_s64(coef, pv[x]);
+        mul_coef(pv[x]);
         return true;
       }
       const int p = f.pos[x], q = f.pos[x + 1];
@@ -200,7 +220,7 @@ struct Eq2Tile {
         if ((C >> cc) & 1) {
           const E old = T[p * S + cc];
           E nv;
-          if (!tile_mad2<E>(a, T[q * S + cc], b, old, nv)) ok = false;
+          if (!mad2(a, T[q * S + cc], b, old, nv)) ok = false;
           saved[cc] = old;
           T[p * S + cc] = nv;
           nz = nv != 0;

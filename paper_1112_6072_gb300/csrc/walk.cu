@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(WalkCfg<TILE>::WARPS * 32, WalkCfg<TILE>::MINB
   D.rowbits = reinterpret_cast<uint64_t*>(base + TileCfg<TILE, WE>::TILE_BYTES);
   D.colbits = D.rowbits + TILE;
   D.lane = lane;
+  D.modp = A.mod;
   // scratch line of the in-place children: mask at [-1], line at [0, TILE)
   int64_t* scratch = reinterpret_cast<int64_t*>(D.colbits + TILE) + 2;
   uint64_t* stage = reinterpret_cast<uint64_t*>(base + WalkCfg<TILE>::FIXED_BYTES);
