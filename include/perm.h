@@ -121,6 +121,15 @@ typedef struct {
                               (perm_result_words word 0, perm_result a non-negative value,
                               perm_result_bits 0).  Residues for several primes and perm_crt give
                               per(A) itself.  PERM_EINVAL if p is not an odd prime below 2^31 */
+  int32_t single_launch;   /* evaluation: 0 = one persistent launch per kernel variant (leaf
+                              variants grouped, depth-first jobs by tile width; queue order kept
+                              inside each group).  1 = the whole queue in one persistent launch:
+                              warps take queue positions in queue order through one counter and
+                              run each job's own evaluator as a device function (leaf jobs'
+                              Gray-code tasks shared with idle warps; depth-first jobs of order
+                              <= 32 on an int64 tile), so the queue order holds across all jobs;
+                              depth-first jobs of order > 32 run in a launch before it.  The
+                              results are the same either way */
 } perm_opts;
 
 /* Fill opts with the defaults above. */

@@ -72,7 +72,7 @@ class perm_opts(ctypes.Structure):
                 ("alloc_ctx", ctypes.c_void_p), ("timeout_ns", ctypes.c_int64),
                 ("model_uses_estimate", ctypes.c_int32), ("fused_levels", ctypes.c_int32),
                 ("dense_split", ctypes.c_int32), ("expand_walk", ctypes.c_int32),
-                ("modulus", ctypes.c_uint32)]
+                ("modulus", ctypes.c_uint32), ("single_launch", ctypes.c_int32)]
 
 
 class perm_job_result(ctypes.Structure):
@@ -270,7 +270,8 @@ class Plan:
 
     def _create(self, desc, keep, split_depth=-1, leaf_size=0, order="lpt", kklll_trials=0, seed=0x5EED,
                 workers_per_sm=0, chunk_log2=0, stream=None, torch_allocator=False, timeout_ns=0,
-                model_uses_estimate=True, fused_levels=True, dense_split=False, expand_walk=True, modulus=0):
+                model_uses_estimate=True, fused_levels=True, dense_split=False, expand_walk=True, modulus=0,
+                single_launch=False):
         lib = _lib()
         self._h = None
         self._keep = keep  # the host matrices the descriptors point into
@@ -293,6 +294,7 @@ class Plan:
         o.dense_split = 1 if dense_split else 0
         o.expand_walk = 1 if expand_walk else 0
         o.modulus = int(modulus)
+        o.single_launch = 1 if single_launch else 0
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator()

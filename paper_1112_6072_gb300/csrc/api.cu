@@ -255,6 +255,12 @@ struct EvalState {
   int frames = 64;
   int chunk = 10;
   bool wide_first = false;
+  // single-launch mode (perm_opts.single_launch)
+  bool single = false;
+  int single_w = 2;                 // ring words of the persistent kernel (0: residues)
+  uint32_t* keys = nullptr;         // evaluation key per queue position
+  unsigned long long* pctr = nullptr;  // [0] queue positions taken, [1] board
+  uint32_t* task_ctr = nullptr;     // 2 * nq: tasks taken, tasks finished
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr;
@@ -285,7 +291,7 @@ static void free_eval(Mem& M, perm_jobs* J) {
   if (E->cap) cudaStreamDestroy(E->cap);
   for (void* p : {(void*)E->d_q, (void*)E->d_g, (void*)E->d_rq, (void*)E->rflags, (void*)E->rpos,
                   (void*)E->counts, (void*)E->prefix, (void*)E->owner, E->stmp, (void*)E->ctr, (void*)E->sum,
-                  (void*)E->undo})
+                  (void*)E->undo, (void*)E->keys, (void*)E->pctr, (void*)E->task_ctr})
     M.put(p);
   delete E;
   J->ev = nullptr;
@@ -1382,7 +1388,11 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order, int64_t nq_
     CK(sort_asc_u32(keys, keys + n, vals, E.d_g, n, 7, sort_tmp, sort_b, s));
     CK(cudaMemcpyAsync(h.data(), hist, 8 * EVAL_KEYS, cudaMemcpyDeviceToHost, s));
   }
-  M.put(keys);
+  E.single = P->opts.single_launch != 0;
+  if (E.single)
+    E.keys = keys;  // keys[0, n) stay in queue order (the sort wrote its output after them)
+  else
+    M.put(keys);
   M.put(vals);
   M.put(sort_tmp);
   CK(cudaStreamSynchronize(s));
@@ -1407,8 +1417,9 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order, int64_t nq_
   E.d_rq = dget<uint32_t>(M, nd);
   E.rflags = dget<int32_t>(M, nd + 1);
   E.rpos = dget<int32_t>(M, nd + 1);
-  // the narrow variant (int32 tile, leaves <= 16 rows) unless the leaf order needs the wide one
-  E.wide_first = P->L > 16;
+  // the narrow variant (int32 tile, leaves <= 16 rows) unless the leaf order needs the
+  // wide one (single-launch mode: always wide, so nothing is handed on)
+  E.wide_first = P->L > 16 || E.single;
   E.chunk = P->opts.chunk_log2 > 0 ? P->opts.chunk_log2 : 10;
   uint64_t leaf_tasks = 0;
   if (order) {
@@ -1432,8 +1443,23 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order, int64_t nq_
   // Eq. 2's third child keeps the order, so a path can hold more levels than rows
   E.frames = P->opts.dense_split ? 4 * max_tile : max_tile;
   E.undo_w = dfs_undo_words(max_tile, E.frames);
-  E.undo = nd > 0 ? dget<int64_t>(M, E.undo_w * dfs_warps) : nullptr;
-  if (!E.counts || !E.prefix || !E.owner || !E.stmp || !E.d_rq || !E.rflags || !E.rpos || (nd > 0 && !E.undo))
+  int64_t undo_words = E.undo_w * dfs_warps;
+  if (E.single) {
+    // ring of the persistent kernel: the widest matrix's (residues: 0)
+    E.single_w = 2;
+    for (int i = 0; i < P->count; ++i) E.single_w = std::max(E.single_w, (int)P->w[i]);
+    if (P->mod.p) E.single_w = 0;
+    int64_t pw = 0;
+    CK(persist_warps(E.single_w, P->sms, &pw));
+    // the persistent kernel's depth-first part: 32-wide tiles
+    undo_words = std::max(undo_words, dfs_undo_words(32, E.frames) * pw);
+    E.pctr = dget<unsigned long long>(M, 2);
+    E.task_ctr = dget<uint32_t>(M, 2 * std::max<int64_t>(n, 1));
+    if (!E.pctr || !E.task_ctr) return PERM_ENOMEM;
+  }
+  E.undo = (nd > 0 || E.single) ? dget<int64_t>(M, undo_words) : nullptr;
+  if (!E.counts || !E.prefix || !E.owner || !E.stmp || !E.d_rq || !E.rflags || !E.rpos ||
+      ((nd > 0 || E.single) && !E.undo))
     return PERM_ENOMEM;
   return PERM_OK;
 }
@@ -1482,6 +1508,39 @@ static cudaError_t eval_enqueue(perm_jobs* J, cudaStream_t s) {
   EQ(cudaMemsetAsync(P->d_mat_acc, 0, 32ull * P->count, s));
   EQ(cudaMemsetAsync(E.ctr, 0, 8 * (1 + EVAL_DFS_GROUPS), s));
   EQ(cudaMemsetAsync(E.sum + SUM_STATUS, 0xff, 8, s));
+  if (E.single) {
+    // depth-first jobs of order > 32 first (tile 64), then everything else in one launch
+    for (int g = 0; g < EVAL_DFS_GROUPS; ++g) {
+      const int64_t nq = E.db[g + 1] - E.db[g];
+      if (nq == 0 || dfs_group_tile(g) != 64) continue;
+      EQ(launch_dfs(dfs_args(J, g, E.d_dq + E.db[g], nq), 64, true, dfs_group_w(g), P->sms, dfs_wps(P, 64), s));
+      ++launches;
+    }
+    EQ(cudaMemsetAsync(E.pctr, 0, 8, s));
+    EQ(cudaMemsetAsync(E.pctr + 1, 0xff, 8, s));
+    EQ(cudaMemsetAsync(E.task_ctr, 0, 8 * (size_t)std::max<int64_t>(E.nq, 1), s));
+    PersistArgs A{};
+    A.queue = E.d_q;
+    A.keys = E.keys;
+    A.nq = E.nq;
+    A.chunk_log2 = E.chunk;
+    A.qctr = E.pctr;
+    A.board = reinterpret_cast<long long*>(E.pctr + 1);
+    A.task_next = E.task_ctr;
+    A.task_done = E.task_ctr + std::max<int64_t>(E.nq, 1);
+    A.dfs = dfs_args(J, 2, nullptr, 0);
+    A.dfs.undo_words_per_warp = dfs_undo_words(32, E.frames);
+    if (E.nq > 0) {
+      EQ(launch_persist(A, E.single_w, P->sms, s));
+      ++launches;
+    }
+    if (J->n > 0) {
+      EQ(launch_status_summary(J->out.status, J->n, E.sum + SUM_STATUS, s));
+      ++launches;
+    }
+    P->last_launches = launches;
+    return cudaSuccess;
+  }
   // depth-first groups: tile 64 (the largest jobs) first; each its own job counter
   for (int g = 0; g < EVAL_DFS_GROUPS; ++g) {
     const int64_t nq = E.db[g + 1] - E.db[g];

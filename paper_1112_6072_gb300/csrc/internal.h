@@ -256,6 +256,30 @@ int dfs_warps_per_block(int tile, bool wide);
 // undo words per warp for a stack of `frames` levels
 int64_t dfs_undo_words(int tile, int frames);
 
+// ---- single-launch evaluation (persist.cu) ------------------------------------
+// The whole queue in one persistent launch: leaf jobs by their variant's
+// Ryser walk (tasks shared through a board), other jobs of order <= 32 by
+// the depth-first walk on a 32-wide int64 tile; jobs of order > 32 that are
+// not leaves are skipped (the caller runs them first).  keys: the
+// evaluation key of every queue position (launch_eval_keys).  qctr (zero),
+// board (-1), task_next and task_done (nq entries, zero) are reset by the
+// caller before every launch.  dfs: the depth-first arguments (queue, nq
+// and job_counter unused; undo sized for persist_warps warps).
+struct PersistArgs {
+  const uint32_t* queue;
+  const uint32_t* keys;
+  int64_t nq;
+  int32_t chunk_log2;
+  unsigned long long* qctr;
+  long long* board;
+  uint32_t* task_next;
+  uint32_t* task_done;
+  DfsArgs dfs;
+};
+// W: 2 or 4 (ring words; 4 also serves matrices of width 2), 0 = the residue path
+cudaError_t launch_persist(const PersistArgs& a, int W, int sms, cudaStream_t s);
+cudaError_t persist_warps(int W, int sms, int64_t* warps);
+
 // ---- K4 KKLLL estimator -------------------------------------------------------
 // scratch: kklll_scratch_bytes(njobs, max_order, trials) bytes of device memory
 cudaError_t launch_kklll(const JobArrays& jobs, int64_t njobs, const uint64_t* arena, int trials, uint64_t seed,
