@@ -349,6 +349,50 @@ def run_c60(pk, torch, args, leaf=C60_LEAF):
     return out
 
 
+def run_c60_path(pk, torch, iters, leaf):
+    """C60's whole path in natural order, `iters` times: plan, expansion,
+    evaluation (wall and device times of each, best and median)."""
+    a = W.c60(seed=C60_SEED)
+    rows = []
+    for _ in range(iters):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with pk.Plan([a], leaf_size=leaf, order="natural") as p:
+            t1 = time.perf_counter()
+            nj = p.expand()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            p.evaluate()
+            v = p.result(0)
+            t3 = time.perf_counter()
+            rows.append(dict(create_ms=(t1 - t0) * 1e3, expand_wall_ms=(t2 - t1) * 1e3, expand_device_ms=p.last_expand_ms,
+                             eval_wall_ms=(t3 - t2) * 1e3, eval_device_ms=p.last_eval_ms, jobs=nj, per=str(v),
+                             driver=p.expand_driver))
+        torch.cuda.synchronize()
+        rows[-1]["total_ms"] = (time.perf_counter() - t0) * 1e3
+    keys = [k for k in rows[0] if k.endswith("_ms")]
+    return {"leaf_size": leaf, "best": min(rows, key=lambda r: r["total_ms"]),
+            "median": {k: float(np.median([r[k] for r in rows])) for k in keys}}
+
+
+def run_shifted(pk, torch, k, leaf):
+    """per(I - A) of C60 (the paper's Section 4.2 matrix at x = 1) modulo
+    2^31 - 1: the automatic split (jobs of order 32) evaluated depth first,
+    all jobs or k evenly spaced ones (evaluate_subset)."""
+    a = W.c60(seed=C60_SEED)
+    b = np.eye(60, dtype=np.int64) - a
+    p_ = 2147483647
+    with pk.Plan([b], leaf_size=leaf, modulus=p_, order="natural") as p:
+        nj = p.expand()
+        if k:
+            sub = (np.arange(k, dtype=np.int64) * (nj // k)).astype(np.uint32)
+            p.evaluate_subset(sub)
+        else:
+            p.evaluate()
+        return {"jobs": nj, "evaluated": int(k or nj), "eval_ms": p.last_eval_ms, "leaf_size": leaf,
+                "residue": str(p.result(0)), "modulus": p_}
+
+
 def run_ordering(pk, torch, args, n=80, depth=40, leaf=14):
     """Natural vs KKLLL-LPT vs learned order on a coarse split (few jobs per
     worker, where the order matters): device evaluation time of the whole
@@ -367,10 +411,12 @@ def run_ordering(pk, torch, args, n=80, depth=40, leaf=14):
     a = W.regular3(n, 1)
     out = {"workload": f"random 3-regular n={n} (seed 1), split depth {depth}, leaf order {leaf}",
            "train": f"job times of n={n} seed 7, final loss {loss:.4f} (without the estimate {loss_c:.4f})"}
-    variants = (("natural", "natural", None, True), ("lpt", "lpt", None, True), ("learned", "learned", params, True),
-                ("learned_no_estimate", "learned", params_c, False))
-    for name, order, prm, use_ap in variants:
-        with pk.Plan([a], split_depth=depth, leaf_size=leaf, order=order, model_uses_estimate=use_ap) as p:
+    variants = (("natural", "natural", None, True, False), ("lpt", "lpt", None, True, False),
+                ("learned", "learned", params, True, False), ("learned_no_estimate", "learned", params_c, False, False),
+                ("lpt_single_launch", "lpt", None, True, True))
+    for name, order, prm, use_ap, single in variants:
+        with pk.Plan([a], split_depth=depth, leaf_size=leaf, order=order, model_uses_estimate=use_ap,
+                     single_launch=single) as p:
             nj = p.expand()
             if prm is not None:
                 p.attach_model(prm)
@@ -385,7 +431,7 @@ def run_ordering(pk, torch, args, n=80, depth=40, leaf=14):
                 p.replay()
                 evs.append(p.last_eval_ms)
             out[name] = {"eval_ms": min(evs), "order_ms": order_ms, "order_plus_eval_ms": order_ms + min(evs),
-                         "jobs": nj, "per": str(p.result(0))}
+                         "jobs": nj, "per": str(p.result(0)), "launches": p.last_launches}
     return out
 
 
@@ -681,10 +727,29 @@ def main():
     ap.add_argument("--mixed", action="store_true",
                     help="the mixed batch of 256 matrices (3-regular and sparse rows), three orders")
     ap.add_argument("--leaf-size", type=int, default=12)
+    ap.add_argument("--c60-path", type=int, default=0, metavar="K",
+                    help="run only C60's whole path (natural order) K times and print its time split "
+                         "(the command the C60 profiles are taken with)")
+    ap.add_argument("--shifted", type=int, default=0, metavar="K",
+                    help="per(I - A) of C60 on the residue path (p = 2^31 - 1): K evenly spaced jobs of the "
+                         "split at order 32 (all jobs when K = 0 and --shifted-all), depth-first evaluation")
+    ap.add_argument("--shifted-all", action="store_true")
     ap.add_argument("--regular", type=int, default=0,
                     help="per(A) of one random 3-regular graph of this order (seed 1), natural order")
     args = ap.parse_args()
     globals()["LEAF_COUNT"] = args.leaf_count
+    if args.c60_path:
+        import torch
+        import paper_1112_6072_gb300 as pk
+        torch.cuda.set_device(0)
+        print(json.dumps({"c60_path": run_c60_path(pk, torch, args.c60_path, args.leaf_size)}))
+        return
+    if args.shifted or args.shifted_all:
+        import torch
+        import paper_1112_6072_gb300 as pk
+        torch.cuda.set_device(0)
+        print(json.dumps({"c60_shifted": run_shifted(pk, torch, args.shifted, args.leaf_size)}))
+        return
     if args.c60_only:
         import torch
         import paper_1112_6072_gb300 as pk

@@ -224,7 +224,8 @@ struct JobBuf {
 #define SUM_STATUS 0
 #define SUM_RETRY 1
 #define SUM_HIST (SUM_RETRY + EVAL_DFS_GROUPS + 1)
-#define SUM_WORDS (SUM_HIST + EVAL_KEYS)
+#define SUM_RFLAG (SUM_HIST + EVAL_KEYS)  // single-launch mode: a depth-first job handed on
+#define SUM_WORDS (SUM_RFLAG + 1)
 
 // depth-first group g of the grouped queue: tile 64 first, ring width 2 then 4
 static inline int dfs_group_tile(int g) { return g >= 2 ? 32 : 64; }
@@ -1417,9 +1418,8 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order, int64_t nq_
   E.d_rq = dget<uint32_t>(M, nd);
   E.rflags = dget<int32_t>(M, nd + 1);
   E.rpos = dget<int32_t>(M, nd + 1);
-  // the narrow variant (int32 tile, leaves <= 16 rows) unless the leaf order needs the
-  // wide one (single-launch mode: always wide, so nothing is handed on)
-  E.wide_first = P->L > 16 || E.single;
+  // the narrow variant (int32 tile, leaves <= 16 rows) unless the leaf order needs the wide one
+  E.wide_first = P->L > 16;
   E.chunk = P->opts.chunk_log2 > 0 ? P->opts.chunk_log2 : 10;
   uint64_t leaf_tasks = 0;
   if (order) {
@@ -1509,11 +1509,16 @@ static cudaError_t eval_enqueue(perm_jobs* J, cudaStream_t s) {
   EQ(cudaMemsetAsync(E.ctr, 0, 8 * (1 + EVAL_DFS_GROUPS), s));
   EQ(cudaMemsetAsync(E.sum + SUM_STATUS, 0xff, 8, s));
   if (E.single) {
-    // depth-first jobs of order > 32 first (tile 64), then everything else in one launch
+    // depth-first jobs of order > 32 first (tile 64), then everything else in one
+    // launch; a job the narrow tile hands on only raises a flag here (the
+    // wide rerun happens after, when the flag is set)
+    EQ(cudaMemsetAsync(E.sum + SUM_RFLAG, 0, 8, s));
     for (int g = 0; g < EVAL_DFS_GROUPS; ++g) {
       const int64_t nq = E.db[g + 1] - E.db[g];
       if (nq == 0 || dfs_group_tile(g) != 64) continue;
-      EQ(launch_dfs(dfs_args(J, g, E.d_dq + E.db[g], nq), 64, true, dfs_group_w(g), P->sms, dfs_wps(P, 64), s));
+      DfsArgs d = dfs_args(J, g, E.d_dq + E.db[g], nq);
+      d.retry_flag = E.sum + SUM_RFLAG;
+      EQ(launch_dfs(d, 64, E.wide_first, dfs_group_w(g), P->sms, dfs_wps(P, 64), s));
       ++launches;
     }
     EQ(cudaMemsetAsync(E.pctr, 0, 8, s));
@@ -1595,6 +1600,23 @@ static perm_status eval_finish(perm_jobs* J, perm_job_result* results) {
   for (int k = 0; k < SUM_HIST; ++k) sum[k] = k == SUM_STATUS ? ~0ull : 0ull;
   if (n) CK(cudaMemcpyAsync(sum, E.sum, sizeof(sum), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (E.single) {
+    // single-launch mode collects the jobs handed on only when one was
+    for (int k = 0; k <= EVAL_DFS_GROUPS; ++k) sum[SUM_RETRY + k] = 0;
+    unsigned long long flag = 0;
+    if (n && E.nd > 0 && !E.wide_first) {
+      CK(cudaMemcpyAsync(&flag, E.sum + SUM_RFLAG, 8, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    if (flag) {
+      RetryBounds rb;
+      for (int g = 0; g <= EVAL_DFS_GROUPS; ++g) rb.b[g] = E.db[g];
+      CK(launch_retry_collect(E.d_dq, E.nd, rb, J->out.status, E.rflags, E.rpos, E.stmp, E.stb, E.d_rq,
+                              E.sum + SUM_RETRY, s));
+      CK(cudaMemcpyAsync(sum + SUM_RETRY, E.sum + SUM_RETRY, 8 * (EVAL_DFS_GROUPS + 1), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+  }
   const unsigned long long* at = sum + SUM_RETRY;
   if (n && E.nd > 0 && !E.wide_first && at[EVAL_DFS_GROUPS] > 0) {
     // jobs the narrow variant handed on run again on the wide one, by group

@@ -424,6 +424,7 @@ __device__ __forceinline__ void dfs_job(Dfs<TILE, E, LN, W>& D, const DfsArgs& A
     A.out.nodes[job] = nodes;
     for (int t = 0; t < 4; ++t) A.out.acc[4ll * job + t] = acc.w[t];
     if (status == 0) atomic_add_words(A.mat_acc + 4ll * A.jobs.mat[job], acc.w, 4);
+    if (status == DFS_RETRY && A.retry_flag) atomicOr(A.retry_flag, 1ull);
   }
   __syncwarp();
 }

@@ -245,6 +245,7 @@ struct DfsArgs {
   int64_t timeout_ns;
   int32_t three;          // s >= 5 nodes split by Eq. 2's three children (else leaves)
   int32_t max_depth;      // undo frames per warp
+  unsigned long long* retry_flag;  // nullable: set to 1 when a job reports DFS_RETRY
   ModP mod;               // p = 0: the ring path; else every value modulo p (W is ignored)
 };
 // Internal job status of the narrow depth-first variant (int32 tile, leaves

@@ -78,18 +78,42 @@ __device__ __forceinline__ void leaf_unit_key(int key, const uint64_t* arena, in
   }
 }
 
-// coef * per of a finished leaf job into out.acc and its matrix (lane 0)
-__device__ __forceinline__ void leaf_close(const PersistArgs& A, uint32_t job, int m, const uint64_t* sigma) {
+// A warp's running sum of the leaf jobs it closed for one matrix (lane 0):
+// added into the matrix accumulator when the matrix changes and at the end,
+// so jobs of one matrix taken one after another cost one atomic sum.
+struct MatSum {
+  int mat = -1;
+  u256 v;
+  __device__ void flush(unsigned long long* mat_acc) {
+    if (mat >= 0) atomic_add_words(mat_acc + 4ll * mat, v.w, 4);
+    mat = -1;
+  }
+  __device__ void add(unsigned long long* mat_acc, int m2, const u256& x) {
+    if (m2 != mat) {
+      flush(mat_acc);
+      mat = m2;
+      v = x;
+    } else {
+      v = u256_add(v, x);
+    }
+  }
+};
+
+// coef * per of a finished leaf job into out.acc and the warp's matrix sum (lane 0)
+__device__ __forceinline__ void leaf_close(const PersistArgs& A, uint32_t job, int m, const uint64_t* sigma,
+                                           MatSum& ms) {
   const u256 v = leaf_finish(sigma, m, A.dfs.jobs.coef + 4ll * job, A.dfs.mod.p);
   for (int k = 0; k < 4; ++k) A.dfs.out.acc[4ll * job + k] = v.w[k];
   A.dfs.out.nodes[job] = 1;
-  atomic_add_words(A.dfs.mat_acc + 4ll * A.dfs.jobs.mat[job], v.w, 4);
+  ms.add(A.dfs.mat_acc, A.dfs.jobs.mat[job], v);
 }
 
-// Take tasks of the leaf job at queue position q until none is left.
+// Take tasks of the leaf job at queue position q until none is left
+// (sole: a one-task job this warp took from the queue, which no other warp
+// can reach, so its task needs no counter).
 template <int W>
 __device__ __forceinline__ void leaf_tasks(const PersistArgs& A, int64_t q, int lane, int32_t* delta, int32_t* rho0,
-                                           int32_t* colcnt) {
+                                           int32_t* colcnt, MatSum& ms, bool sole) {
   const uint32_t job = A.queue[q];
   const int key = (int)A.keys[q];
   const JobArrays& J = A.dfs.jobs;
@@ -100,17 +124,21 @@ __device__ __forceinline__ void leaf_tasks(const PersistArgs& A, int64_t q, int 
   const JobOut& out = A.dfs.out;
   if ((key >> 3) == P_BAD) {  // a row sum beyond the exact leaf's range
     unsigned t = 0;
-    if (lane == 0) t = atomicAdd(A.task_next + q, 1u);
+    if (lane == 0 && !sole) t = atomicAdd(A.task_next + q, 1u);
     t = __shfl_sync(0xffffffffu, t, 0);
     if (lane == 0 && t == 0) out.status[job] = PERM_EOVERFLOW;
     return;
   }
   bool loaded = false;
-  for (;;) {
+  for (int it = 0;; ++it) {
     unsigned t = 0;
-    if (lane == 0) t = atomicAdd(A.task_next + q, 1u);
-    t = __shfl_sync(0xffffffffu, t, 0);
-    if ((uint64_t)t >= T) break;
+    if (sole) {
+      if (it > 0) break;
+    } else {
+      if (lane == 0) t = atomicAdd(A.task_next + q, 1u);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if ((uint64_t)t >= T) break;
+    }
     const uint64_t t0 = globaltimer_ns();
     uint64_t words[4];
     leaf_unit_key<W>(key, A.dfs.arena, off, m, nnz, !loaded, t, A.chunk_log2, delta, rho0, colcnt, lane, A.dfs.mod,
@@ -123,7 +151,7 @@ __device__ __forceinline__ void leaf_tasks(const PersistArgs& A, int64_t q, int 
         out.t_start[job] = t0;
         out.t_end[job] = t1;
         out.sm[job] = (int32_t)smid();
-        leaf_close(A, job, m, words);
+        leaf_close(A, job, m, words, ms);
       } else {
         atomic_add_words(out.acc + 4ll * job, words, 4);
         const unsigned long long prev = atomicMin(out.t_start + job, (unsigned long long)t0);
@@ -134,7 +162,7 @@ __device__ __forceinline__ void leaf_tasks(const PersistArgs& A, int64_t q, int 
           __threadfence();
           uint64_t sig[4];
           for (int k = 0; k < 4; ++k) sig[k] = __ldcg(reinterpret_cast<const uint64_t*>(out.acc) + 4ll * job + k);
-          leaf_close(A, job, m, sig);
+          leaf_close(A, job, m, sig, ms);
         }
       }
     }
@@ -162,13 +190,14 @@ __global__ void __launch_bounds__(kPersistWarps * 32, 2) k_eval_persist(PersistA
   D.modp = A.dfs.mod.p;
   const int cut = A.dfs.leaf_size > 2 ? A.dfs.leaf_size : 2;
   int32_t* colcnt = reinterpret_cast<int32_t*>(D.cmask);
+  MatSum ms;
   for (;;) {
     // a posted leaf job with tasks left comes first
     long long b = -1;
     if (lane == 0) b = *(volatile long long*)A.board;
     b = __shfl_sync(0xffffffffu, b, 0);
     if (b >= 0) {
-      leaf_tasks<W>(A, b, lane, D.delta, D.rho0, colcnt);
+      leaf_tasks<W>(A, b, lane, D.delta, D.rho0, colcnt, ms, false);
       if (lane == 0) atomicCAS(reinterpret_cast<unsigned long long*>(A.board), (unsigned long long)b, ~0ull);
       __syncwarp();
       continue;
@@ -180,16 +209,16 @@ __global__ void __launch_bounds__(kPersistWarps * 32, 2) k_eval_persist(PersistA
     const int64_t q = (int64_t)qi;
     const uint32_t key = A.keys[q];
     if (key < EVAL_KEY_DFS) {
-      const int m = A.dfs.jobs.m[A.queue[q]];
-      if (lane == 0 && leaf_tasks_dev(m, A.chunk_log2) > 1)
-        atomicExch(reinterpret_cast<unsigned long long*>(A.board), (unsigned long long)q);
+      const bool many = leaf_tasks_dev(A.dfs.jobs.m[A.queue[q]], A.chunk_log2) > 1;
+      if (lane == 0 && many) atomicExch(reinterpret_cast<unsigned long long*>(A.board), (unsigned long long)q);
       __syncwarp();
-      leaf_tasks<W>(A, q, lane, D.delta, D.rho0, colcnt);
+      leaf_tasks<W>(A, q, lane, D.delta, D.rho0, colcnt, ms, !many);
     } else if (A.dfs.jobs.m[A.queue[q]] <= 32) {
       dfs_job<32, int64_t, 32, W>(D, A.dfs, A.queue[q], cut);
     }
     // else: a depth-first job of order above 32, evaluated by the launch before this one
   }
+  if (lane == 0) ms.flush(A.dfs.mat_acc);
 }
 
 template <int W>
