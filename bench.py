@@ -301,22 +301,17 @@ def train_cost_model_configs(pk):
     return learned.train(np.concatenate(Xs), np.concatenate(ts), steps=600)
 
 
-def run_c60(pk, torch, args, leaf=C60_LEAF):
-    """C60 (coordinates, vertex shuffle seed 60) through the whole path at
-    leaf order 11 (103,940 jobs): natural order, the paper's KKLLL-LPT order
-    and the learned order (the cost model without the estimate, trained on
-    configurations 1-3).  Per order: wall time of the whole call sequence,
-    device time of the expansion and of the evaluation, ordering time, and
-    their sum; the expansion's achieved bandwidth on its algorithmic bytes."""
-    a = W.c60(seed=C60_SEED)
-    params, loss = train_cost_model_configs(pk)
-    out = {"leaf_size": leaf, "model_loss": loss}
-    for order in ("natural", "lpt", "learned"):
+def _c60_orders(pk, torch, a, params, knobs, orders=("natural", "lpt", "learned"), reps=5):
+    """Whole path of C60 per order: wall time of the call sequence, device
+    time of the expansion and of the evaluation, ordering time and their
+    sum (best of reps); the natural run's job orders and nonzeros."""
+    out, ords, nnzs = {}, None, None
+    for order in orders:
         best = None
-        for it in range(5):
+        for it in range(reps):
             torch.cuda.synchronize()
             t = time.perf_counter()
-            with pk.Plan([a], leaf_size=leaf, order=order, model_uses_estimate=False) as p:
+            with pk.Plan([a], order=order, model_uses_estimate=False, **knobs) as p:
                 nj = p.expand()
                 if order == "learned":
                     p.attach_model(params)
@@ -329,7 +324,7 @@ def run_c60(pk, torch, args, leaf=C60_LEAF):
                 val = p.result(0)
                 r = {"wall_ms": 0.0, "expand_device_ms": p.last_expand_ms, "order_ms": order_ms,
                      "eval_ms": p.last_eval_ms, "jobs": nj, "per": str(val), "driver": p.expand_driver}
-                if it == 0:
+                if it == 0 and order == "natural":
                     nnzs, ords = rec["nnz"], rec["order"]
             torch.cuda.synchronize()
             r["wall_ms"] = (time.perf_counter() - t) * 1e3
@@ -337,7 +332,26 @@ def run_c60(pk, torch, args, leaf=C60_LEAF):
             if best is None or r["wall_ms"] < best["wall_ms"]:
                 best = r
         out[order] = best
-    nat = out["natural"]
+    return out, ords, nnzs
+
+
+def run_c60(pk, torch, args):
+    """C60 (coordinates, vertex shuffle seed 60) through the whole path at
+    leaf order 11 with the automatic split (103,940 jobs, within the
+    configuration's 10^5 - 10^6): natural order, the paper's KKLLL-LPT order
+    and the learned order (the cost model without the estimate, trained on
+    configurations 1-3).  Per order: wall time of the whole call sequence,
+    device time of the expansion and of the evaluation, ordering time, and
+    their sum; the expansion's achieved bandwidth on its algorithmic bytes.
+    Also, for reference, the fastest split of the autotuner's grid
+    (autotune.tune_hybrid), which may leave far fewer, larger jobs."""
+    from paper_1112_6072_gb300 import autotune
+    a = W.c60(seed=C60_SEED)
+    params, loss = train_cost_model_configs(pk)
+    out = {"leaf_size": C60_LEAF, "split_depth": "automatic", "model_loss": loss}
+    res, ords, nnzs = _c60_orders(pk, torch, a, params, {"leaf_size": C60_LEAF})
+    out.update(res)
+    nat = res["natural"]
     abytes = expand_algorithmic_bytes(ords, nnzs)
     pk_ = peaks()
     out["roofline_expand"] = {"bound": "hbm", "achieved": abytes / (nat["expand_device_ms"] * 1e-3) / 1e9,
@@ -346,6 +360,12 @@ def run_c60(pk, torch, args, leaf=C60_LEAF):
                               "algorithmic_bytes": abytes,
                               "basis": "per emitted job: parent block read + own block written + 56-byte header; "
                                        "device time of perm_expand (events), natural-order run"}
+    tuned = autotune.tune_hybrid(a)
+    knobs = {k: tuned[k] for k in ("leaf_size", "split_depth", "workers_per_sm")}
+    t_res, _, _ = _c60_orders(pk, torch, a, params, knobs, orders=("natural",))
+    out["tuned_split"] = dict(t_res["natural"], **knobs,
+                              note="fastest (leaf order, split depth, warps) of the autotuner's grid; "
+                                   "its job count is outside the configuration's 10^5 - 10^6")
     return out
 
 

@@ -54,9 +54,12 @@ def _time_path(mats, reps=2, **opts) -> float:
     return best
 
 
-def tune_hybrid(a, leaf_sizes=(8, 10, 12, 14), depth_offsets=(-6, -3, 0), workers=(8, 16),
+def tune_hybrid(a, leaf_sizes=(10, 11, 12, 13, 14), depth_offsets=(-16, -12, -8, -4, 0), workers=(8, 16),
                 order="natural", cache_file: str | None = None) -> dict:
-    """Best (leaf_size, split_depth, workers_per_sm) for a sparse matrix."""
+    """Best (leaf_size, split_depth, workers_per_sm) for a sparse matrix: the
+    whole path timed at split depths from the automatic one (jobs at the
+    leaf order, evaluated by the leaf kernel) up to 16 levels above it (fewer,
+    larger jobs, evaluated depth first)."""
     key = "hybrid_" + _key(a)
     if cache_file and os.path.exists(cache_file):
         _CACHE.update(json.load(open(cache_file)))

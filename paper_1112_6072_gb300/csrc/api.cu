@@ -275,7 +275,8 @@ struct perm_jobs {
   uint64_t* arena = nullptr;
   int64_t arena_words = 0;
   int max_order = 0;
-  std::vector<int32_t> h_m, h_mat;
+  std::vector<int32_t> h_m;
+  std::vector<int64_t> order_count;  // jobs per order (PERM_MAX_N + 1 entries)
   uint32_t* d_queue = nullptr;
   bool has_order = false;
   float* d_logap = nullptr;
@@ -1159,7 +1160,7 @@ static perm_status perm_expand_impl(perm_plan_t* P, perm_jobs_t** jobs_out, int6
   return finish_jobset(P, J, jobs_out, njobs);
 }
 
-// The job set's host copies of orders and matrices, and its output arrays.
+// The job set's host copy of the job orders, and its output arrays.
 static perm_status finish_jobset(perm_plan* P, perm_jobs* J, perm_jobs_t** jobs_out, int64_t* njobs) {
   Mem& M = P->M;
   cudaStream_t s = P->s;
@@ -1167,15 +1168,15 @@ static perm_status finish_jobset(perm_plan* P, perm_jobs* J, perm_jobs_t** jobs_
   const JobArrays cur = J->a;
   CK(cudaEventRecord(P->xe1, s));
   J->h_m.resize(ncur);
-  J->h_mat.resize(ncur);
-  if (ncur > 0) {
-    CK(cudaMemcpyAsync(J->h_m.data(), cur.m, 4 * ncur, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(J->h_mat.data(), cur.mat, 4 * ncur, cudaMemcpyDeviceToHost, s));
-  }
+  if (ncur > 0) CK(cudaMemcpyAsync(J->h_m.data(), cur.m, 4 * ncur, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaEventElapsedTime(&P->last_expand_ms, P->xe0, P->xe1));
   J->max_order = 0;
-  for (int32_t v : J->h_m) J->max_order = std::max(J->max_order, (int)v);
+  J->order_count.assign(PERM_MAX_N + 1, 0);
+  for (int32_t v : J->h_m) {
+    J->max_order = std::max(J->max_order, (int)v);
+    J->order_count[std::min(std::max(v, 0), PERM_MAX_N)] += 1;
+  }
   // outputs
   const int64_t nj = std::max<int64_t>(ncur, 1);
   J->out.acc = dget<unsigned long long>(M, 4 * nj);
@@ -1288,10 +1289,7 @@ static perm_status perm_order_impl(perm_jobs_t* J, int32_t kind, uint32_t* order
     return PERM_OK;
   }
   if (kind == PERM_ORDER_NATURAL) {
-    std::vector<uint32_t> iota(n);
-    std::iota(iota.begin(), iota.end(), 0u);
-    CK(cudaMemcpyAsync(J->d_queue, iota.data(), 4 * n, cudaMemcpyHostToDevice, P->s));
-    CK(cudaStreamSynchronize(P->s));
+    CK(launch_iota_u32(J->d_queue, n, P->s));
   } else if (kind == PERM_ORDER_LPT || (kind == PERM_ORDER_LEARNED && P->mlp.empty())) {
     if (!J->has_logap) {
       perm_status st = perm_estimate(J, nullptr);
@@ -1422,12 +1420,12 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order, int64_t nq_
   E.wide_first = P->L > 16;
   E.chunk = P->opts.chunk_log2 > 0 ? P->opts.chunk_log2 : 10;
   uint64_t leaf_tasks = 0;
-  if (order) {
+  if (order && n < nj) {  // a sub-queue: its own jobs
     for (int64_t k = 0; k < n; ++k)
       if (J->h_m[order[k]] <= leaf_max) leaf_tasks += leaf_tasks_host(J->h_m[order[k]], E.chunk);
-  } else {
-    for (int64_t j = 0; j < n; ++j)
-      if (J->h_m[j] <= leaf_max) leaf_tasks += leaf_tasks_host(J->h_m[j], E.chunk);
+  } else {  // every job (any order): from the count of jobs per order
+    for (int m = 0; m <= std::min(leaf_max, PERM_MAX_N); ++m)
+      if (J->order_count[m]) leaf_tasks += (uint64_t)J->order_count[m] * leaf_tasks_host(m, E.chunk);
   }
   E.owner = dget<uint32_t>(M, (int64_t)std::max<uint64_t>(leaf_tasks, 1));
   int dfs_warps = 0, max_tile = 32;

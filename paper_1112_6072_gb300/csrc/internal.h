@@ -40,6 +40,8 @@ size_t sort_tmp_bytes_u64(int64_t n);
 cudaError_t sort_asc_u32(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
                          int64_t n, int end_bit, void* tmp, size_t tmp_bytes, cudaStream_t s);
 size_t sort_tmp_bytes_u32(int64_t n, int end_bit);
+// out[i] = i for i < n (the natural order of a job list)
+cudaError_t launch_iota_u32(uint32_t* out, int64_t n, cudaStream_t s);
 // *out = min over jobs j < n with status s not in {0, DFS_RETRY} of j * 256 + s
 // (unchanged when there is none; set it to ~0 first).
 cudaError_t launch_status_summary(const int32_t* status, int64_t n, unsigned long long* out, cudaStream_t s);

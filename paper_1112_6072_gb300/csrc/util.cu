@@ -86,6 +86,17 @@ __global__ void k_status_summary(const int32_t* __restrict__ status, int64_t n, 
   if ((threadIdx.x & 31) == 0 && key != ~0ull) atomicMin(out, key);
 }
 
+__global__ void k_iota_u32(uint32_t* __restrict__ out, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (uint32_t)i;
+}
+
+cudaError_t launch_iota_u32(uint32_t* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_iota_u32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_status_summary(const int32_t* status, int64_t n, unsigned long long* out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_status_summary<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(status, n, out);
