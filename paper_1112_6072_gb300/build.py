@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libperm.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["api.cu", "leaf.cu", "expand.cu", "dfs.cu", "kklll.cu", "mlp.cu", "util.cu", "noalloc.cu", "walk.cu", "crt.cu", "persist.cu"]
+SOURCES = ["api.cu", "leaf.cu", "expand.cu", "dfs.cu", "kklll.cu", "mlp.cu", "util.cu", "noalloc.cu", "walk.cu", "crt.cu", "persist.cu", "persist_narrow.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

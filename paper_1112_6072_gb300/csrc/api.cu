@@ -1448,7 +1448,7 @@ static perm_status eval_prepare(perm_jobs* J, const uint32_t* order, int64_t nq_
     for (int i = 0; i < P->count; ++i) E.single_w = std::max(E.single_w, (int)P->w[i]);
     if (P->mod.p) E.single_w = 0;
     int64_t pw = 0;
-    CK(persist_warps(E.single_w, P->sms, &pw));
+    CK(persist_warps(E.single_w, !E.wide_first, P->sms, &pw));
     // the persistent kernel's depth-first part: 32-wide tiles
     undo_words = std::max(undo_words, dfs_undo_words(32, E.frames) * pw);
     E.pctr = dget<unsigned long long>(M, 2);
@@ -1533,8 +1533,9 @@ static cudaError_t eval_enqueue(perm_jobs* J, cudaStream_t s) {
     A.task_done = E.task_ctr + std::max<int64_t>(E.nq, 1);
     A.dfs = dfs_args(J, 2, nullptr, 0);
     A.dfs.undo_words_per_warp = dfs_undo_words(32, E.frames);
+    A.dfs.retry_flag = E.sum + SUM_RFLAG;
     if (E.nq > 0) {
-      EQ(launch_persist(A, E.single_w, P->sms, s));
+      EQ(launch_persist(A, E.single_w, !E.wide_first, P->sms, s));
       ++launches;
     }
     if (J->n > 0) {

@@ -279,9 +279,13 @@ struct PersistArgs {
   uint32_t* task_done;
   DfsArgs dfs;
 };
-// W: 2 or 4 (ring words; 4 also serves matrices of width 2), 0 = the residue path
-cudaError_t launch_persist(const PersistArgs& a, int W, int sms, cudaStream_t s);
-cudaError_t persist_warps(int W, int sms, int64_t* warps);
+// W: 2 or 4 (ring words; 4 also serves matrices of width 2), 0 = the residue
+// path.  narrow: int32 tiles and depth-first leaves up to 16 rows (a job that
+// needs more reports DFS_RETRY and sets dfs.retry_flag), else int64 and 32.
+cudaError_t launch_persist(const PersistArgs& a, int W, bool narrow, int sms, cudaStream_t s);
+cudaError_t persist_warps(int W, bool narrow, int sms, int64_t* warps);
+cudaError_t launch_persist_narrow(const PersistArgs& a, int W, int sms, cudaStream_t s);
+cudaError_t persist_warps_narrow(int W, int sms, int64_t* warps);
 
 // ---- K4 KKLLL estimator -------------------------------------------------------
 // scratch: kklll_scratch_bytes(njobs, max_order, trials) bytes of device memory

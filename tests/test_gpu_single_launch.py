@@ -41,6 +41,9 @@ CASES = {
     "dfs_only": ([W.regular3(36, 2), W.regular3(34, 3)], dict(split_depth=2, leaf_size=12)),
     # the three-child split in the depth-first walk
     "dense_split": ([W.sparse_rows(26, 3, kmin=4, kmax=6)], dict(split_depth=3, leaf_size=8, dense_split=True)),
+    # dense jobs of order 20 above the leaf order: the narrow tile hands them to the wide kernel
+    "retry_wide": ([(np.random.default_rng(8).random((20, 20)) < 0.5).astype(np.int64),
+                    W.regular3(30, 4)], dict(split_depth=1, leaf_size=12)),
 }
 
 
@@ -64,8 +67,9 @@ def test_single_launch_matches_grouped_and_oracle(case, order):
     assert one["res"] == oracle_values(case)
     rec = one["rec"]
     assert (rec["status"] == 0).all() and (rec["queue_pos"] >= 0).all()
-    # the persistent launch, the status summary, and the tile-64 launch when a job is above order 32
-    assert one["launches"] <= 3
+    # the persistent launch, the status summary, and the tile-64 launch when a job is above
+    # order 32; jobs the narrow tile hands on add their wide rerun and a second summary
+    assert one["launches"] <= (3 if case != "retry_wide" else 5)
 
 
 def test_single_launch_residues_and_wide_ring():
