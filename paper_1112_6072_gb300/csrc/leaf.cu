@@ -8,7 +8,8 @@
 // A classification pass gives every job its variant: register width NMAX
 // (8/16/24/32 rows), ring width W (2 or 4 words) and path -- the blocked
 // walk of ryser4.cuh with 8 or 16 "N" slots when the row sums fit 7 bits
-// and the two sparsest columns touch at most 16 rows, else the plain walk
+// and the two sparsest columns touch at most 16 rows (the 8 slots split
+// 4 + 4 when the sparser column touches at most 4), else the plain walk
 // of ryser.cuh with the 7-, 15- or 31-bit product tree.  On the residue
 // path every leaf takes the modular walk of ryser_mod.cuh.  Each variant is
 // its own kernel, so each gets the registers it needs and no more.
@@ -95,8 +96,9 @@ __device__ int leaf_class(uint32_t job, const JobArrays& jobs, const uint64_t* _
             pb = b;
           }
         }
-      // 16 N slots: one of the two columns must fit the first 8
-      if (k <= 8) path = P_F8;
+      // 16 N slots: one of the two columns must fit the first 8; 4 + 4 split:
+      // the smaller column within the first 4
+      if (k <= 8) path = min(__popc(cm[pa]), __popc(cm[pb])) <= 4 ? P_F4 : P_F8;
       else if (k <= 16 && m > 8 && min(__popc(cm[pa]), __popc(cm[pb])) <= 8) path = P_F16;
     }
   }
@@ -249,6 +251,7 @@ cudaError_t launch_path(int path, const uint32_t* queue, int64_t nq, const uint6
     case P_G15: return launch_variant<NMAX, W, P_G15>(LEAF_ARGS);
     case P_G31: return launch_variant<NMAX, W, P_G31>(LEAF_ARGS);
     case P_F8: return launch_variant<NMAX, W, P_F8>(LEAF_ARGS);
+    case P_F4: return launch_variant<NMAX, W, P_F4>(LEAF_ARGS);
     case P_F16:
       if constexpr (NMAX >= 16) return launch_variant<NMAX, W, P_F16>(LEAF_ARGS);
       return cudaErrorInvalidValue;

@@ -14,7 +14,7 @@
 namespace {
 
 // path codes
-constexpr int P_G7 = 0, P_G15 = 1, P_G31 = 2, P_F8 = 3, P_F16 = 4, P_MOD = 5, P_BAD = 7;
+constexpr int P_G7 = 0, P_G15 = 1, P_G31 = 2, P_F8 = 3, P_F16 = 4, P_MOD = 5, P_F4 = 6, P_BAD = 7;
 
 __host__ __device__ __forceinline__ void leaf_split(int m, int chunk_log2, int& lanes, int& clog,
                                                     uint64_t& tasks) {
@@ -94,7 +94,9 @@ __device__ void load_blocked(const uint64_t* __restrict__ arena, int64_t off, in
   const int cb = (int)(key & 0xff);
   int clast = m - 1;
   while (clast == ca || clast == cb) --clast;
-  const bool a_first = __popc((unsigned)colcnt[ca]) <= 8;
+  // Gray column 0: the column of the pair touching fewer rows (at most 8 for
+  // the 16-slot form, at most 4 for the 4 + 4 split)
+  const bool a_first = __popc((unsigned)colcnt[ca]) <= __popc((unsigned)colcnt[cb]);
   const int g0 = a_first ? ca : cb, g1 = a_first ? cb : ca;  // Gray columns 0 and 1
   const uint32_t am = (uint32_t)colcnt[g0];
   const uint32_t tm = am | (uint32_t)colcnt[g1];
@@ -160,7 +162,7 @@ __device__ __forceinline__ void leaf_load(const uint64_t* __restrict__ arena, in
   if constexpr (PATH == P_MOD)
     load_mod(arena, off, m, nnz, NMAX, reinterpret_cast<uint32_t*>(delta), reinterpret_cast<uint32_t*>(rho0), lane,
              mod);
-  else if constexpr (PATH == P_F8 || PATH == P_F16)
+  else if constexpr (PATH == P_F8 || PATH == P_F16 || PATH == P_F4)
     load_blocked(arena, off, m, nnz, NMAX, delta, rho0, colcnt, lane);
   else
     load_plain(arena, off, m, nnz, NMAX, delta, rho0, lane);
@@ -195,6 +197,13 @@ __device__ __forceinline__ void leaf_task(const uint64_t* __restrict__ arena, in
     const uint32_t sm_ = ryser_lane_mod<NMAX>(reinterpret_cast<const uint32_t*>(delta),
                                               reinterpret_cast<const uint32_t*>(rho0), m, gb, mycnt, mod);
     words[0] = from_mont(warp_sum_mod(sm_, mod.p), mod);  // Sigma mod p, a plain residue
+  } else if constexpr (PATH == P_F4) {
+    if (m >= 3) {
+      run_lane4<NMAX, 8, W, true>(delta, rho0, m, gb, mycnt, words);
+      return;
+    }
+    typename WideT<W>::type sw = ryser_lane<NMAX, W, 7>(delta, rho0, m, gb, mycnt);
+    to_words(warp_sum(sw), words);
   } else if constexpr (PATH == P_F8) {
     if (m >= 3) {
       run_lane4<NMAX, 8, W>(delta, rho0, m, gb, mycnt, words);

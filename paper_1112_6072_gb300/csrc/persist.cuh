@@ -66,6 +66,7 @@ __device__ __forceinline__ void leaf_unit_path(int path, const uint64_t* arena, 
       case P_G15: leaf_unit<NMAX, W, P_G15>(LEAF_UNIT_ARGS); break;
       case P_G31: leaf_unit<NMAX, W, P_G31>(LEAF_UNIT_ARGS); break;
       case P_F8: leaf_unit<NMAX, W, P_F8>(LEAF_UNIT_ARGS); break;
+      case P_F4: leaf_unit<NMAX, W, P_F4>(LEAF_UNIT_ARGS); break;
       default:
         if constexpr (NMAX >= 16) leaf_unit<NMAX, W, P_F16>(LEAF_UNIT_ARGS);
         break;

@@ -15,7 +15,13 @@
 // column 0 sit in slots [0, 8) (N1) and slots [8, 16) hold none (N2), so the
 // N2 product only changes when column 1 flips and
 //     sum_t (-1)^t P1(t) P2(t) = (P1(0) - P1(1)) P2(0) + (P1(2) - P1(3)) P2(2),
-// two 64 x 64 -> wide products per block.
+// two 64 x 64 -> wide products per block.  For NN = 8 with Gray column 0
+// touching at most 4 rows (SPLIT4: its rows sit in slots [0, 4), so slots
+// [4, 8) only change when column 1 flips) the same identity with 4-slot
+// halves A and B gives
+//     sum_t (-1)^t prod_N = (PA(0) - PA(1)) PB(0) + (PA(2) - PA(3)) PB(2),
+// six 32-bit quad products and two widening multiplies per block instead of
+// four 8-slot products, and column 0 updates four slots instead of eight.
 // Column j >= 2 flips at code g with j = ctz(g) and updates every row from
 // shared memory (a broadcast, uniform across the warp).
 #pragma once
@@ -24,6 +30,11 @@
 #include "ryser.cuh"
 
 // product of the 8 slots [b, b+8) for |rho| < 2^7: two int32 quads, one widening multiply
+template <int NMAX>
+__device__ __forceinline__ int32_t prod4(const int32_t (&r)[NMAX], int b) {
+  return r[b] * r[b + 1] * r[b + 2] * r[b + 3];
+}
+
 template <int NMAX>
 __device__ __forceinline__ int64_t prod8(const int32_t (&r)[NMAX], int b) {
   const int32_t q0 = r[b] * r[b + 1] * r[b + 2] * r[b + 3];
@@ -44,12 +55,13 @@ __device__ __forceinline__ typename WideT<W>::type prod_groups(const int32_t (&r
   return p;
 }
 
-template <int NMAX, int NN, int W>
+template <int NMAX, int NN, int W, bool SPLIT4 = false>
 __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __restrict__ delta,
                                                                const int32_t* __restrict__ rho0, int m,
                                                                uint64_t gb, uint64_t cnt) {
   typedef typename WideT<W>::type T;
   static_assert(NN % 8 == 0 && NN <= NMAX && NMAX % 8 == 0, "slot groups of 8");
+  static_assert(!SPLIT4 || NN == 8, "the 4 + 4 split is of the 8-slot form");
   constexpr int GN = NN / 8;
   constexpr int GZ = (NMAX - NN) / 8;
   if (cnt == 0) return wide_from64(0, (T*)nullptr);
@@ -100,7 +112,27 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __
   const uint64_t ge = gb + cnt;
   for (uint64_t g = gb;;) {
     const int32_t s1 = ((g >> 2) & 1) ? -1 : 1;
-    if constexpr (GN == 1) {
+    if constexpr (SPLIT4) {
+      // |rho| < 2^7: quads below 2^28, their differences below 2^29, sn below 2^58
+      const int32_t a0 = prod4<NMAX>(rho, 0), b0 = prod4<NMAX>(rho, 4);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) rho[i] += d0[i];
+      const int32_t a1 = prod4<NMAX>(rho, 0);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) rho[i] += s1 * d1[i];
+      const int32_t a2 = prod4<NMAX>(rho, 0), b2 = prod4<NMAX>(rho, 4);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) rho[i] -= d0[i];
+      const int32_t a3 = prod4<NMAX>(rho, 0);
+      const int64_t sn = (int64_t)(a0 - a1) * b0 + (int64_t)(a2 - a3) * b2;
+      if constexpr (GZ == 0) {
+        wide_add(acc, wide_from64(sn, (T*)nullptr));
+      } else if constexpr (GZ == 1) {
+        wide_add(acc, wide_mul64x64(sn, prod8<NMAX>(rho, NN), (T*)nullptr));
+      } else {
+        wide_add(acc, wide_mul64(prod_groups<NMAX, W, NN, GZ>(rho), sn));
+      }
+    } else if constexpr (GN == 1) {
       const int64_t n0 = prod8<NMAX>(rho, 0);
 #pragma unroll
       for (int i = 0; i < NN; ++i) rho[i] += d0[i];
@@ -162,10 +194,10 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __
 }
 
 // Lane share of the blocked walk, warp-summed into lane 0.
-template <int NMAX, int NN, int W>
+template <int NMAX, int NN, int W, bool SPLIT4 = false>
 __device__ __forceinline__ void run_lane4(const int32_t* delta, const int32_t* rho0, int m, uint64_t gb,
                                           uint64_t cnt, uint64_t* words) {
-  typename WideT<W>::type s = ryser_lane4<NMAX, NN, W>(delta, rho0, m, gb, cnt);
+  typename WideT<W>::type s = ryser_lane4<NMAX, NN, W, SPLIT4>(delta, rho0, m, gb, cnt);
   s = warp_sum(s);
   to_words(s, words);
 }
