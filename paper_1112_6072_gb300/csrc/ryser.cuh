@@ -107,6 +107,47 @@ __device__ __forceinline__ typename WideT<W>::type row_product(const int32_t (&r
   return p;
 }
 
+// rho -= col or rho += col over NMAX slots (col 16-byte aligned in shared
+// memory).  The direction is a branch, not a multiply by +-1: the updates
+// are plain integer adds on the ALU pipe, leaving the multiply pipe to the
+// row products (the direction is uniform across the warp at all but one step
+// of a lane's block of codes).
+template <int NMAX>
+__device__ __forceinline__ void col_update(int32_t (&rho)[NMAX], const int32_t* __restrict__ col, bool neg) {
+  const int4* p = reinterpret_cast<const int4*>(col);
+  if (neg) {
+#pragma unroll
+    for (int k = 0; k < NMAX / 4; ++k) {
+      const int4 v = p[k];
+      rho[4 * k] -= v.x;
+      rho[4 * k + 1] -= v.y;
+      rho[4 * k + 2] -= v.z;
+      rho[4 * k + 3] -= v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NMAX / 4; ++k) {
+      const int4 v = p[k];
+      rho[4 * k] += v.x;
+      rho[4 * k + 1] += v.y;
+      rho[4 * k + 2] += v.z;
+      rho[4 * k + 3] += v.w;
+    }
+  }
+}
+
+// the same for N register values
+template <int N, int NMAX>
+__device__ __forceinline__ void reg_update(int32_t (&rho)[NMAX], const int32_t* d, bool neg) {
+  if (neg) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) rho[i] -= d[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) rho[i] += d[i];
+  }
+}
+
 // One lane's share of Sigma: codes g in [gb, gb + cnt), gb and cnt even.
 // delta: shared memory, column j at delta[j * NMAX + i] = 2 a_ij (j < m-1),
 // rows i >= m zero.  rho0: shared, rho_i(empty), rows i >= m equal to 1.
@@ -153,24 +194,13 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane(const int32_t* __r
     // even code g: +prod
     wide_add(acc, row_product<NMAX, W, BC>(rho));
     // odd code g+1 flips column 0; it enters S iff bit 1 of g+1 is 0
-    const int32_t s0 = ((g >> 1) & 1) ? -1 : 1;
-#pragma unroll
-    for (int i = 0; i < NMAX; ++i) rho[i] += s0 * d0[i];
+    reg_update<NMAX, NMAX>(rho, d0, (g >> 1) & 1);
     wide_sub(acc, row_product<NMAX, W, BC>(rho));
     g += 2;
     if (g >= ge) break;
     // even code g flips column j = ctz(g) >= 1
     const int j = __ffsll((long long)g) - 1;
-    const int32_t s = ((g >> (j + 1)) & 1) ? -1 : 1;
-    const int4* p = reinterpret_cast<const int4*>(delta + j * NMAX);
-#pragma unroll
-    for (int k = 0; k < NMAX / 4; ++k) {
-      int4 v = p[k];
-      rho[4 * k] += s * v.x;
-      rho[4 * k + 1] += s * v.y;
-      rho[4 * k + 2] += s * v.z;
-      rho[4 * k + 3] += s * v.w;
-    }
+    col_update<NMAX>(rho, delta + j * NMAX, (g >> (j + 1)) & 1);
   }
   return acc;
 }

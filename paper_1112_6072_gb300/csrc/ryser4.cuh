@@ -118,8 +118,7 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __
 #pragma unroll
       for (int i = 0; i < 4; ++i) rho[i] += d0[i];
       const int32_t a1 = prod4<NMAX>(rho, 0);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) rho[i] += s1 * d1[i];
+      reg_update<8, NMAX>(rho, d1, s1 < 0);
       const int32_t a2 = prod4<NMAX>(rho, 0), b2 = prod4<NMAX>(rho, 4);
 #pragma unroll
       for (int i = 0; i < 4; ++i) rho[i] -= d0[i];
@@ -137,8 +136,7 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __
 #pragma unroll
       for (int i = 0; i < NN; ++i) rho[i] += d0[i];
       const int64_t n1 = prod8<NMAX>(rho, 0);
-#pragma unroll
-      for (int i = 0; i < NN; ++i) rho[i] += s1 * d1[i];
+      reg_update<NN, NMAX>(rho, d1, s1 < 0);
       const int64_t n2 = prod8<NMAX>(rho, 0);
 #pragma unroll
       for (int i = 0; i < NN; ++i) rho[i] -= d0[i];
@@ -158,8 +156,7 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __
 #pragma unroll
       for (int i = 0; i < 8; ++i) rho[i] += d0[i];
       const int64_t a1 = prod8<NMAX>(rho, 0);
-#pragma unroll
-      for (int i = 0; i < NN; ++i) rho[i] += s1 * d1[i];
+      reg_update<NN, NMAX>(rho, d1, s1 < 0);
       const int64_t a2 = prod8<NMAX>(rho, 0);
       const int64_t b2 = prod8<NMAX>(rho, 8);
 #pragma unroll
@@ -179,16 +176,7 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __
     g += 4;
     if (g >= ge) break;
     const int j = __ffsll((long long)g) - 1;  // >= 2
-    const int32_t s = ((g >> (j + 1)) & 1) ? -1 : 1;
-    const int4* p = reinterpret_cast<const int4*>(delta + j * NMAX);
-#pragma unroll
-    for (int k = 0; k < NMAX / 4; ++k) {
-      const int4 v = p[k];
-      rho[4 * k] += s * v.x;
-      rho[4 * k + 1] += s * v.y;
-      rho[4 * k + 2] += s * v.z;
-      rho[4 * k + 3] += s * v.w;
-    }
+    col_update<NMAX>(rho, delta + j * NMAX, (g >> (j + 1)) & 1);
   }
   return acc;
 }
