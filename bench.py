@@ -34,9 +34,9 @@ METRIC = "C60 60x60 permanent wall time; leaf permanents/sec; % of integer-ALU r
 LEAF_COUNT = 100_000
 # DRAM bytes (read + write) of one evaluation per leaf matrix, measured with
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum over the evaluation's
-# launches) on the 20,000-matrix case of the same seed: 32.4 MB per
+# launches) on the 20,000-matrix case of the same seed: 29.9 MB per
 # evaluation; the traffic is per leaf, so it scales with the batch
-LEAF_TRAFFIC_BYTES_PER_MATRIX = 32.4e6 / 20_000
+LEAF_TRAFFIC_BYTES_PER_MATRIX = 29.9e6 / 20_000
 LEAF_SEED = 20240601
 C60_SEED = 60
 

@@ -38,11 +38,12 @@ template <int NM, int W, int PATH>
 __device__ __forceinline__ void leaf_walk(const int32_t* delta, const int32_t* rho0, int m, uint64_t gb, uint64_t cnt,
                                        uint64_t* words) {
   if constexpr (PATH == 3) {
-    run_lane4<NM, 8, W>(delta, rho0, m, gb, cnt, words);
+    run_lane4<NM, 8, W, false, false>(delta, rho0, m, gb, cnt, words);
   } else if constexpr (PATH == 4) {
-    run_lane4<NM, 16, W>(delta, rho0, m, gb, cnt, words);
+    run_lane4<NM, 16, W, false, false>(delta, rho0, m, gb, cnt, words);
   } else {
-    typename WideT<W>::type s = ryser_lane<NM, W, PATH == 0 ? 7 : (PATH == 1 ? 15 : 31)>(delta, rho0, m, gb, cnt);
+    typename WideT<W>::type s =
+        ryser_lane<NM, W, PATH == 0 ? 7 : (PATH == 1 ? 15 : 31), false>(delta, rho0, m, gb, cnt);
     s = warp_sum(s);
     to_words(s, words);
   }

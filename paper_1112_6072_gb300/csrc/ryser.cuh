@@ -108,14 +108,26 @@ __device__ __forceinline__ typename WideT<W>::type row_product(const int32_t (&r
 }
 
 // rho -= col or rho += col over NMAX slots (col 16-byte aligned in shared
-// memory).  The direction is a branch, not a multiply by +-1: the updates
-// are plain integer adds on the ALU pipe, leaving the multiply pipe to the
-// row products (the direction is uniform across the warp at all but one step
-// of a lane's block of codes).
-template <int NMAX>
+// memory).  BR: the direction is a branch, not a multiply by +-1, so the
+// updates are plain integer adds on the ALU pipe, leaving the multiply pipe
+// to the row products (the direction is uniform across the warp at all but
+// one step of a lane's block of codes).  The leaf kernels take the branch;
+// the depth-first evaluator, whose leaves sit in a larger kernel, keeps the
+// shorter multiply form.
+template <int NMAX, bool BR>
 __device__ __forceinline__ void col_update(int32_t (&rho)[NMAX], const int32_t* __restrict__ col, bool neg) {
   const int4* p = reinterpret_cast<const int4*>(col);
-  if (neg) {
+  if constexpr (!BR) {
+    const int32_t s = neg ? -1 : 1;
+#pragma unroll
+    for (int k = 0; k < NMAX / 4; ++k) {
+      const int4 v = p[k];
+      rho[4 * k] += s * v.x;
+      rho[4 * k + 1] += s * v.y;
+      rho[4 * k + 2] += s * v.z;
+      rho[4 * k + 3] += s * v.w;
+    }
+  } else if (neg) {
 #pragma unroll
     for (int k = 0; k < NMAX / 4; ++k) {
       const int4 v = p[k];
@@ -137,9 +149,13 @@ __device__ __forceinline__ void col_update(int32_t (&rho)[NMAX], const int32_t* 
 }
 
 // the same for N register values
-template <int N, int NMAX>
+template <int N, int NMAX, bool BR>
 __device__ __forceinline__ void reg_update(int32_t (&rho)[NMAX], const int32_t* d, bool neg) {
-  if (neg) {
+  if constexpr (!BR) {
+    const int32_t s = neg ? -1 : 1;
+#pragma unroll
+    for (int i = 0; i < N; ++i) rho[i] += s * d[i];
+  } else if (neg) {
 #pragma unroll
     for (int i = 0; i < N; ++i) rho[i] -= d[i];
   } else {
@@ -151,7 +167,7 @@ __device__ __forceinline__ void reg_update(int32_t (&rho)[NMAX], const int32_t* 
 // One lane's share of Sigma: codes g in [gb, gb + cnt), gb and cnt even.
 // delta: shared memory, column j at delta[j * NMAX + i] = 2 a_ij (j < m-1),
 // rows i >= m zero.  rho0: shared, rho_i(empty), rows i >= m equal to 1.
-template <int NMAX, int W, int BC>
+template <int NMAX, int W, int BC, bool BR = true>
 __device__ __forceinline__ typename WideT<W>::type ryser_lane(const int32_t* __restrict__ delta,
                                                               const int32_t* __restrict__ rho0, int m,
                                                               uint64_t gb, uint64_t cnt) {
@@ -194,13 +210,13 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane(const int32_t* __r
     // even code g: +prod
     wide_add(acc, row_product<NMAX, W, BC>(rho));
     // odd code g+1 flips column 0; it enters S iff bit 1 of g+1 is 0
-    reg_update<NMAX, NMAX>(rho, d0, (g >> 1) & 1);
+    reg_update<NMAX, NMAX, BR>(rho, d0, (g >> 1) & 1);
     wide_sub(acc, row_product<NMAX, W, BC>(rho));
     g += 2;
     if (g >= ge) break;
     // even code g flips column j = ctz(g) >= 1
     const int j = __ffsll((long long)g) - 1;
-    col_update<NMAX>(rho, delta + j * NMAX, (g >> (j + 1)) & 1);
+    col_update<NMAX, BR>(rho, delta + j * NMAX, (g >> (j + 1)) & 1);
   }
   return acc;
 }

@@ -55,7 +55,7 @@ __device__ __forceinline__ typename WideT<W>::type prod_groups(const int32_t (&r
   return p;
 }
 
-template <int NMAX, int NN, int W, bool SPLIT4 = false>
+template <int NMAX, int NN, int W, bool SPLIT4 = false, bool BR = true>
 __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __restrict__ delta,
                                                                const int32_t* __restrict__ rho0, int m,
                                                                uint64_t gb, uint64_t cnt) {
@@ -118,7 +118,7 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __
 #pragma unroll
       for (int i = 0; i < 4; ++i) rho[i] += d0[i];
       const int32_t a1 = prod4<NMAX>(rho, 0);
-      reg_update<8, NMAX>(rho, d1, s1 < 0);
+      reg_update<8, NMAX, BR>(rho, d1, s1 < 0);
       const int32_t a2 = prod4<NMAX>(rho, 0), b2 = prod4<NMAX>(rho, 4);
 #pragma unroll
       for (int i = 0; i < 4; ++i) rho[i] -= d0[i];
@@ -136,7 +136,7 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __
 #pragma unroll
       for (int i = 0; i < NN; ++i) rho[i] += d0[i];
       const int64_t n1 = prod8<NMAX>(rho, 0);
-      reg_update<NN, NMAX>(rho, d1, s1 < 0);
+      reg_update<NN, NMAX, BR>(rho, d1, s1 < 0);
       const int64_t n2 = prod8<NMAX>(rho, 0);
 #pragma unroll
       for (int i = 0; i < NN; ++i) rho[i] -= d0[i];
@@ -156,7 +156,7 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __
 #pragma unroll
       for (int i = 0; i < 8; ++i) rho[i] += d0[i];
       const int64_t a1 = prod8<NMAX>(rho, 0);
-      reg_update<NN, NMAX>(rho, d1, s1 < 0);
+      reg_update<NN, NMAX, BR>(rho, d1, s1 < 0);
       const int64_t a2 = prod8<NMAX>(rho, 0);
       const int64_t b2 = prod8<NMAX>(rho, 8);
 #pragma unroll
@@ -176,16 +176,16 @@ __device__ __forceinline__ typename WideT<W>::type ryser_lane4(const int32_t* __
     g += 4;
     if (g >= ge) break;
     const int j = __ffsll((long long)g) - 1;  // >= 2
-    col_update<NMAX>(rho, delta + j * NMAX, (g >> (j + 1)) & 1);
+    col_update<NMAX, BR>(rho, delta + j * NMAX, (g >> (j + 1)) & 1);
   }
   return acc;
 }
 
 // Lane share of the blocked walk, warp-summed into lane 0.
-template <int NMAX, int NN, int W, bool SPLIT4 = false>
+template <int NMAX, int NN, int W, bool SPLIT4 = false, bool BR = true>
 __device__ __forceinline__ void run_lane4(const int32_t* delta, const int32_t* rho0, int m, uint64_t gb,
                                           uint64_t cnt, uint64_t* words) {
-  typename WideT<W>::type s = ryser_lane4<NMAX, NN, W, SPLIT4>(delta, rho0, m, gb, cnt);
+  typename WideT<W>::type s = ryser_lane4<NMAX, NN, W, SPLIT4, BR>(delta, rho0, m, gb, cnt);
   s = warp_sum(s);
   to_words(s, words);
 }
