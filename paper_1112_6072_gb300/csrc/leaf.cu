@@ -85,17 +85,19 @@ __device__ int leaf_class(uint32_t job, const JobArrays& jobs, const uint64_t* _
     const int bc = bit_class(rmax);
     path = bc == 7 ? P_G7 : (bc == 15 ? P_G15 : P_G31);
     if (bc == 7 && m >= 3) {
-      // the column pair touching the fewest rows (lowest pair on ties)
-      int k = 64, pa = 0, pb = 1;
+      // the column pair for the blocked walk: a pair for the 4 + 4 split
+      // (union within 8 rows, one column within 4) if there is one, else the
+      // pair touching the fewest rows; fewest rows, then lowest pair, on ties
+      // (the same rule as load_blocked)
+      unsigned best = 0xffffffffu;
       for (int a = 0; a < m; ++a)
         for (int b = a + 1; b < m; ++b) {
-          const int u = __popc(cm[a] | cm[b]);
-          if (u < k) {
-            k = u;
-            pa = a;
-            pb = b;
-          }
+          const unsigned u = (unsigned)__popc(cm[a] | cm[b]);
+          const bool split = u <= 8 && min(__popc(cm[a]), __popc(cm[b])) <= 4;
+          const unsigned kk = ((split ? 0u : 1u) << 24) | (u << 16) | ((unsigned)a << 8) | (unsigned)b;
+          best = kk < best ? kk : best;
         }
+      const int k = (int)((best >> 16) & 0xff), pa = (int)((best >> 8) & 0xff), pb = (int)(best & 0xff);
       // 16 N slots: one of the two columns must fit the first 8; 4 + 4 split:
       // the smaller column within the first 4
       if (k <= 8) path = min(__popc(cm[pa]), __popc(cm[pb])) <= 4 ? P_F4 : P_F8;

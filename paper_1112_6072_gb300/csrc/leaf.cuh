@@ -79,12 +79,17 @@ __device__ void load_blocked(const uint64_t* __restrict__ arena, int64_t off, in
     for (int p = v.rowptr[lane]; p < v.rowptr[lane + 1]; ++p)
       atomicOr(reinterpret_cast<unsigned*>(&colcnt[v.col[p]]), 1u << lane);
   __syncwarp();
-  // the column pair touching the fewest rows, lowest (a, b) on ties
+  // the column pair: one for the 4 + 4 split (union within 8 rows, one
+  // column within 4) if there is one, else the pair touching the fewest
+  // rows; fewest rows, then lowest (a, b), on ties (leaf_class's rule)
   unsigned key = 0xffffffffu;
   if (lane < m) {
     const unsigned ma = (unsigned)colcnt[lane];
+    const int na = __popc(ma);
     for (int b = lane + 1; b < m; ++b) {
-      const unsigned kk = ((unsigned)__popc(ma | (unsigned)colcnt[b]) << 16) | ((unsigned)lane << 8) | (unsigned)b;
+      const unsigned u = (unsigned)__popc(ma | (unsigned)colcnt[b]);
+      const bool split = u <= 8 && min(na, __popc((unsigned)colcnt[b])) <= 4;
+      const unsigned kk = ((split ? 0u : 1u) << 24) | (u << 16) | ((unsigned)lane << 8) | (unsigned)b;
       key = kk < key ? kk : key;
     }
   }
