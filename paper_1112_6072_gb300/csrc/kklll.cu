@@ -399,9 +399,10 @@ cudaError_t launch_k(const JobArrays& jobs, int64_t njobs, const uint64_t* arena
 // second kernel combines a job's parts.
 template <int MT>
 struct TCfg {
-  // as many warps as 227 KB of shared memory holds (14, 6, 3)
-  static constexpr int WARPS = MT <= 8 ? 14 : (MT <= 12 ? 6 : 3);
   static constexpr size_t WARP_BYTES = sizeof(float2) * MT * MT * 32;
+  // as many warps as 227 KB of shared memory holds (14 for MT = 8, 9 for 10,
+  // 7 for 11, 6 for 12)
+  static constexpr int WARPS = (int)(232448 / WARP_BYTES) < 16 ? (int)(232448 / WARP_BYTES) : 16;
   static constexpr size_t SMEM = WARPS * WARP_BYTES;
   static_assert(SMEM <= 232448, "at most 227 KB of dynamic shared memory per block");
 };
@@ -780,6 +781,10 @@ cudaError_t launch_kklll(const JobArrays& jobs, int64_t njobs, const uint64_t* a
   double2* part = reinterpret_cast<double2*>(scratch);
   const int chunks = kklll_chunks(njobs, max_order, trials);
   if (max_order <= 8) return launch_thread<8>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
+  // jobs of order 9-12 padded to the next of 10, 11, 12 (less padding: fewer
+  // flops and more warps per SM)
+  if (max_order <= 10) return launch_thread<10>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
+  if (max_order <= 11) return launch_thread<11>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
   if (max_order <= 12) return launch_thread<12>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
   if (max_order <= 16) return launch_lanes<16, 2>(jobs, njobs, arena, trials, seed, log_ap, part, chunks, s);
   const int ct = kklll_chunk_trials(njobs, max_order, trials);
