@@ -187,6 +187,41 @@ def run_ours(args, rank, world, torch):
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t) * 1e3)
     assert r2 == res
+    serial_ms = min(e2e_ms)
+    # the same steps pipelined: the next step's plan (validation and CSR
+    # blocks on host threads, its upload on a stream of its own) is built
+    # while the current step evaluates on another stream; every step still
+    # uploads its inputs and downloads its results inside the timed region
+    pipelined_ms = None
+    try:
+        import concurrent.futures as cf
+        streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+
+        def make(i):
+            torch.cuda.set_device(dev)
+            pn = pk.Plan.packed(packed, orders_n, chunk_log2=args.chunk_log2, order="natural", stream=streams[i % 2])
+            pn.expand()
+            return pn
+
+        nsteps = max(2, min(args.steps, 4))
+        ok = True
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        with cf.ThreadPoolExecutor(1) as ex:
+            fut = ex.submit(make, 0)
+            for i in range(nsteps):
+                p2 = fut.result()
+                if i + 1 < nsteps:
+                    fut = ex.submit(make, i + 1)
+                p2.evaluate(order=order)
+                ok = ok and p2.results() == res
+                p2.close()
+        torch.cuda.synchronize()
+        if ok:
+            pipelined_ms = (time.perf_counter() - t) * 1e3 / nsteps
+    except Exception as exc:  # the serial figure stands
+        print(f"pipelined end-to-end run skipped: {exc}", file=sys.stderr)
+    e2e_best = min(serial_ms, pipelined_ms) if pipelined_ms else serial_ms
     # the same from a list of separate arrays (one address read per array)
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -235,8 +270,9 @@ def run_ours(args, rank, world, torch):
                    "autotune": tune,
                    "step": "one evaluation of the whole batch, replayed as a captured CUDA graph",
                    "parallelism": f"jobs sharded per rank (x{world})"},
-        "e2e": {"value": LEAF_COUNT * world / (min(e2e_ms) * 1e-3), "unit": "leaf permanents/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms": min(e2e_ms),
+        "e2e": {"value": LEAF_COUNT * world / (e2e_best * 1e-3), "unit": "leaf permanents/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms": e2e_best,
+                "serial_ms": serial_ms, "pipelined_ms": pipelined_ms,
                 "input": "one host buffer of the matrices back to back (Plan.packed)",
                 "list_input_ms": min(list_ms)},
         "gpu_launches": launches * args.steps if launches is not None else None,
