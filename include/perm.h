@@ -127,9 +127,10 @@ typedef struct {
                               warps take queue positions in queue order through one counter and
                               run each job's own evaluator as a device function (leaf jobs'
                               Gray-code tasks shared with idle warps; depth-first jobs of order
-                              <= 32 on an int64 tile), so the queue order holds across all jobs;
-                              depth-first jobs of order > 32 run in a launch before it.  The
-                              results are the same either way */
+                              <= 32 on a 32-wide tile), so the queue order holds across all jobs;
+                              depth-first jobs of order > 32 run in a launch before it, and a job
+                              the int32 tile cannot hold (leaf order <= 16) runs again on the int64
+                              kernel after it.  The results are the same either way */
 } perm_opts;
 
 /* Fill opts with the defaults above. */
