@@ -15,6 +15,10 @@ over the rest the block contributes Z (P(0) - P(1) + P(2) - P(3)).  When the
 rows of column 0 sit in slots [0, 8) and slots [8, 16) hold none of them,
 the product P2 over [8, 16) only changes when column 1 flips, so
 P(0) - P(1) + P(2) - P(3) = (P1(0) - P1(1)) P2(0) + (P1(2) - P1(3)) P2(2).
+The same split of 8 slots into 4 + 4 applies when column 0 touches at most
+4 rows; the leaf kernels then take a pair eligible for it (union within 8
+rows, one column within 4) before the fewest-rows pair, column 0 being the
+sparser column, and form the quad products in 32 bits (|rho| < 2^7).
 """
 import math
 
@@ -24,11 +28,22 @@ import pytest
 from oracle import exact as oracle
 
 
-def _layout(a, lim0):
+def _layout(a, lim0, kernel_rule=False):
     m = a.shape[0]
     nz = a != 0
-    u, ca, cb = min((int((nz[:, x] | nz[:, y]).sum()), x, y) for x in range(m) for y in range(x + 1, m))
-    g0, g1 = (ca, cb) if nz[:, ca].sum() <= lim0 else (cb, ca)
+    cnt = nz.sum(axis=0)
+    if kernel_rule:
+        # the leaf kernels' rule: a pair for the 4 + 4 split first, then the
+        # fewest rows, then the lowest pair; column 0 the sparser column
+        def key(x, y):
+            u = int((nz[:, x] | nz[:, y]).sum())
+            split = u <= 8 and min(cnt[x], cnt[y]) <= 4
+            return (0 if split else 1, u, x, y)
+        _, u, ca, cb = min(key(x, y) for x in range(m) for y in range(x + 1, m))
+        g0, g1 = (ca, cb) if cnt[ca] <= cnt[cb] else (cb, ca)
+    else:
+        u, ca, cb = min((int((nz[:, x] | nz[:, y]).sum()), x, y) for x in range(m) for y in range(x + 1, m))
+        g0, g1 = (ca, cb) if nz[:, ca].sum() <= lim0 else (cb, ca)
     clast = m - 1
     while clast in (ca, cb):
         clast -= 1
@@ -49,9 +64,9 @@ def _layout(a, lim0):
     return u, int(am.sum()), slot, gray_index
 
 
-def _blocked_walk(a, nmax, nn, split):
+def _blocked_walk(a, nmax, nn, split, kernel_rule=False):
     m = a.shape[0]
-    _, n_col0, slot, gray_index = _layout(a, nn // 2 if split else nn)
+    _, n_col0, slot, gray_index = _layout(a, nn // 2 if split else nn, kernel_rule)
     delta = [[0] * nmax for _ in range(m - 1)]
     rho = [1] * nmax
     for r in range(m):
@@ -81,6 +96,8 @@ def _blocked_walk(a, nmax, nn, split):
     while True:
         s1 = -1 if (g >> 2) & 1 else 1
         if split:
+            if nn == 8:  # the quads of the 4 + 4 split are formed in 32 bits
+                assert all(abs(prod(lo, lo + 4)) < 1 << 28 for lo in (0, 4))
             a0, b0 = prod(0, half), prod(half, nn)
             add(0, 0, half)
             a1 = prod(0, half)
@@ -142,4 +159,26 @@ def test_sixteen_slot_split_identity(seed):
         if np.abs(a).sum(axis=1).max() >= 128 or not (8 < u <= 16 and kmin <= 8):
             continue
         assert _blocked_walk(a, 16, 16, True) == oracle.permanent(a.astype(np.int64))
+        done += 1
+
+
+@pytest.mark.parametrize("seed", [7, 8, 9])
+def test_eight_slot_four_plus_four_identity(seed):
+    """Pairs eligible for the 4 + 4 split (union within 8 rows, one column
+    within 4), chosen and oriented as the leaf kernels do: the split block
+    sum with every quad product in 32 bits."""
+    rng = np.random.default_rng(seed)
+    done = 0
+    while done < 12:
+        n = int(rng.integers(5, 21))
+        a = (rng.random((n, n)) < rng.uniform(0.15, 0.35)) * rng.integers(1, 4, size=(n, n))
+        if np.abs(a).sum(axis=1).max() >= 128 or (a != 0).sum(axis=1).min() == 0:
+            continue
+        nz = a != 0
+        cnt = nz.sum(axis=0)
+        if not any(int((nz[:, x] | nz[:, y]).sum()) <= 8 and min(cnt[x], cnt[y]) <= 4
+                   for x in range(n) for y in range(x + 1, n)):
+            continue
+        nmax = 8 if n <= 8 else (16 if n <= 16 else 24)
+        assert _blocked_walk(a, nmax, 8, True, kernel_rule=True) == oracle.permanent(a.astype(np.int64))
         done += 1
