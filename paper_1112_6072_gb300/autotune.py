@@ -10,8 +10,9 @@
 * evaluator warps per SM for the depth-first kernel.
 
 Every candidate runs through the library on the GPU on a sample input and
-the fastest whole-path time wins.  Results are cached per (order, nonzeros
-per row, GPU name) in memory and optionally in a JSON file.
+the fastest whole-path time wins.  Results are cached per matrix (order,
+nonzeros, the range of nonzeros per row and a hash of the entries) and GPU
+name, in memory and optionally in a JSON file.
 """
 from __future__ import annotations
 
@@ -35,10 +36,14 @@ def _gpu_name():
 
 
 def _key(a) -> str:
-    a = np.asarray(a)
+    """Cache key of a matrix: two matrices share tuned knobs only when their
+    entries are equal (a hash of them), on the same GPU model."""
+    import hashlib
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int64))
     n = a.shape[0]
-    r = (a != 0).sum(axis=1)
-    return f"n{n}_r{int(r.min())}-{int(r.max())}_{_gpu_name()}"
+    r = (a != 0).sum(axis=1) if n else np.zeros(1, np.int64)
+    h = hashlib.sha256(a.tobytes() + np.int64(n).tobytes()).hexdigest()[:16]
+    return f"n{n}_nnz{int((a != 0).sum())}_r{int(r.min())}-{int(r.max())}_{h}_{_gpu_name()}"
 
 
 def _time_path(mats, reps=2, **opts) -> float:

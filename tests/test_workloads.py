@@ -86,3 +86,14 @@ def test_random01_exact_count_and_no_empty_line():
     a = W.random01(60, 240, 3)
     assert int(a.sum()) == 240 and set(np.unique(a)) == {0, 1}
     assert (a.sum(axis=0) > 0).all() and (a.sum(axis=1) > 0).all()
+
+
+def test_autotune_cache_key_tells_matrices_apart():
+    """The tuner's cache key: equal matrices share it, a different pattern
+    with the same order and row counts does not."""
+    from paper_1112_6072_gb300 import autotune
+    a = W.regular3(36, 1)
+    b = W.regular3(36, 2)  # same order, every row with 3 nonzeros
+    assert autotune._key(a) == autotune._key(a.copy())
+    assert autotune._key(a) != autotune._key(b)
+    assert autotune._key(a) != autotune._key(2 * a)
